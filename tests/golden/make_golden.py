@@ -1,0 +1,41 @@
+"""Writes the stored expected values under tests/golden/.
+
+Calls only ``oracle.exact`` (mpmath brute force) on inputs from
+``dqmc_inputs``; nothing here comes from the CUDA path.
+
+single_n16_mpmath.txt -- 4x4 periodic lattice, t=1, U=4, dtau=0.1, beta=8
+(M=80), Hirsch +-1 field of seed 2003_05286*1000 + 100 + 0: the exact
+G = [1 + B_80...B_1]^{-1} (Eq. (etgf)) and log|det(1 + B_80...B_1)| with its
+sign, from the naive product at the precision oracle.exact.required_dps picks.
+First row: logdet, sign; then the 256 entries of G in row-major order.
+
+Run from the repository root:  python tests/golden/make_golden.py
+"""
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+import dqmc_inputs as di  # noqa: E402
+from oracle import exact as ex  # noqa: E402
+
+
+def main():
+    inst = di.single_n16()
+    bf = ex.BruteForce(inst.K, inst.dtau, inst.V)
+    G, ld, s = bf.greens(1)
+    G = bf.to_numpy(G)
+    out = os.path.join(os.path.dirname(os.path.abspath(__file__)), "single_n16_mpmath.txt")
+    with open(out, "w") as f:
+        f.write(f"# mpmath dps={bf.dps}; first row: logdet sign; then G row-major\n")
+        f.write(f"{float(ld):.17e} {s:d}\n")
+        for v in G.ravel():
+            f.write(f"{v:.17e}\n")
+    print("wrote", out, "dps", bf.dps)
+
+
+if __name__ == "__main__":
+    main()
