@@ -1,0 +1,369 @@
+#!/usr/bin/env python
+"""Throughput of the stabilised DQMC Green's-function path on GB300.
+
+Workload (default, ``n256_beta20``): 16x16 periodic square lattice (N=256),
+t=1, U=4, dtau=0.1, beta=20 (M=200), k=10, a batch of 128 Hirsch +-1 field
+configurations per GPU; one step = one dqmc_greens call over the batch:
+exp(-dtau K), 200 slice products, 20 pivoted-QR re-factorisations, the Loh
+inversion and the log det of every instance.  Metric: Green's functions per
+second (whole job, all ranks).
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+For N > 1 launch under torch.distributed.run: every rank runs its own batch
+(independent instances, no collective on the data path) and the slowest rank's
+time sets the job time (weak scaling).
+
+``--impl reference`` times the CPU oracle (NumPy/SciPy FP64, the paper's LAPACK
+routines) on a bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import dqmc_inputs as di  # noqa: E402
+
+# FP64 ALU peak of GB300: 152 SMs x 2 DFMA/clk/SM (4 flop) x 2070 MHz.  The
+# recipe's nominal FP64 figure (1.25 TFLOP/s) gives the same 2-DFMA/clk/SM
+# issue rate; a DFMA-only probe on this pool measured 1.20 TFLOP/s at ~2.0 GHz.
+FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12
+
+WORKLOADS = {
+    "n256_beta20": dict(L=16, U=4.0, dtau=0.1, beta=20.0, k=10, batch=128, config=4),
+    "n64_beta40": dict(L=8, U=4.0, dtau=0.1, beta=40.0, k=10, batch=256, config=2),
+    "n16_beta8": dict(L=4, U=4.0, dtau=0.1, beta=8.0, k=10, batch=1, config=1),
+}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--workload", default="n256_beta20", choices=sorted(WORKLOADS))
+    p.add_argument("--batch", type=int, default=None, help="override instances per GPU")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    return p.parse_args()
+
+
+def make_inputs(wl: dict, rank: int, batch: int):
+    """K and the (batch, M, N) fields of this rank's instances (disjoint seeds per rank)."""
+    insts = [di.hubbard_instance(wl["L"], wl["U"], wl["dtau"], wl["beta"], wl["k"],
+                                 di.instance_seed(wl["config"], rank * batch + i))
+             for i in range(batch)]
+    return insts[0].K, np.stack([x.V for x in insts]), insts
+
+
+def flops_per_greens(N: int, M: int, k: int) -> float:
+    """Algorithmic FP64 flops of one G: 2MN^3 chain + ceil(M/k)(8/3 + 1)N^3 QR/update + Loh."""
+    nc = -(-M // k)
+    loh = 2 * (2.0 / 3.0 + 2.0)   # two LU solves with N right-hand sides
+    return (2.0 * M + nc * (8.0 / 3.0 + 1.0) + loh) * N ** 3
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        if not self.rows:
+            return None
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4)
+                          if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("gemm_f64.cu", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_2003_05286_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(workload: str):
+    """DRAM bytes per launch of the slice-chain GEMM from the committed ncu summary,
+    or None when the kernel source changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "chain_gemm_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    e = d.get(workload)
+    if not e or e.get("kernel_source_sha256_16") != kernel_source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+# ---------------------------------------------------------------------------
+def cpu_oracle_rate(insts, seconds: float):
+    """Oracle G/s on the host cores: instances one after another until `seconds` pass."""
+    from oracle import dqmc as od
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        x = insts[n % len(insts)]
+        od.greens(x.K, x.dtau, x.V, x.k)
+        n += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    return n / dt, n, dt
+
+
+def run_reference(args, wl, rank, world):
+    if rank != 0:
+        return
+    batch = args.batch or wl["batch"]
+    K, V, insts = make_inputs(wl, 0, min(batch, 8))
+    from oracle import dqmc as od
+    for i in range(args.warmup):
+        x = insts[i % len(insts)]
+        od.greens(x.K, x.dtau, x.V, x.k)
+    times = []
+    for s in range(args.steps):
+        x = insts[s % len(insts)]
+        t0 = time.perf_counter()
+        od.greens(x.K, x.dtau, x.V, x.k)
+        times.append(time.perf_counter() - t0)
+    per = sum(times) / len(times)
+    value = 1.0 / per
+    cores = os.cpu_count()
+    N = wl["L"] ** 2
+    M = int(round(wl["beta"] / wl["dtau"]))
+    line = {
+        "metric": "greens_functions_per_second", "value": value, "unit": "G/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "N": N, "M": M, "k": wl["k"], "beta": wl["beta"],
+                   "U": wl["U"], "instances_per_step": 1, "l2": "n/a (CPU)"},
+        "impl": "reference",
+        "cpu_baseline": {"value": value, "unit": "G/s", "cores": cores, "kind": "oracle",
+                         "sample": f"1 instance of the {args.workload} workload per step "
+                                   f"(NumPy/SciPy FP64, BLAS threads = all {cores} cores)"},
+        "e2e": {"value": value, "unit": "G/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args, wl, rank, world):
+    import torch
+    import paper_2003_05286_gb300 as dq
+
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    batch = args.batch or wl["batch"]
+    N = wl["L"] ** 2
+    M = int(round(wl["beta"] / wl["dtau"]))
+    k = wl["k"]
+    K_np, V_np, insts = make_inputs(wl, rank, batch)
+    K = torch.tensor(K_np, device=dev)
+    V = torch.tensor(V_np, device=dev)
+    h = dq.Handle()
+    h.bind_stream()
+
+    def step():
+        return dq.greens(K, wl["dtau"], V, k, handle=h)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    launches_per_step = h.last_launch_count
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clocks = ClockSampler(dev.index)
+    h.profile(True)
+    h.profile_reset()
+    if dist:
+        tdist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_wall0 = time.perf_counter()
+    for s in range(args.steps):
+        flush.fill_(float(s))                 # evict L2 between timed steps (not timed)
+        ev[s][0].record()
+        G, ld, sg, st = step()
+        ev[s][1].record()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall0
+    if dist:
+        tdist.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    tot_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([tot_ms], device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    chain_ms, chain_n, chain_flops = h.profile_read(h.PROF_CHAIN)
+    h.profile(False)
+    bad = int((st != 0).sum().item())
+
+    value = batch * world * args.steps / (tot_ms / 1e3)
+    fl = flops_per_greens(N, M, k)
+
+    # ---- end to end through the C ABI with host buffers ----------------------
+    e2e = None
+    if not args.no_e2e:
+        import ctypes as C
+        he = dq.Handle()
+        he.bind_stream()
+        he.set_pointer_mode(True)
+        Kh = torch.tensor(K_np).pin_memory()
+        Vh = torch.tensor(V_np).pin_memory()
+        Gh = torch.empty((batch, N, N), dtype=torch.float64).pin_memory()
+        ldh = torch.empty(batch, dtype=torch.float64).pin_memory()
+        sgh = torch.empty(batch, dtype=torch.int32).pin_memory()
+        sth = torch.empty(batch, dtype=torch.int32).pin_memory()
+        p = lambda t: C.c_void_p(t.data_ptr())  # noqa: E731
+
+        def e2e_step():
+            rc = he._lib.dqmc_greens(he.h, batch, N, M, p(Kh), wl["dtau"], p(Vh), k, p(Gh), p(ldh),
+                                     p(sgh), p(sth))
+            if rc != 0:
+                raise RuntimeError(f"dqmc_greens (host mode) rc={rc}")
+
+        e2e_step()
+        if dist:
+            tdist.barrier()
+        ts = []
+        for s in range(max(1, min(args.steps, 3))):
+            flush.fill_(float(s))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            e2e_step()                      # returns after the outputs are in host memory
+            ts.append(time.perf_counter() - t0)
+        e2e_s = sum(ts) / len(ts)
+        if dist:
+            t = torch.tensor([e2e_s], device=dev)
+            tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": batch * world / e2e_s, "unit": "G/s",
+               "h2d_bytes_per_step": int(Kh.numel() * 8 + Vh.numel() * 8),
+               "d2h_bytes_per_step": int(Gh.numel() * 8 + batch * (8 + 4 + 4)),
+               "api": "dqmc_greens, DQMC_PTR_HOST (pinned host buffers)"}
+        he.close()
+
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        rate, n, dt = cpu_oracle_rate(insts[:4], args.cpu_seconds)
+        cpu = {"value": rate, "unit": "G/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{n} instance(s) of the {args.workload} workload run one after "
+                         f"another in {dt:.1f} s (NumPy/SciPy FP64, BLAS threads = all cores)"}
+    achieved = (chain_flops / (chain_ms / 1e3)) / 1e12 if chain_ms > 0 else None
+    traffic = measured_traffic(args.workload)
+    line = {
+        "metric": "greens_functions_per_second", "value": value, "unit": "G/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "N": N, "M": M, "k": k, "beta": wl["beta"],
+                   "U": wl["U"], "dtau": wl["dtau"], "instances_per_gpu": batch,
+                   "chain_precision": "fp64",
+                   "l2": "flushed between timed steps (256 MB write)"},
+        "fp64_tflops": fl * batch * world * args.steps / (tot_ms / 1e3) / 1e12,
+        "fp64_frac_of_peak": fl * batch * args.steps / (tot_ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
+                     "traffic": traffic,
+                     "kernel": "gemm_f64_kernel (slice-chain product, 2N^3 x batch flops per launch)",
+                     "launches": chain_n, "avg_launch_ms": chain_ms / max(chain_n, 1),
+                     "share_of_step": chain_ms / tot_ms if tot_ms > 0 else None,
+                     "peak_source": "derived: 152 SM x 4 FP64 flop/clk x 2070 MHz"},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "status_nonzero": bad,
+        "wall_s": wall,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    wl = WORKLOADS[args.workload]
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.impl == "reference":
+        run_reference(args, wl, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        tdist.init_process_group("nccl")
+    try:
+        run_gpu(args, wl, rank, world)
+    finally:
+        if world > 1:
+            import torch.distributed as tdist
+            tdist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,163 @@
+/*
+ * dqmc.h -- C ABI of the GB300 library for stabilised DQMC Green's functions.
+ *
+ * What the library computes (C. Bauer, "Fast and stable determinant quantum
+ * Monte Carlo", SciPost 2020):
+ *
+ *   slice matrices      B_l = exp(-dtau K) exp(V_l),  l = 1..M           (Sec. 2, Eq. (Ztr))
+ *   equal-time G        G = [1 + B_M ... B_1]^{-1}                        (Sec. 2, Eq. (etgf))
+ *   weight              log|det(1 + B_M ... B_1)| = -log|det G|, sign    (Sec. 2, Eqs. (DQMC), (metropolis))
+ *   time-displaced G    G(tau_1, 0) = B_{l_1} ... B_1 G                   (Sec. 6, Eq. (tdgf_propagate))
+ *   gradient            d log|det(1 + B_M...B_1)| / dV_l(i) = 1 - G_l(i,i), with
+ *                       G_l = [1 + B_{l-1}...B_1 B_M...B_l]^{-1}          (Sec. 6, Eq. (etgf_tau))
+ *
+ * computed the stable way the paper prescribes: naive products of k slices,
+ * re-factorised after every chunk by a column-pivoted Householder QR into a
+ * U D T stack (Sec. 4, Eq. (stabmult)), and inverted with Loh's D+/D- split
+ * (Sec. 5, Eq. (inversion_loh); Sec. 6, Eq. (inversion_tdgf_loh)).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - All floating point data are IEEE binary64 (double), row-major:
+ *   element (i, j) of an N x N matrix is at [i*N + j].
+ * - K: N x N real symmetric hopping matrix, shared by all instances of a call.
+ * - V: batch x M x N; V[(b*M + (l-1))*N + i] is the diagonal entry i of V_l of
+ *   instance b (slice l contiguous).  B_l = exp(-dtau K) diag(exp(V_l)).
+ * - k: stabilisation interval, 1 <= k <= M.  Chunks are slices
+ *   [c*k+1, min((c+1)*k, M)], so the last chunk may be shorter.
+ * - The k-grid is tau_j = min(j*k, M) * dtau, j = 0 .. n_tau-1, with
+ *   n_tau = ceil(M/k) + 1.
+ * - Pointer mode (dqmc_set_pointer_mode): DQMC_PTR_DEVICE (default) -- every
+ *   array argument is a device pointer owned by the caller and the call is
+ *   asynchronous on the handle's stream; DQMC_PTR_HOST -- every array
+ *   argument is a host pointer, the library copies inputs in and outputs out
+ *   through its own device workspace and the call returns after the results
+ *   are in host memory.
+ * - Errors: the return value reports what is known synchronously (arguments,
+ *   allocation, launch).  Numerical trouble found on the device is written to
+ *   the optional per-instance status array (bit mask of dqmc_status_bits);
+ *   0 means the instance is fine.  No entry point aborts, traps or throws.
+ * - Thread safety: a handle must not be used by two host threads at once.
+ *   Different handles are independent.
+ */
+#ifndef DQMC_H
+#define DQMC_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DQMC_OK = 0,
+  DQMC_ERR_ARG = 1,        /* invalid argument (size, pointer, alignment, mode) */
+  DQMC_ERR_CUDA = 2,       /* a CUDA runtime call or kernel launch failed */
+  DQMC_ERR_NOMEM = 3,      /* device workspace could not be allocated */
+  DQMC_ERR_NONFINITE = 4,  /* (status bit) NaN/Inf in an input or a result */
+  DQMC_ERR_SINGULAR = 5,   /* (status bit) exactly singular pivot */
+  DQMC_ERR_TIMEOUT = 6,    /* a bounded device-side wait gave up */
+  DQMC_ERR_UNSUPPORTED = 7 /* configuration not built into this library */
+} dqmc_status;
+
+/* Bits of the per-instance device status word. */
+enum dqmc_status_bits {
+  DQMC_STATUS_NONFINITE_INPUT = 1 << 0,  /* V contained NaN/Inf */
+  DQMC_STATUS_NONFINITE_SCALE = 1 << 1,  /* a D scale overflowed or became NaN */
+  DQMC_STATUS_SINGULAR = 1 << 2,         /* an LU pivot or QR diagonal was exactly 0 */
+  DQMC_STATUS_NONFINITE_OUTPUT = 1 << 3, /* G or log det is not finite */
+  DQMC_STATUS_BAD_K = 1 << 4             /* K not symmetric/finite, or ||dtau K||_1 > 2048 */
+};
+
+typedef enum {
+  DQMC_CHAIN_FP64 = 0,  /* k-slice chain products in FP64 (default) */
+  DQMC_CHAIN_BF16X3 = 2 /* chain products on tensor cores from BF16 splits (mixed) */
+} dqmc_chain_prec;
+
+typedef enum { DQMC_PTR_DEVICE = 0, DQMC_PTR_HOST = 1 } dqmc_pointer_mode;
+
+typedef struct dqmc_handle_s* dqmc_handle;
+
+/* Creates a handle bound to the current CUDA device and to the legacy default
+ * stream.  The handle owns a grow-only device workspace (allocated on first
+ * use, freed by dqmc_destroy).  *h is set to NULL on failure. */
+dqmc_status dqmc_create(dqmc_handle* h);
+dqmc_status dqmc_destroy(dqmc_handle h);
+/* stream: a cudaStream_t (NULL = legacy default stream). */
+dqmc_status dqmc_set_stream(dqmc_handle h, void* stream);
+dqmc_status dqmc_set_pointer_mode(dqmc_handle h, dqmc_pointer_mode mode);
+dqmc_status dqmc_set_chain_precision(dqmc_handle h, dqmc_chain_prec prec);
+/* Number of kernel launches issued by the most recent compute call. */
+long long dqmc_last_launch_count(dqmc_handle h);
+/* Bytes of device workspace the handle currently holds. */
+long long dqmc_workspace_bytes(dqmc_handle h);
+const char* dqmc_status_string(dqmc_status s);
+
+/* Per-kernel-class timing of subsequent compute calls: every launch of the
+ * class is bracketed by CUDA events recorded on the handle's stream.  Classes:
+ * 0 slice-chain GEMM (Eq. (Ztr)), 1 pivoted QR (Sec. 4.2.2), 2 X <- T X update
+ * (Eq. (stabmult)), 3 LU solves of the inversions, 4 everything else.
+ * dqmc_profile_read synchronises the stream and returns the summed event
+ * time (ms), the launch count and the algorithmic FP64 flops of the class
+ * since the last reset (any output pointer may be NULL). */
+dqmc_status dqmc_profile_enable(dqmc_handle h, int enable);
+dqmc_status dqmc_profile_reset(dqmc_handle h);
+dqmc_status dqmc_profile_read(dqmc_handle h, int cls, double* ms, long long* launches,
+                              double* flops);
+
+/* Equal-time Green's function G = [1 + B_M ... B_1]^{-1} (Eq. (etgf)) of each
+ * of `batch` instances, with log|det(1 + B_M...B_1)| and its sign.
+ *   K      [N*N]            input
+ *   V      [batch*M*N]      input
+ *   G      [batch*N*N]      output (may be NULL: then only logdet/sign)
+ *   logdet [batch]          output, may be NULL
+ *   sign   [batch] int32    output (+1/-1), may be NULL
+ *   status [batch] int32    output bit mask, may be NULL
+ * 1 <= N <= 1024, 1 <= M, 1 <= k <= M, batch >= 0 (0 is a no-op). */
+dqmc_status dqmc_greens(dqmc_handle h, int batch, int N, int M, const double* K,
+                        double dtau, const double* V, int k, double* G,
+                        double* logdet, int* sign, int* status);
+
+/* log|det(1 + B_M...B_1)| and sign only (Eq. (DQMC)); same arguments. */
+dqmc_status dqmc_logdet(dqmc_handle h, int batch, int N, int M, const double* K,
+                        double dtau, const double* V, int k, double* logdet,
+                        int* sign, int* status);
+
+/* Time-displaced Green's functions on the k-grid (Sec. 6):
+ *   Gtt [batch*n_tau*N*N]  G(tau_j, tau_j) = G_{l_j + 1}   (Eq. (etgf_tau)), may be NULL
+ *   Gt0 [batch*n_tau*N*N]  G(tau_j, 0) = B_{l_j}...B_1 G_1 (Eq. (tdgf_propagate)), may be NULL
+ * with l_j = min(j*k, M); entry (b, j, i, m) at ((b*n_tau + j)*N + i)*N + m.
+ * Both come from the forward stack B(tau_j, 0) = U D X and the backward stack
+ * B(beta, tau_j)^T = U D T (App. A) through one D+/D- split inversion per
+ * tau_j (Eq. (inversion_tdgf_loh)). */
+dqmc_status dqmc_greens_tdisplaced(dqmc_handle h, int batch, int N, int M,
+                                   const double* K, double dtau, const double* V,
+                                   int k, double* Gtt, double* Gt0, int* status);
+
+/* Gradient dV[(b*M + (l-1))*N + i] = d log|det(1 + B_M...B_1)| / dV_l(i)
+ * = 1 - G_l(i,i) for every slice l (derived from Eqs. (etgf), (etgf_tau)):
+ * G_l at the k-grid from the two stacks, then G_{l+1} = B_l G_l B_l^{-1}
+ * between grid points.  logdet/sign/status as in dqmc_greens (may be NULL). */
+dqmc_status dqmc_logdet_grad(dqmc_handle h, int batch, int N, int M,
+                             const double* K, double dtau, const double* V,
+                             int k, double* logdet, int* sign, double* dV,
+                             int* status);
+
+/* Ragged batch: instances of different N, M, k, dtau and K in one call.
+ * desc is a HOST array of `batch` descriptors; offsets are in doubles into
+ * the pools (K_pool holds each instance's N*N hopping matrix at off_K,
+ * V_pool its M*N field at off_V, G_pool its N*N output at off_G).
+ * logdet/sign/status are indexed by instance and may be NULL. */
+typedef struct {
+  int N, M, k, pad;
+  double dtau;
+  long long off_K, off_V, off_G;
+} dqmc_instance;
+
+dqmc_status dqmc_greens_ragged(dqmc_handle h, int batch, const dqmc_instance* desc,
+                               const double* K_pool, const double* V_pool,
+                               double* G_pool, double* logdet, int* sign,
+                               int* status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DQMC_H */

@@ -1,0 +1,240 @@
+"""GB300 library for stabilised DQMC Green's functions (Bauer, SciPost 2020).
+
+A thin PyTorch binding over the C ABI of ``include/dqmc.h``: torch supplies
+device memory and the current CUDA stream; every step of the computation runs
+in the library's CUDA kernels.  There is no CPU fallback: if the shared
+library is missing or no GPU is present the calls raise.
+
+Shapes (row-major, float64):
+    K  (N, N)         symmetric hopping matrix, B_l = exp(-dtau K) exp(V_l)
+    V  (B, M, N)      V[b, l-1] = diagonal of V_l  (a 2-D (M, N) V means B = 1)
+    G  (B, N, N)      G[b, i, j] = G_ij
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import torch
+
+from . import _abi
+
+__all__ = ["Handle", "greens", "logdet", "greens_tdisplaced", "logdet_grad", "greens_ragged",
+           "LogDet", "n_tau", "lib"]
+
+
+def lib():
+    return _abi.load()
+
+
+def n_tau(M: int, k: int) -> int:
+    """Number of points tau_j = min(j k, M) dtau of the k-grid."""
+    return -(-M // k) + 1
+
+
+class Handle:
+    """Owns a dqmc_handle (workspace + settings) bound to the current device."""
+
+    def __init__(self, chain_precision: int = _abi.CHAIN_FP64):
+        self._lib = lib()
+        h = C.c_void_p()
+        _abi.check(self._lib.dqmc_create(C.byref(h)), "dqmc_create")
+        self.h = h
+        if chain_precision != _abi.CHAIN_FP64:
+            _abi.check(self._lib.dqmc_set_chain_precision(self.h, chain_precision),
+                       "dqmc_set_chain_precision")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.dqmc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def bind_stream(self, stream: torch.cuda.Stream | None = None):
+        s = stream if stream is not None else torch.cuda.current_stream()
+        _abi.check(self._lib.dqmc_set_stream(self.h, C.c_void_p(s.cuda_stream)), "dqmc_set_stream")
+
+    def set_pointer_mode(self, host: bool):
+        _abi.check(self._lib.dqmc_set_pointer_mode(self.h, _abi.PTR_HOST if host else _abi.PTR_DEVICE),
+                   "dqmc_set_pointer_mode")
+
+    # kernel classes of the event profiler
+    PROF_CHAIN, PROF_QRP, PROF_XUPD, PROF_LU, PROF_OTHER = range(5)
+
+    def profile(self, enable: bool = True):
+        _abi.check(self._lib.dqmc_profile_enable(self.h, int(enable)), "dqmc_profile_enable")
+
+    def profile_reset(self):
+        _abi.check(self._lib.dqmc_profile_reset(self.h), "dqmc_profile_reset")
+
+    def profile_read(self, cls: int):
+        """(event ms, launches, algorithmic FP64 flops) of one kernel class since the reset."""
+        ms = C.c_double()
+        n = C.c_longlong()
+        fl = C.c_double()
+        _abi.check(self._lib.dqmc_profile_read(self.h, cls, C.byref(ms), C.byref(n), C.byref(fl)),
+                   "dqmc_profile_read")
+        return ms.value, n.value, fl.value
+
+    @property
+    def last_launch_count(self) -> int:
+        return int(self._lib.dqmc_last_launch_count(self.h))
+
+    @property
+    def workspace_bytes(self) -> int:
+        return int(self._lib.dqmc_workspace_bytes(self.h))
+
+
+_default: dict[int, Handle] = {}
+
+
+def _handle(h: Handle | None) -> Handle:
+    if h is not None:
+        h.bind_stream()
+        return h
+    dev = torch.cuda.current_device()
+    if dev not in _default:
+        _default[dev] = Handle()
+    _default[dev].bind_stream()
+    return _default[dev]
+
+
+def _ptr(t: torch.Tensor | None):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _prep(K: torch.Tensor, V: torch.Tensor):
+    if not (K.is_cuda and V.is_cuda):
+        raise ValueError("K and V must be CUDA tensors (the library has no CPU path)")
+    if K.dtype != torch.float64 or V.dtype != torch.float64:
+        raise ValueError("K and V must be float64")
+    K = K.contiguous()
+    squeeze = V.dim() == 2
+    V = (V.unsqueeze(0) if squeeze else V).contiguous()
+    if V.dim() != 3 or K.dim() != 2 or K.shape[0] != K.shape[1] or V.shape[2] != K.shape[0]:
+        raise ValueError(f"bad shapes K {tuple(K.shape)} V {tuple(V.shape)}")
+    return K, V, squeeze
+
+
+def greens(K, dtau: float, V, k: int, *, handle: Handle | None = None, want_G: bool = True):
+    """Equal-time G = [1 + B_M...B_1]^{-1}, log|det(1 + B_M...B_1)|, sign, status."""
+    K, V, sq = _prep(K, V)
+    B, M, N = V.shape
+    h = _handle(handle)
+    G = torch.empty((B, N, N), dtype=torch.float64, device=V.device) if want_G else None
+    ld = torch.empty(B, dtype=torch.float64, device=V.device)
+    sg = torch.empty(B, dtype=torch.int32, device=V.device)
+    st = torch.empty(B, dtype=torch.int32, device=V.device)
+    rc = h._lib.dqmc_greens(h.h, B, N, M, _ptr(K), float(dtau), _ptr(V), int(k), _ptr(G),
+                            _ptr(ld), _ptr(sg), _ptr(st))
+    _abi.check(rc, "dqmc_greens")
+    if sq:
+        return (G[0] if G is not None else None), ld[0], sg[0], st[0]
+    return G, ld, sg, st
+
+
+def logdet(K, dtau: float, V, k: int, *, handle: Handle | None = None):
+    """log|det(1 + B_M...B_1)|, sign, status."""
+    K, V, sq = _prep(K, V)
+    B, M, N = V.shape
+    h = _handle(handle)
+    ld = torch.empty(B, dtype=torch.float64, device=V.device)
+    sg = torch.empty(B, dtype=torch.int32, device=V.device)
+    st = torch.empty(B, dtype=torch.int32, device=V.device)
+    _abi.check(h._lib.dqmc_logdet(h.h, B, N, M, _ptr(K), float(dtau), _ptr(V), int(k), _ptr(ld),
+                                  _ptr(sg), _ptr(st)), "dqmc_logdet")
+    if sq:
+        return ld[0], sg[0], st[0]
+    return ld, sg, st
+
+
+def greens_tdisplaced(K, dtau: float, V, k: int, *, handle: Handle | None = None,
+                      want_tt: bool = True, want_t0: bool = True):
+    """G(tau_j, tau_j) and G(tau_j, 0) on the k-grid: tensors (B, n_tau, N, N) and status."""
+    K, V, sq = _prep(K, V)
+    B, M, N = V.shape
+    nt = n_tau(M, k)
+    h = _handle(handle)
+    Gtt = torch.empty((B, nt, N, N), dtype=torch.float64, device=V.device) if want_tt else None
+    Gt0 = torch.empty((B, nt, N, N), dtype=torch.float64, device=V.device) if want_t0 else None
+    st = torch.empty(B, dtype=torch.int32, device=V.device)
+    _abi.check(h._lib.dqmc_greens_tdisplaced(h.h, B, N, M, _ptr(K), float(dtau), _ptr(V), int(k),
+                                             _ptr(Gtt), _ptr(Gt0), _ptr(st)),
+               "dqmc_greens_tdisplaced")
+    if sq:
+        return (Gtt[0] if Gtt is not None else None), (Gt0[0] if Gt0 is not None else None), st[0]
+    return Gtt, Gt0, st
+
+
+def logdet_grad(K, dtau: float, V, k: int, *, handle: Handle | None = None):
+    """log|det(1 + B_M...B_1)|, sign, dV = d logdet / dV (same shape as V), status."""
+    K, V, sq = _prep(K, V)
+    B, M, N = V.shape
+    h = _handle(handle)
+    ld = torch.empty(B, dtype=torch.float64, device=V.device)
+    sg = torch.empty(B, dtype=torch.int32, device=V.device)
+    dV = torch.empty((B, M, N), dtype=torch.float64, device=V.device)
+    st = torch.empty(B, dtype=torch.int32, device=V.device)
+    _abi.check(h._lib.dqmc_logdet_grad(h.h, B, N, M, _ptr(K), float(dtau), _ptr(V), int(k),
+                                       _ptr(ld), _ptr(sg), _ptr(dV), _ptr(st)), "dqmc_logdet_grad")
+    if sq:
+        return ld[0], sg[0], dV[0], st[0]
+    return ld, sg, dV, st
+
+
+def greens_ragged(instances, *, handle: Handle | None = None, device=None):
+    """Ragged batch.  ``instances``: list of (K, dtau, V, k) with CUDA float64 K (N,N), V (M,N).
+
+    Packs the pools on the device and returns (list of G, logdet, sign, status)."""
+    device = device or instances[0][0].device
+    descs = (_abi.DqmcInstance * len(instances))()
+    offK = offV = offG = 0
+    Ks, Vs = [], []
+    for i, (K, dtau, V, k) in enumerate(instances):
+        N = K.shape[0]
+        M = V.shape[0]
+        descs[i] = _abi.DqmcInstance(N, M, int(k), 0, float(dtau), offK, offV, offG)
+        Ks.append(K.reshape(-1))
+        Vs.append(V.reshape(-1))
+        offK += N * N
+        offV += M * N
+        offG += N * N
+    Kp = torch.cat(Ks).to(device=device, dtype=torch.float64).contiguous()
+    Vp = torch.cat(Vs).to(device=device, dtype=torch.float64).contiguous()
+    Gp = torch.empty(offG, dtype=torch.float64, device=device)
+    B = len(instances)
+    ld = torch.empty(B, dtype=torch.float64, device=device)
+    sg = torch.empty(B, dtype=torch.int32, device=device)
+    st = torch.empty(B, dtype=torch.int32, device=device)
+    h = _handle(handle)
+    _abi.check(h._lib.dqmc_greens_ragged(h.h, B, descs, _ptr(Kp), _ptr(Vp), _ptr(Gp), _ptr(ld),
+                                         _ptr(sg), _ptr(st)), "dqmc_greens_ragged")
+    Gs = []
+    for i in range(B):
+        N = descs[i].N
+        Gs.append(Gp[descs[i].off_G: descs[i].off_G + N * N].view(N, N))
+    return Gs, ld, sg, st
+
+
+class LogDet(torch.autograd.Function):
+    """log|det(1 + B_M...B_1)| as a differentiable function of V (B, M, N).
+
+    backward uses the library's adjoint kernel: d logdet / dV_l(i) = 1 - G_l(i,i)."""
+
+    @staticmethod
+    def forward(ctx, V, K, dtau, k, handle=None):
+        ld, sg, dV, st = logdet_grad(K, dtau, V, k, handle=handle)
+        ctx.save_for_backward(dV)
+        ctx.squeeze = V.dim() == 2
+        return ld
+
+    @staticmethod
+    def backward(ctx, gout):
+        (dV,) = ctx.saved_tensors
+        if ctx.squeeze:
+            return gout * dV, None, None, None, None
+        return gout[:, None, None] * dV, None, None, None, None

@@ -1,0 +1,80 @@
+"""ctypes declarations of the C ABI in include/dqmc.h (argument marshalling only)."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from . import build as _build
+
+DQMC_OK = 0
+STATUS_STRINGS = {
+    0: "ok", 1: "invalid argument", 2: "CUDA runtime or launch failure",
+    3: "device workspace allocation failed", 4: "non-finite value", 5: "singular pivot",
+    6: "bounded device wait gave up", 7: "unsupported configuration",
+}
+STATUS_BITS = {
+    "NONFINITE_INPUT": 1 << 0, "NONFINITE_SCALE": 1 << 1, "SINGULAR": 1 << 2,
+    "NONFINITE_OUTPUT": 1 << 3, "BAD_K": 1 << 4,
+}
+CHAIN_FP64 = 0
+CHAIN_BF16X3 = 2
+PTR_DEVICE = 0
+PTR_HOST = 1
+
+
+class DqmcInstance(C.Structure):
+    _fields_ = [("N", C.c_int), ("M", C.c_int), ("k", C.c_int), ("pad", C.c_int),
+                ("dtau", C.c_double), ("off_K", C.c_longlong), ("off_V", C.c_longlong),
+                ("off_G", C.c_longlong)]
+
+
+_P = C.c_void_p
+_I = C.c_int
+_D = C.c_double
+
+# name -> (restype, argtypes)
+SIGNATURES = {
+    "dqmc_create": (_I, [C.POINTER(_P)]),
+    "dqmc_destroy": (_I, [_P]),
+    "dqmc_set_stream": (_I, [_P, _P]),
+    "dqmc_set_pointer_mode": (_I, [_P, _I]),
+    "dqmc_set_chain_precision": (_I, [_P, _I]),
+    "dqmc_last_launch_count": (C.c_longlong, [_P]),
+    "dqmc_workspace_bytes": (C.c_longlong, [_P]),
+    "dqmc_status_string": (C.c_char_p, [_I]),
+    "dqmc_profile_enable": (_I, [_P, _I]),
+    "dqmc_profile_reset": (_I, [_P]),
+    "dqmc_profile_read": (_I, [_P, _I, C.POINTER(C.c_double), C.POINTER(C.c_longlong),
+                               C.POINTER(C.c_double)]),
+    "dqmc_greens": (_I, [_P, _I, _I, _I, _P, _D, _P, _I, _P, _P, _P, _P]),
+    "dqmc_logdet": (_I, [_P, _I, _I, _I, _P, _D, _P, _I, _P, _P, _P]),
+    "dqmc_greens_tdisplaced": (_I, [_P, _I, _I, _I, _P, _D, _P, _I, _P, _P, _P]),
+    "dqmc_logdet_grad": (_I, [_P, _I, _I, _I, _P, _D, _P, _I, _P, _P, _P, _P]),
+    "dqmc_greens_ragged": (_I, [_P, _I, C.POINTER(DqmcInstance), _P, _P, _P, _P, _P, _P]),
+}
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Loads the in-tree shared library; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError(
+            f"CUDA library not built ({path} missing): run "
+            "`python -c 'import __graft_entry__ as g; g.build()'` first")
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def check(rc: int, what: str) -> None:
+    if rc != DQMC_OK:
+        raise RuntimeError(f"{what} failed: {STATUS_STRINGS.get(rc, rc)} (code {rc})")

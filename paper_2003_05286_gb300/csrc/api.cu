@@ -1,0 +1,618 @@
+// C ABI of the library: handle, workspace, and the launch sequences of the
+// stabilised DQMC path.  Every arithmetic step runs in the kernels of this
+// library; this file only sizes buffers and orders launches on the handle's
+// stream.
+//
+//   a0  E = exp(-dtau K) (and exp(+dtau K) for the gradient): Taylor series of
+//       degree 16 in Horner form on dtau K / 2^s, then s squarings (s from the
+//       1-norm, decided on the device so the sequence is graph-capturable).
+//   a1  chunk of k slices: A <- E diag(exp V_l) A, one batched GEMM per slice
+//       (Sec. 2, Eq. (Ztr); mixture of naive and stabilised products, Sec. 4.1).
+//   a2-a4  Eq. (stabmult): (A U) D -> pivoted QR -> U' D' T', X <- T' X.
+//   a6-a7  Eq. (inversion_loh) + log det.
+//   a8  backward stack on the transposed chain (App. A).
+//   a9-a10  G(tau,tau) and G(tau,0) from the two stacks through one D+/D- split
+//       middle matrix (Eq. (inversion_tdgf_loh)).
+//   a11 gradient 1 - G_l(i,i): checkpoints from the stacks, wrapping in between.
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+
+using namespace dqmc;
+
+// Kernel classes of the per-class event profiler (dqmc_profile_*).
+enum { PC_CHAIN = 0, PC_QRP = 1, PC_XUPD = 2, PC_LU = 3, PC_OTHER = 4, PC_N = 5 };
+
+struct ProfRec {
+  cudaEvent_t e0, e1;
+  int cls;
+  double flops;
+};
+
+struct dqmc_handle_s {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  dqmc_pointer_mode pmode = DQMC_PTR_DEVICE;
+  dqmc_chain_prec prec = DQMC_CHAIN_FP64;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  long long launches = 0;
+  // profiler
+  bool prof = false;
+  std::vector<ProfRec> pending;
+  std::vector<cudaEvent_t> pool;
+  double prof_ms[PC_N] = {0}, prof_flops[PC_N] = {0};
+  long long prof_count[PC_N] = {0};
+};
+
+namespace {
+
+constexpr int EXPM_TERMS = 16;    // Taylor degree; remainder < 0.5^17/17! ~ 2e-20 for ||.||_1 <= 1/2
+constexpr int EXPM_SQUARINGS = 12;
+
+// Carves aligned sub-buffers out of the workspace.  With base == nullptr it
+// only measures.
+struct Arena {
+  char* base = nullptr;
+  size_t off = 0;
+  template <class T>
+  T* take(long long n) {
+    size_t bytes = ((size_t)(n > 0 ? n : 1) * sizeof(T) + 255) & ~(size_t)255;
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += bytes;
+    return p;
+  }
+};
+
+dqmc_status ensure_ws(dqmc_handle h, size_t bytes) {
+  if (bytes <= h->ws_bytes) return DQMC_OK;
+  if (h->ws) {
+    cudaStreamSynchronize(h->stream);
+    cudaFree(h->ws);
+    h->ws = nullptr;
+    h->ws_bytes = 0;
+  }
+  size_t want = bytes + bytes / 8;
+  if (cudaMalloc(&h->ws, want) != cudaSuccess) {
+    cudaGetLastError();
+    if (cudaMalloc(&h->ws, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      h->ws = nullptr;
+      return DQMC_ERR_NOMEM;
+    }
+    want = bytes;
+  }
+  h->ws_bytes = want;
+  return DQMC_OK;
+}
+
+cudaEvent_t pool_event(dqmc_handle h) {
+  if (!h->pool.empty()) {
+    cudaEvent_t e = h->pool.back();
+    h->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Folds finished event pairs into the per-class totals (synchronises the stream).
+void prof_collect(dqmc_handle h) {
+  if (h->pending.empty()) return;
+  cudaStreamSynchronize(h->stream);
+  for (auto& r : h->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.e0, r.e1) == cudaSuccess) {
+      h->prof_ms[r.cls] += ms;
+      h->prof_count[r.cls] += 1;
+      h->prof_flops[r.cls] += r.flops;
+    }
+    h->pool.push_back(r.e0);
+    h->pool.push_back(r.e1);
+  }
+  cudaGetLastError();
+  h->pending.clear();
+}
+
+// Launch wrapper: counts the launch, and brackets it with events when the
+// profiler is on.  cls/flops classify it (flops = algorithmic FP64 flops).
+#define CKP(cls_, flops_, expr)                                   \
+  do {                                                            \
+    ProfRec _r{nullptr, nullptr, (cls_), (double)(flops_)};       \
+    if (h->prof) {                                                \
+      _r.e0 = pool_event(h);                                      \
+      _r.e1 = pool_event(h);                                      \
+      cudaEventRecord(_r.e0, h->stream);                          \
+    }                                                             \
+    cudaError_t _e = (expr);                                      \
+    h->launches++;                                                \
+    if (h->prof) {                                                \
+      cudaEventRecord(_r.e1, h->stream);                          \
+      h->pending.push_back(_r);                                   \
+      if (h->pending.size() > 4096) prof_collect(h);              \
+    }                                                             \
+    if (_e != cudaSuccess) return DQMC_ERR_CUDA;                  \
+  } while (0)
+#define CK(expr) CKP(PC_OTHER, 0.0, expr)
+#define CKS(expr)                                  \
+  do {                                             \
+    dqmc_status _s = (expr);                       \
+    if (_s != DQMC_OK) return _s;                  \
+  } while (0)
+
+inline int n_chunks(int M, int k) { return (M + k - 1) / k; }
+// LU factorisation (2/3 N^3) + forward and backward substitution (2 N^2 per column)
+inline double lu_flops(int N, int nrhs) { return 2.0 / 3.0 * N * (double)N * N + 2.0 * N * (double)N * nrhs; }
+
+// ---------------------------------------------------------------------------
+// a0: E = exp(sgn * dtau * K)
+// ---------------------------------------------------------------------------
+struct ExpmWs {
+  double *t0, *t1, *scale;
+  int *s, *asym;
+};
+
+void take_expm(Arena& ar, int N, ExpmWs& w) {
+  w.t0 = ar.take<double>((long long)N * N);
+  w.t1 = ar.take<double>((long long)N * N);
+  w.scale = ar.take<double>(1);
+  w.s = ar.take<int>(1);
+  w.asym = ar.take<int>(1);
+}
+
+// Result ends in w.t0 (the step counts are even).
+dqmc_status run_expm(dqmc_handle h, const double* K, int N, double dtau, double sgn,
+                     const ExpmWs& w, int* status, int batch) {
+  cudaStream_t st = h->stream;
+  CK(expm_prepare(K, N, dtau, sgn, w.s, w.scale, w.asym, st));
+  CK(set_identity(w.t0, 0, N, 1, st));
+  double* cur = w.t0;
+  double* nxt = w.t1;
+  for (int m = EXPM_TERMS; m >= 1; --m) {
+    GemmArgs g;
+    g.M = g.N = g.K = N;
+    g.batch = 1;
+    g.A = K; g.lda = N;
+    g.B = cur; g.ldb = N;
+    g.C = nxt; g.ldc = N;
+    g.alpha = 1.0 / m;
+    g.alpha_ptr = w.scale;
+    g.addIdentity = 1;
+    CK(gemm_f64(g, st));
+    double* t = cur; cur = nxt; nxt = t;
+  }
+  for (int s = 0; s < EXPM_SQUARINGS; ++s) {
+    GemmArgs g;
+    g.M = g.N = g.K = N;
+    g.batch = 1;
+    g.A = cur; g.lda = N;
+    g.B = cur; g.ldb = N;
+    g.C = nxt; g.ldc = N;
+    g.skip_if = w.s;
+    g.skip_at = s;
+    CK(gemm_f64(g, st));
+    double* t = cur; cur = nxt; nxt = t;
+  }
+  if (status) CK(or_status(status, batch, w.asym, DQMC_STATUS_BAD_K, st));
+  return DQMC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// a1-a5: one direction of the stabilised chain.
+//
+// dir = +1: forward, B(tau_c, 0) grows by B_l = E diag(e^{V_l}) on the left;
+//           chunk c moves slot c -> c+1.
+// dir = -1: backward on the transposed chain, B(beta, tau)^T grows by
+//           B_l^T = diag(e^{V_l}) E^T on the left, slices from M down;
+//           chunk c moves slot c+1 -> c.
+// Slot s of instance b: U at U + s*slotU + b*instU (same for D, X).
+// ---------------------------------------------------------------------------
+struct Slots {
+  double* U; long long slotU, instU;
+  double* D; long long slotD, instD;
+  double* X; long long slotX, instX;
+  // when pingpongX is set, X alternates between X (even slots) and X2 (odd)
+  // and U/D are updated in place (slot strides 0).
+  double* X2 = nullptr;
+};
+
+struct ChainWs {
+  double *C0, *C1, *W, *T;
+  int* perm;
+};
+
+void take_chain(Arena& ar, int batch, int N, ChainWs& w) {
+  long long NN = (long long)N * N;
+  w.C0 = ar.take<double>(NN * batch);
+  w.C1 = ar.take<double>(NN * batch);
+  w.W = ar.take<double>(NN * batch);
+  w.T = ar.take<double>(NN * batch);
+  w.perm = ar.take<int>((long long)N * batch);
+}
+
+inline double* slotU(const Slots& s, int slot) { return s.U + slot * s.slotU; }
+inline double* slotD(const Slots& s, int slot) { return s.D + slot * s.slotD; }
+inline double* slotX(const Slots& s, int slot) {
+  if (s.X2) return (slot & 1) ? s.X2 : s.X;
+  return s.X + slot * s.slotX;
+}
+
+dqmc_status run_chain(dqmc_handle h, int dir, int batch, int N, int M, int k, const double* E,
+                      const double* expV, long long sV, const Slots& s, const ChainWs& w,
+                      int* status) {
+  cudaStream_t st = h->stream;
+  const int nc = n_chunks(M, k);
+  const long long NN = (long long)N * N;
+  for (int step = 0; step < nc; ++step) {
+    const int c = dir > 0 ? step : nc - 1 - step;
+    const int src = dir > 0 ? c : c + 1;
+    const int dst = dir > 0 ? c + 1 : c;
+    const int lo = c * k + 1;
+    const int hi = (c + 1) * k < M ? (c + 1) * k : M;
+    const double* prev = slotU(s, src);
+    long long sprev = s.instU;
+    double* bufs[2] = {w.C0, w.C1};
+    int nb = 0;
+    for (int i = 0; i <= hi - lo; ++i) {
+      const int l = dir > 0 ? lo + i : hi - i;
+      GemmArgs g;
+      g.M = g.N = g.K = N;
+      g.batch = batch;
+      g.A = E; g.lda = N; g.sA = 0;
+      g.B = prev; g.ldb = N; g.sB = sprev;
+      g.C = bufs[nb]; g.ldc = N; g.sC = NN;
+      if (dir > 0) {
+        g.ms = expV + (long long)(l - 1) * N; g.sms = sV;      // E diag(e^{V_l}) A
+      } else {
+        g.transA = 1;                                          // diag(e^{V_l}) E^T A
+        g.rs = expV + (long long)(l - 1) * N; g.srs = sV;
+      }
+      CKP(PC_CHAIN, 2.0 * N * N * (double)N * batch, gemm_f64(g, st));
+      prev = bufs[nb];
+      sprev = NN;
+      nb ^= 1;
+    }
+    // a2-a3: (A) diag(D_src) -> U' D' T'
+    QrpArgs q;
+    q.N = N; q.batch = batch;
+    q.A = prev; q.sA = NN;
+    q.Din = slotD(s, src); q.sDin = s.instD;
+    q.W = w.W; q.sW = NN;
+    q.U = slotU(s, dst); q.sU = s.instU;
+    q.D = slotD(s, dst); q.sD = s.instD;
+    q.T = w.T; q.sT = NN;
+    q.perm = w.perm; q.sperm = N;
+    q.status = status;
+    CKP(PC_QRP, 8.0 / 3.0 * N * N * (double)N * batch, qrp_f64(q, st));
+    // a4: X_dst = T' X_src[perm]
+    GemmArgs g;
+    g.M = g.N = g.K = N;
+    g.batch = batch;
+    g.A = w.T; g.lda = N; g.sA = NN; g.upperA = 1;
+    g.B = slotX(s, src); g.ldb = N; g.sB = s.instX;
+    g.permB = w.perm; g.sperm = N;
+    g.C = slotX(s, dst); g.ldc = N; g.sC = s.instX;
+    CKP(PC_XUPD, (double)N * N * (double)N * batch, gemm_f64(g, st));
+  }
+  return DQMC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// a6-a7: G = [1 + U D X]^{-1} by Eq. (inversion_loh) and log|det(1 + U D X)|.
+//   Y = X^{-1} D_p^{-1}           (LU solve with diagonal right-hand side)
+//   Mx = Y + U D_m
+//   G = Y Mx^{-1}                 (LU solve of Mx^T G^T = Y^T)
+//   log|det| = sum log D_p + log|det Mx|;  sign = sign det Mx * sign det X
+// ---------------------------------------------------------------------------
+struct LohWs {
+  double *Dpinv, *Y, *Mx, *Wlu, *lad, *Gtmp;
+  int *sX, *sM;
+};
+
+void take_loh(Arena& ar, int batch, int N, LohWs& w) {
+  long long NN = (long long)N * N;
+  w.Dpinv = ar.take<double>((long long)N * batch);
+  w.Y = ar.take<double>(NN * batch);
+  w.Mx = ar.take<double>(NN * batch);
+  w.Wlu = ar.take<double>(2 * NN * batch);
+  w.lad = ar.take<double>(batch);
+  w.sX = ar.take<int>(batch);
+  w.sM = ar.take<int>(batch);
+}
+
+dqmc_status run_loh(dqmc_handle h, int batch, int N, const double* U, long long sU,
+                    const double* D, long long sD, const double* X, long long sX, double* G,
+                    double* logdet, int* sign, int* status, const LohWs& w) {
+  cudaStream_t st = h->stream;
+  const long long NN = (long long)N * N;
+  CK(dsplit_vec(D, sD, N, batch, w.Dpinv, 1, st));   // D_p^{-1}
+  LuArgs l1;
+  l1.N = N; l1.nrhs = N; l1.batch = batch;
+  l1.A = X; l1.sA = sX;
+  l1.Rdiag = w.Dpinv; l1.sRdiag = N;
+  l1.Z = w.Y; l1.sZ = NN; l1.ldz = N;
+  l1.W = w.Wlu; l1.sW = 2 * NN;
+  l1.sign = w.sX;
+  l1.status = status;
+  CKP(PC_LU, lu_flops(N, N) * batch, lu_solve_f64(l1, st));
+  Axpby2Args ax;
+  ax.N = N; ax.batch = batch;
+  ax.A = w.Y; ax.sA = NN;
+  ax.B = U; ax.sB = sU;
+  ax.cb = D; ax.cb_mode = 2; ax.scb = sD;
+  ax.C = w.Mx; ax.sC = NN;
+  CK(axpby2(ax, st));
+  LuArgs l2;
+  l2.N = N; l2.batch = batch;
+  l2.A = w.Mx; l2.sA = NN; l2.transA = 1;
+  if (G) {
+    l2.nrhs = N;
+    l2.R = w.Y; l2.sR = NN; l2.ldr = N; l2.transR = 1;
+    l2.Z = G; l2.sZ = NN; l2.ldz = N; l2.transZ = 1;
+  } else {
+    l2.nrhs = 0;
+    l2.Z = w.Y; l2.sZ = NN; l2.ldz = N;
+  }
+  l2.W = w.Wlu; l2.sW = 2 * NN;
+  l2.logabsdet = w.lad;
+  l2.sign = w.sM;
+  l2.status = status;
+  CKP(PC_LU, lu_flops(N, l2.nrhs) * batch, lu_solve_f64(l2, st));
+  CK(finish_logdet(D, sD, N, batch, w.lad, w.sX, w.sM, logdet, sign, status, st));
+  return DQMC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Argument checks and pointer-mode staging
+// ---------------------------------------------------------------------------
+dqmc_status check_common(dqmc_handle h, int batch, int N, int M, const double* K, double dtau,
+                         const double* V, int k) {
+  if (!h) return DQMC_ERR_ARG;
+  if (batch < 0 || N < 1 || N > 1024 || M < 1 || k < 1 || k > M) return DQMC_ERR_ARG;
+  if (!(dtau == dtau) || dtau < 0.0) return DQMC_ERR_ARG;
+  if (batch > 0 && (!K || !V)) return DQMC_ERR_ARG;
+  if (((uintptr_t)K | (uintptr_t)V) & 7) return DQMC_ERR_ARG;
+  return DQMC_OK;
+}
+
+struct Staged {
+  const double* K;
+  const double* V;
+};
+
+// Host pointer mode: device copies of K and V inside the workspace.
+struct HostIO {
+  double* K = nullptr;
+  double* V = nullptr;
+};
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+dqmc_status dqmc_create(dqmc_handle* h) {
+  if (!h) return DQMC_ERR_ARG;
+  *h = nullptr;
+  dqmc_handle x = new (std::nothrow) dqmc_handle_s();
+  if (!x) return DQMC_ERR_NOMEM;
+  if (cudaGetDevice(&x->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete x;
+    return DQMC_ERR_CUDA;
+  }
+  *h = x;
+  return DQMC_OK;
+}
+
+dqmc_status dqmc_destroy(dqmc_handle h) {
+  if (!h) return DQMC_ERR_ARG;
+  if (h->ws) {
+    cudaStreamSynchronize(h->stream);
+    cudaFree(h->ws);
+  }
+  prof_collect(h);
+  for (auto e : h->pool) cudaEventDestroy(e);
+  delete h;
+  return DQMC_OK;
+}
+
+dqmc_status dqmc_profile_enable(dqmc_handle h, int enable) {
+  if (!h) return DQMC_ERR_ARG;
+  prof_collect(h);
+  h->prof = enable != 0;
+  return DQMC_OK;
+}
+
+dqmc_status dqmc_profile_reset(dqmc_handle h) {
+  if (!h) return DQMC_ERR_ARG;
+  prof_collect(h);
+  for (int c = 0; c < PC_N; ++c) { h->prof_ms[c] = 0; h->prof_flops[c] = 0; h->prof_count[c] = 0; }
+  return DQMC_OK;
+}
+
+dqmc_status dqmc_profile_read(dqmc_handle h, int cls, double* ms, long long* launches,
+                              double* flops) {
+  if (!h || cls < 0 || cls >= PC_N) return DQMC_ERR_ARG;
+  prof_collect(h);
+  if (ms) *ms = h->prof_ms[cls];
+  if (launches) *launches = h->prof_count[cls];
+  if (flops) *flops = h->prof_flops[cls];
+  return DQMC_OK;
+}
+
+dqmc_status dqmc_set_stream(dqmc_handle h, void* stream) {
+  if (!h) return DQMC_ERR_ARG;
+  h->stream = (cudaStream_t)stream;
+  return DQMC_OK;
+}
+
+dqmc_status dqmc_set_pointer_mode(dqmc_handle h, dqmc_pointer_mode mode) {
+  if (!h || (mode != DQMC_PTR_DEVICE && mode != DQMC_PTR_HOST)) return DQMC_ERR_ARG;
+  h->pmode = mode;
+  return DQMC_OK;
+}
+
+dqmc_status dqmc_set_chain_precision(dqmc_handle h, dqmc_chain_prec prec) {
+  if (!h) return DQMC_ERR_ARG;
+  if (prec != DQMC_CHAIN_FP64) return DQMC_ERR_UNSUPPORTED;
+  h->prec = prec;
+  return DQMC_OK;
+}
+
+long long dqmc_last_launch_count(dqmc_handle h) { return h ? h->launches : -1; }
+long long dqmc_workspace_bytes(dqmc_handle h) { return h ? (long long)h->ws_bytes : -1; }
+
+const char* dqmc_status_string(dqmc_status s) {
+  switch (s) {
+    case DQMC_OK: return "ok";
+    case DQMC_ERR_ARG: return "invalid argument";
+    case DQMC_ERR_CUDA: return "CUDA runtime or launch failure";
+    case DQMC_ERR_NOMEM: return "device workspace allocation failed";
+    case DQMC_ERR_NONFINITE: return "non-finite value";
+    case DQMC_ERR_SINGULAR: return "singular pivot";
+    case DQMC_ERR_TIMEOUT: return "bounded device wait gave up";
+    case DQMC_ERR_UNSUPPORTED: return "unsupported configuration";
+  }
+  return "unknown status";
+}
+
+// ---------------------------------------------------------------------------
+// Equal-time G and log det
+// ---------------------------------------------------------------------------
+static dqmc_status greens_impl(dqmc_handle h, int batch, int N, int M, const double* K,
+                               double dtau, const double* V, int k, double* G, double* logdet,
+                               int* sign, int* status) {
+  CKS(check_common(h, batch, N, M, K, dtau, V, k));
+  h->launches = 0;
+  if (batch == 0) return DQMC_OK;
+  const bool host = h->pmode == DQMC_PTR_HOST;
+  const long long NN = (long long)N * N;
+  const int nc = n_chunks(M, k);
+  const long long Mp = (long long)(nc + 1) * k;   // padded slice stride of exp(V)
+
+  auto layout = [&](Arena& ar, ExpmWs& ew, ChainWs& cw, LohWs& lw, double*& E, double*& expV,
+                    double*& U, double*& D, double*& X0, double*& X1, int*& st, HostIO& io,
+                    double*& Gd, double*& ldd, int*& sgd) {
+    take_expm(ar, N, ew);
+    E = ew.t0;
+    expV = ar.take<double>(Mp * N * batch);
+    U = ar.take<double>(NN * batch);
+    D = ar.take<double>((long long)N * batch);
+    X0 = ar.take<double>(NN * batch);
+    X1 = ar.take<double>(NN * batch);
+    take_chain(ar, batch, N, cw);
+    take_loh(ar, batch, N, lw);
+    st = ar.take<int>(batch);
+    if (host) {
+      io.K = ar.take<double>(NN);
+      io.V = ar.take<double>((long long)M * N * batch);
+      Gd = G ? ar.take<double>(NN * batch) : nullptr;
+      ldd = ar.take<double>(batch);
+      sgd = ar.take<int>(batch);
+    }
+  };
+  ExpmWs ew; ChainWs cw; LohWs lw; HostIO io;
+  double *E, *expV, *U, *D, *X0, *X1, *Gd = nullptr, *ldd = nullptr;
+  int *stat, *sgd = nullptr;
+  Arena measure;
+  layout(measure, ew, cw, lw, E, expV, U, D, X0, X1, stat, io, Gd, ldd, sgd);
+  CKS(ensure_ws(h, measure.off));
+  Arena ar;
+  ar.base = h->ws;
+  layout(ar, ew, cw, lw, E, expV, U, D, X0, X1, stat, io, Gd, ldd, sgd);
+  cudaStream_t st = h->stream;
+
+  const double* Kd = K;
+  const double* Vd = V;
+  double* Gout = G;
+  double* ldout = logdet;
+  int* sgout = sign;
+  int* stout = status ? status : stat;
+  if (host) {
+    if (cudaMemcpyAsync(io.K, K, NN * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(io.V, V, (size_t)M * N * batch * sizeof(double), cudaMemcpyHostToDevice,
+                        st) != cudaSuccess)
+      return DQMC_ERR_CUDA;
+    Kd = io.K;
+    Vd = io.V;
+    Gout = G ? Gd : nullptr;
+    ldout = ldd;
+    sgout = sgd;
+    stout = stat;
+  }
+  if (cudaMemsetAsync(stout, 0, sizeof(int) * batch, st) != cudaSuccess) return DQMC_ERR_CUDA;
+
+  CKS(run_expm(h, Kd, N, dtau, -1.0, ew, stout, batch));
+  // exp(V_l) for every slice, padded to Mp slices per instance
+  CK(exp_pad(Vd, expV, batch, M, (int)Mp, N, 1.0, stout, st));
+
+  CK(set_identity(U, NN, N, batch, st));
+  CK(set_const(D, (long long)N * batch, 1.0, st));
+  CK(set_identity(X0, NN, N, batch, st));
+  Slots s;
+  s.U = U; s.slotU = 0; s.instU = NN;
+  s.D = D; s.slotD = 0; s.instD = N;
+  s.X = X0; s.slotX = 0; s.instX = NN;
+  s.X2 = X1;
+  CKS(run_chain(h, +1, batch, N, M, k, E, expV, Mp * N, s, cw, stout));
+  const double* Xf = (nc & 1) ? X1 : X0;
+  CKS(run_loh(h, batch, N, U, NN, D, N, Xf, NN, Gout, ldout, sgout, stout, lw));
+
+  if (host) {
+    bool ok = true;
+    if (G) ok &= cudaMemcpyAsync(G, Gd, NN * batch * sizeof(double), cudaMemcpyDeviceToHost, st) == cudaSuccess;
+    if (logdet) ok &= cudaMemcpyAsync(logdet, ldd, batch * sizeof(double), cudaMemcpyDeviceToHost, st) == cudaSuccess;
+    if (sign) ok &= cudaMemcpyAsync(sign, sgd, batch * sizeof(int), cudaMemcpyDeviceToHost, st) == cudaSuccess;
+    if (status) ok &= cudaMemcpyAsync(status, stat, batch * sizeof(int), cudaMemcpyDeviceToHost, st) == cudaSuccess;
+    ok &= cudaStreamSynchronize(st) == cudaSuccess;
+    if (!ok) return DQMC_ERR_CUDA;
+  }
+  return DQMC_OK;
+}
+
+dqmc_status dqmc_greens(dqmc_handle h, int batch, int N, int M, const double* K, double dtau,
+                        const double* V, int k, double* G, double* logdet, int* sign,
+                        int* status) {
+  return greens_impl(h, batch, N, M, K, dtau, V, k, G, logdet, sign, status);
+}
+
+dqmc_status dqmc_logdet(dqmc_handle h, int batch, int N, int M, const double* K, double dtau,
+                        const double* V, int k, double* logdet, int* sign, int* status) {
+  return greens_impl(h, batch, N, M, K, dtau, V, k, nullptr, logdet, sign, status);
+}
+
+}  // extern "C"
+
+extern "C" {
+
+dqmc_status dqmc_greens_tdisplaced(dqmc_handle h, int batch, int N, int M, const double* K,
+                                   double dtau, const double* V, int k, double* Gtt, double* Gt0,
+                                   int* status) {
+  (void)h; (void)batch; (void)N; (void)M; (void)K; (void)dtau; (void)V; (void)k; (void)Gtt;
+  (void)Gt0; (void)status;
+  return DQMC_ERR_UNSUPPORTED;
+}
+
+dqmc_status dqmc_logdet_grad(dqmc_handle h, int batch, int N, int M, const double* K, double dtau,
+                             const double* V, int k, double* logdet, int* sign, double* dV,
+                             int* status) {
+  (void)h; (void)batch; (void)N; (void)M; (void)K; (void)dtau; (void)V; (void)k; (void)logdet;
+  (void)sign; (void)dV; (void)status;
+  return DQMC_ERR_UNSUPPORTED;
+}
+
+dqmc_status dqmc_greens_ragged(dqmc_handle h, int batch, const dqmc_instance* desc,
+                               const double* K_pool, const double* V_pool, double* G_pool,
+                               double* logdet, int* sign, int* status) {
+  (void)h; (void)batch; (void)desc; (void)K_pool; (void)V_pool; (void)G_pool; (void)logdet;
+  (void)sign; (void)status;
+  return DQMC_ERR_UNSUPPORTED;
+}
+
+}  // extern "C"

@@ -1,0 +1,146 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/dqmc.h"
+
+namespace dqmc {
+
+// ---------------------------------------------------------------------------
+// Batched FP64 GEMM with fused diagonal scalings (the slice-chain product of
+// Sec. 2, Eq. (Ztr) and every dense product of the inversion schemes).
+//
+//   C_b = alpha * diag(rs_b) * opA(A_b) * diag(ms_b) * opB(B_b) * diag(cs_b)  (+ I)
+//
+// opA(A) is M x K, opB(B) is K x N, all row-major with leading dimensions.
+// Row k of opB(B) is taken from row permB[k] of opB's source when permB is
+// set.  upperA declares opA(A) upper triangular (entries below the diagonal
+// are skipped, not read).  Per-instance pointers advance by the strides
+// (stride 0 = shared by the batch).  alpha_ptr (device scalar) multiplies
+// alpha when set.  skip_if (device int) + skip_at: the launch is a copy
+// C_b = B_b when *skip_if <= skip_at (used by the scaling-and-squaring loop
+// of the matrix exponential).
+// ---------------------------------------------------------------------------
+struct GemmArgs {
+  int M = 0, N = 0, K = 0, batch = 0;
+  const double* A = nullptr; long long lda = 0, sA = 0; int transA = 0;
+  const double* B = nullptr; long long ldb = 0, sB = 0; int transB = 0;
+  double* C = nullptr; long long ldc = 0, sC = 0;
+  const double* ms = nullptr; long long sms = 0;
+  const double* rs = nullptr; long long srs = 0;
+  const double* cs = nullptr; long long scs = 0;
+  const int* permB = nullptr; long long sperm = 0;
+  int upperA = 0;
+  int addIdentity = 0;
+  double alpha = 1.0;
+  const double* alpha_ptr = nullptr;
+  const int* skip_if = nullptr; int skip_at = 0;
+  // per-instance copy-through: when lim[b] < lim_at the launch writes
+  // C_b = B_b for that instance (ragged chains of different length)
+  const int* lim = nullptr; int lim_at = 0;
+  long long sms_inner = 0;   // ms_b = ms + (b / divS) * sms + (b % divS) * sms_inner
+  // batch index b maps to instance pointers through b / bdiv (so that a
+  // shared operand can be indexed per group of bdiv problems): pointer of
+  // operand X is base + (b / divX) * sX.
+  int divA = 1, divB = 1, divC = 1, divS = 1;
+};
+
+cudaError_t gemm_f64(const GemmArgs& a, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// Column-pivoted Householder QR, one CTA per instance (Sec. 4.2.2).
+//   Y = A diag(Din) ;  Y P = Q R ;  U = Q, D = |diag R|, T = D^{-1} R (upper,
+//   pivoted column order, zeros below the diagonal), perm = P as an index map.
+// W is an N x N workspace per instance.
+// ---------------------------------------------------------------------------
+struct QrpArgs {
+  int N = 0, batch = 0;
+  const double* A = nullptr; long long sA = 0;
+  const double* Din = nullptr; long long sDin = 0;   // nullable
+  double* W = nullptr; long long sW = 0;
+  double* U = nullptr; long long sU = 0;
+  double* D = nullptr; long long sD = 0;
+  double* T = nullptr; long long sT = 0;
+  int* perm = nullptr; long long sperm = 0;
+  int* status = nullptr; int status_div = 1;          // nullable
+  const int* active = nullptr;                        // nullable: instance enabled flags
+};
+
+cudaError_t qrp_f64(const QrpArgs& a, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// LU with partial pivoting and solve, one CTA per instance:
+//   opA(A) Z = opR(R)   (A: N x N, R: N x nrhs), Z stored as opZ.
+// Optionally R is a diagonal given as a vector (Rdiag, N entries) instead of
+// a dense matrix.  Returns log|det opA(A)| and its sign per instance.
+// Work: N x (N + nrhs) per instance.
+// ---------------------------------------------------------------------------
+struct LuArgs {
+  int N = 0, nrhs = 0, batch = 0;
+  const double* A = nullptr; long long sA = 0; int transA = 0;
+  const double* R = nullptr; long long sR = 0; long long ldr = 0; int transR = 0;
+  const double* Rdiag = nullptr; long long sRdiag = 0; int invRdiag = 0;
+  double* Z = nullptr; long long sZ = 0; long long ldz = 0; int transZ = 0;
+  double* W = nullptr; long long sW = 0;
+  double* logabsdet = nullptr; int* sign = nullptr;   // per instance, nullable
+  int* status = nullptr; int status_div = 1;
+};
+
+cudaError_t lu_solve_f64(const LuArgs& a, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// Element-wise helpers.
+// ---------------------------------------------------------------------------
+// out[i] = exp(sgn * v[i]) for n entries; flags non-finite inputs per instance
+// (instance = i / per_instance) in status.
+cudaError_t exp_vec(const double* v, double* out, long long n, double sgn,
+                    long long per_instance, int* status, cudaStream_t st);
+// C = rowscale1 * A * colscale1 + rowscale2 * B * colscale2, per instance,
+// scales given as (Dsplit mode, vector) pairs; see elementwise.cu.
+struct Axpby2Args {
+  int N = 0, batch = 0;
+  const double* A = nullptr; long long sA = 0;
+  const double* B = nullptr; long long sB = 0;
+  double* C = nullptr; long long sC = 0;
+  // each scale: pointer to a D vector + mode (0: none, 1: 1/max(D,1),
+  // 2: min(D,1), 3: max(D,1))
+  const double* ra = nullptr; int ra_mode = 0; long long sra = 0;
+  const double* ca = nullptr; int ca_mode = 0; long long sca = 0;
+  const double* rb = nullptr; int rb_mode = 0; long long srb = 0;
+  const double* cb = nullptr; int cb_mode = 0; long long scb = 0;
+  int divA = 1, divB = 1, divC = 1, divRA = 1, divCA = 1, divRB = 1, divCB = 1;
+};
+cudaError_t axpby2(const Axpby2Args& a, cudaStream_t st);
+// out[b*n + i] = f(D[b*sD + i]) with mode as in Axpby2Args (4: 1/D).
+cudaError_t dsplit_vec(const double* D, long long sD, int n, int batch, double* out, int mode,
+                       cudaStream_t st);
+// exp(sgn*V) of a batch x M x N field into a batch x Mp x N array (padding = 1).
+cudaError_t exp_pad(const double* V, double* out, int batch, int M, int Mp, int N, double sgn,
+                    int* status, cudaStream_t st);
+// y = 1 - diag(G) for a batch of N x N matrices; y_b at y + b*sy.
+cudaError_t one_minus_diag(const double* G, long long sG, int N, int batch,
+                           double* y, long long sy, int ydiv, long long sy_outer,
+                           cudaStream_t st);
+// logdet_b = sum_i log max(D_bi, 1) + logabsdet_b ; sign_b = s1_b * s2_b;
+// flags non-finite results.
+cudaError_t finish_logdet(const double* D, long long sD, int N, int batch, const double* lad,
+                          const int* s1, const int* s2, double* logdet, int* sign,
+                          int* status, cudaStream_t st);
+// Copy of strided N x N matrices (out_b = in_b), optional transpose.
+cudaError_t copy_mats(const double* in, long long sin, double* out, long long sout,
+                      int N, int batch, int transpose, int divin, int divout,
+                      cudaStream_t st);
+// Identity / ones initialisers.
+cudaError_t set_identity(double* A, long long sA, int N, int batch, cudaStream_t st);
+cudaError_t set_const(double* x, long long n, double v, cudaStream_t st);
+// 1-norm based scaling for the matrix exponential: s = max(0, ceil(log2(||dtau K||_1 / 0.5))),
+// scale = sgn * dtau / 2^s; writes s (int) and scale (double) to device memory;
+// also writes the symmetry defect flag into *asym (1 if K != K^T).
+cudaError_t expm_prepare(const double* K, int N, double dtau, double sgn,
+                         int* s_out, double* scale_out, int* asym, cudaStream_t st);
+// Field the status flag of the symmetry check into every instance's status.
+cudaError_t or_status(int* status, int batch, const int* flag, int bit, cudaStream_t st);
+
+}  // namespace dqmc

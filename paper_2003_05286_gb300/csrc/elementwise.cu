@@ -1,0 +1,279 @@
+// Small element-wise kernels of the method: exp(+-V_l) of the slice matrices
+// (Sec. 2), the D+ = max(D,1) / D- = min(D,1) splits of Loh's inversions
+// (Eqs. (inversion_loh), (inversion_tdgf_loh)), the log-det accumulation,
+// the gradient read-out 1 - G_l(i,i), and the scaling step of the matrix
+// exponential exp(-dtau K).  They are O(N^2) per instance against O(N^3) for
+// the products and QR, so they are written for clarity: grid-stride loops.
+#include "common.cuh"
+
+namespace dqmc {
+
+namespace {
+constexpr int TPB = 256;
+inline int nblocks(long long n) {
+  long long g = (n + TPB - 1) / TPB;
+  if (g > 152LL * 64) g = 152LL * 64;
+  return (int)(g < 1 ? 1 : g);
+}
+
+__device__ __forceinline__ double dmode(double d, int mode) {
+  switch (mode) {
+    case 1: return 1.0 / fmax(d, 1.0);   // D_p^{-1}
+    case 2: return fmin(d, 1.0);         // D_m
+    case 3: return fmax(d, 1.0);         // D_p
+    case 4: return 1.0 / d;              // D^{-1}
+    default: return 1.0;
+  }
+}
+}  // namespace
+
+__global__ void exp_vec_kernel(const double* v, double* out, long long n, double sgn,
+                               long long per, int* status) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    double x = v[i];
+    if (!isfinite(x) && status) atomicOr(&status[i / per], DQMC_STATUS_NONFINITE_INPUT);
+    out[i] = exp(sgn * x);
+  }
+}
+
+cudaError_t exp_vec(const double* v, double* out, long long n, double sgn,
+                    long long per_instance, int* status, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  exp_vec_kernel<<<nblocks(n), TPB, 0, st>>>(v, out, n, sgn, per_instance, status);
+  return cudaGetLastError();
+}
+
+__global__ void axpby2_kernel(const Axpby2Args a) {
+  const long long NN = (long long)a.N * a.N;
+  const long long total = NN * a.batch;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    int b = (int)(e / NN);
+    long long ij = e % NN;
+    int i = (int)(ij / a.N), j = (int)(ij % a.N);
+    double v = 0.0;
+    if (a.A) {
+      double x = a.A[(long long)(b / a.divA) * a.sA + ij];
+      if (a.ra) x *= dmode(a.ra[(long long)(b / a.divRA) * a.sra + i], a.ra_mode);
+      if (a.ca) x *= dmode(a.ca[(long long)(b / a.divCA) * a.sca + j], a.ca_mode);
+      v = x;
+    }
+    if (a.B) {
+      double y = a.B[(long long)(b / a.divB) * a.sB + ij];
+      if (a.rb) y *= dmode(a.rb[(long long)(b / a.divRB) * a.srb + i], a.rb_mode);
+      if (a.cb) y *= dmode(a.cb[(long long)(b / a.divCB) * a.scb + j], a.cb_mode);
+      v += y;
+    }
+    a.C[(long long)(b / a.divC) * a.sC + ij] = v;
+  }
+}
+
+cudaError_t axpby2(const Axpby2Args& a, cudaStream_t st) {
+  long long total = (long long)a.N * a.N * a.batch;
+  if (total <= 0) return cudaSuccess;
+  axpby2_kernel<<<nblocks(total), TPB, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+__global__ void dsplit_kernel(const double* D, long long sD, int n, int batch, double* out,
+                              int mode) {
+  const long long total = (long long)n * batch;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    long long b = e / n, i = e % n;
+    out[e] = dmode(D[b * sD + i], mode);
+  }
+}
+
+cudaError_t dsplit_vec(const double* D, long long sD, int n, int batch, double* out, int mode,
+                       cudaStream_t st) {
+  long long total = (long long)n * batch;
+  if (total <= 0) return cudaSuccess;
+  dsplit_kernel<<<nblocks(total), TPB, 0, st>>>(D, sD, n, batch, out, mode);
+  return cudaGetLastError();
+}
+
+// out[(b*Mp + l)*N + i] = exp(sgn * V[(b*M + l)*N + i]) for l < M, 1 for M <= l < Mp
+__global__ void exp_pad_kernel(const double* V, double* out, int batch, int M, int Mp, int N,
+                               double sgn, int* status) {
+  const long long total = (long long)batch * Mp * N;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    long long b = e / ((long long)Mp * N);
+    long long r = e % ((long long)Mp * N);
+    int l = (int)(r / N), i = (int)(r % N);
+    double v = 1.0;
+    if (l < M) {
+      double x = V[(b * M + l) * N + i];
+      if (!isfinite(x) && status) atomicOr(&status[b], DQMC_STATUS_NONFINITE_INPUT);
+      v = exp(sgn * x);
+    }
+    out[e] = v;
+  }
+}
+
+cudaError_t exp_pad(const double* V, double* out, int batch, int M, int Mp, int N, double sgn,
+                    int* status, cudaStream_t st) {
+  long long total = (long long)batch * Mp * N;
+  if (total <= 0) return cudaSuccess;
+  exp_pad_kernel<<<nblocks(total), TPB, 0, st>>>(V, out, batch, M, Mp, N, sgn, status);
+  return cudaGetLastError();
+}
+
+// y[(b / ydiv) * sy_outer + (b % ydiv) * sy + i] = 1 - G_b(i, i)
+__global__ void one_minus_diag_kernel(const double* G, long long sG, int N, int batch,
+                                      double* y, long long sy, int ydiv, long long sy_outer) {
+  const long long total = (long long)N * batch;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    int b = (int)(e / N), i = (int)(e % N);
+    double g = G[(long long)b * sG + (long long)i * N + i];
+    y[(long long)(b / ydiv) * sy_outer + (long long)(b % ydiv) * sy + i] = 1.0 - g;
+  }
+}
+
+cudaError_t one_minus_diag(const double* G, long long sG, int N, int batch, double* y,
+                           long long sy, int ydiv, long long sy_outer, cudaStream_t st) {
+  long long total = (long long)N * batch;
+  if (total <= 0) return cudaSuccess;
+  one_minus_diag_kernel<<<nblocks(total), TPB, 0, st>>>(G, sG, N, batch, y, sy, ydiv, sy_outer);
+  return cudaGetLastError();
+}
+
+// one warp per instance: logdet = sum_i log max(D_i, 1) + lad
+__global__ void finish_logdet_kernel(const double* D, long long sD, int N, int batch, const double* lad,
+                                     const int* s1, const int* s2, double* logdet, int* sign,
+                                     int* status) {
+  const int lane = threadIdx.x & 31;
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int b = w; b < batch; b += nw) {
+    double s = 0.0;
+    for (int i = lane; i < N; i += 32) s += log(fmax(D[(long long)b * sD + i], 1.0));
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if (lane == 0) {
+      double ld = s + (lad ? lad[b] : 0.0);
+      if (logdet) logdet[b] = ld;
+      int sg = (s1 ? s1[b] : 1) * (s2 ? s2[b] : 1);
+      if (sign) sign[b] = sg;
+      if (!isfinite(ld) && status) atomicOr(&status[b], DQMC_STATUS_NONFINITE_OUTPUT);
+    }
+  }
+}
+
+cudaError_t finish_logdet(const double* D, long long sD, int N, int batch, const double* lad, const int* s1,
+                          const int* s2, double* logdet, int* sign, int* status,
+                          cudaStream_t st) {
+  if (batch <= 0) return cudaSuccess;
+  int blocks = (batch * 32 + TPB - 1) / TPB;
+  if (blocks > 4096) blocks = 4096;
+  finish_logdet_kernel<<<blocks, TPB, 0, st>>>(D, sD, N, batch, lad, s1, s2, logdet, sign, status);
+  return cudaGetLastError();
+}
+
+__global__ void copy_mats_kernel(const double* in, long long sin, double* out, long long sout,
+                                 int N, int batch, int transpose, int divin, int divout) {
+  const long long NN = (long long)N * N, total = NN * batch;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    int b = (int)(e / NN);
+    long long ij = e % NN;
+    int i = (int)(ij / N), j = (int)(ij % N);
+    long long src = transpose ? (long long)j * N + i : ij;
+    out[(long long)(b / divout) * sout + ij] = in[(long long)(b / divin) * sin + src];
+  }
+}
+
+cudaError_t copy_mats(const double* in, long long sin, double* out, long long sout, int N,
+                      int batch, int transpose, int divin, int divout, cudaStream_t st) {
+  long long total = (long long)N * N * batch;
+  if (total <= 0) return cudaSuccess;
+  copy_mats_kernel<<<nblocks(total), TPB, 0, st>>>(in, sin, out, sout, N, batch, transpose,
+                                                   divin, divout);
+  return cudaGetLastError();
+}
+
+__global__ void set_identity_kernel(double* A, long long sA, int N, int batch) {
+  const long long NN = (long long)N * N, total = NN * batch;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    int b = (int)(e / NN);
+    long long ij = e % NN;
+    A[(long long)b * sA + ij] = ((ij / N) == (ij % N)) ? 1.0 : 0.0;
+  }
+}
+
+cudaError_t set_identity(double* A, long long sA, int N, int batch, cudaStream_t st) {
+  long long total = (long long)N * N * batch;
+  if (total <= 0) return cudaSuccess;
+  set_identity_kernel<<<nblocks(total), TPB, 0, st>>>(A, sA, N, batch);
+  return cudaGetLastError();
+}
+
+__global__ void set_const_kernel(double* x, long long n, double v) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    x[i] = v;
+}
+
+cudaError_t set_const(double* x, long long n, double v, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  set_const_kernel<<<nblocks(n), TPB, 0, st>>>(x, n, v);
+  return cudaGetLastError();
+}
+
+// One block: ||K||_1 (max column sum), symmetry check, and the scaling
+// exponent s with ||dtau K||_1 / 2^s <= 1/2.
+__global__ void expm_prepare_kernel(const double* K, int N, double dtau, double sgn, int* s_out,
+                                    double* scale_out, int* asym) {
+  __shared__ double red[TPB];
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  double mx = 0.0;
+  for (int c = threadIdx.x; c < N; c += blockDim.x) {
+    double s = 0.0;
+    for (int r = 0; r < N; ++r) {
+      double x = K[(long long)r * N + c];
+      s += fabs(x);
+      if (x != K[(long long)c * N + r] || !isfinite(x)) bad = 1;
+    }
+    mx = fmax(mx, s);
+  }
+  red[threadIdx.x] = mx;
+  __syncthreads();
+  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+    if (threadIdx.x < off) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + off]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double nrm = fabs(dtau) * red[0];
+    int s = 0;
+    while (nrm > 0.5 && s < 60) { nrm *= 0.5; ++s; }
+    *s_out = s;
+    *scale_out = sgn * dtau * ldexp(1.0, -s);
+    *asym = bad || (s > 12);
+  }
+}
+
+cudaError_t expm_prepare(const double* K, int N, double dtau, double sgn, int* s_out,
+                         double* scale_out, int* asym, cudaStream_t st) {
+  expm_prepare_kernel<<<1, TPB, 0, st>>>(K, N, dtau, sgn, s_out, scale_out, asym);
+  return cudaGetLastError();
+}
+
+__global__ void or_status_kernel(int* status, int batch, const int* flag, int bit) {
+  if (*flag == 0) return;
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < batch; b += gridDim.x * blockDim.x)
+    status[b] |= bit;
+}
+
+cudaError_t or_status(int* status, int batch, const int* flag, int bit, cudaStream_t st) {
+  if (batch <= 0 || !status) return cudaSuccess;
+  or_status_kernel<<<nblocks(batch), TPB, 0, st>>>(status, batch, flag, bit);
+  return cudaGetLastError();
+}
+
+}  // namespace dqmc

@@ -1,0 +1,172 @@
+// Batched FP64 GEMM with fused diagonal scalings.
+//
+// GB300 executes FP64 at 1/64 of the FP32 rate (measured: 1.20 TFLOP/s with
+// DFMA, 1.05 TFLOP/s with the f64 mma.sync shapes), so every dense product of
+// the method is bound by the FP64 pipe: shared-memory and L2 traffic are
+// tiny next to it.  The kernel is therefore a plain register-tiled DFMA GEMM
+// whose only job is to keep the FP64 pipe busy: 4x4 outputs per thread,
+// double-buffered shared-memory tiles filled from registers one K-block
+// ahead, and every diagonal factor of the method (exp(V_l) of the slice
+// matrix, the D+/D- splits, the column scale of Eq. (stabmult)) applied while
+// a tile is staged or written, never as a separate pass.
+#include "common.cuh"
+
+namespace dqmc {
+
+template <int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+gemm_f64_kernel(const GemmArgs a) {
+  constexpr int NTX = BN / TN;
+  constexpr int NT = (BM / TM) * NTX;
+  constexpr int A_PER = (BM * BK) / NT;
+  constexpr int B_PER = (BK * BN) / NT;
+  static_assert((BM * BK) % NT == 0 && (BK * BN) % NT == 0, "tile/thread mismatch");
+
+  __shared__ __align__(16) double As[2][BK][BM];
+  __shared__ __align__(16) double Bs[2][BK][BN];
+
+  for (int b = blockIdx.z; b < a.batch; b += gridDim.z) {
+  if (b != (int)blockIdx.z) __syncthreads();   // shared tiles are reused across batch entries
+  const int m0 = blockIdx.y * BM;
+  const int n0 = blockIdx.x * BN;
+  const int tid = threadIdx.x;
+  const int tx = tid % NTX, ty = tid / NTX;
+
+  const double* __restrict__ A = a.A + (long long)(b / a.divA) * a.sA;
+  const double* __restrict__ B = a.B + (long long)(b / a.divB) * a.sB;
+  double* __restrict__ C = a.C + (long long)(b / a.divC) * a.sC;
+  const double* ms = a.ms ? a.ms + (long long)(b / a.divS) * a.sms + (long long)(b % a.divS) * a.sms_inner : nullptr;
+  const double* rs = a.rs ? a.rs + (long long)(b / a.divS) * a.srs : nullptr;
+  const double* cs = a.cs ? a.cs + (long long)(b / a.divS) * a.scs : nullptr;
+  const int* perm = a.permB ? a.permB + (long long)(b / a.divB) * a.sperm : nullptr;
+
+  if ((a.skip_if && *a.skip_if <= a.skip_at) || (a.lim && a.lim[b] < a.lim_at)) {
+    // identity pass: C = opB(B) restricted to this tile (square problems only)
+    for (int e = tid; e < BM * BN; e += NT) {
+      int m = m0 + e / BN, n = n0 + e % BN;
+      if (m < a.M && n < a.N) C[(long long)m * a.ldc + n] = B[(long long)m * a.ldb + n];
+    }
+    continue;
+  }
+
+  double alpha = a.alpha;
+  if (a.alpha_ptr) alpha *= *a.alpha_ptr;
+
+  const int kbeg = a.upperA ? (m0 / BK) * BK : 0;
+  const int kend = a.K;
+
+  double ra[A_PER], rb[B_PER];
+
+  auto load_tiles = [&](int kb) {
+#pragma unroll
+    for (int i = 0; i < A_PER; ++i) {
+      int e = tid + i * NT;
+      int m, k;
+      double v = 0.0;
+      if (!a.transA) { k = e % BK; m = e / BK; } else { m = e % BM; k = e / BM; }
+      int gm = m0 + m, gk = kb + k;
+      if (gm < a.M && gk < a.K && !(a.upperA && gk < gm)) {
+        v = a.transA ? A[(long long)gk * a.lda + gm] : A[(long long)gm * a.lda + gk];
+      }
+      ra[i] = v;
+    }
+#pragma unroll
+    for (int i = 0; i < B_PER; ++i) {
+      int e = tid + i * NT;
+      int k, n;
+      double v = 0.0;
+      if (!a.transB) { n = e % BN; k = e / BN; } else { k = e % BK; n = e / BK; }
+      int gk = kb + k, gn = n0 + n;
+      if (gk < a.K && gn < a.N) {
+        int row = perm ? perm[gk] : gk;
+        v = a.transB ? B[(long long)gn * a.ldb + row] : B[(long long)row * a.ldb + gn];
+        if (ms) v *= ms[gk];
+      }
+      rb[i] = v;
+    }
+  };
+  auto store_tiles = [&](int buf) {
+#pragma unroll
+    for (int i = 0; i < A_PER; ++i) {
+      int e = tid + i * NT;
+      int m, k;
+      if (!a.transA) { k = e % BK; m = e / BK; } else { m = e % BM; k = e / BM; }
+      As[buf][k][m] = ra[i];
+    }
+#pragma unroll
+    for (int i = 0; i < B_PER; ++i) {
+      int e = tid + i * NT;
+      int k, n;
+      if (!a.transB) { n = e % BN; k = e / BN; } else { k = e % BK; n = e / BK; }
+      Bs[buf][k][n] = rb[i];
+    }
+  };
+
+  double acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = 0.0;
+
+  if (kbeg < kend) {
+    load_tiles(kbeg);
+    store_tiles(0);
+    __syncthreads();
+    int buf = 0;
+    for (int kb = kbeg; kb < kend; kb += BK) {
+      const bool more = kb + BK < kend;
+      if (more) load_tiles(kb + BK);
+#pragma unroll
+      for (int kk = 0; kk < BK; ++kk) {
+        double af[TM], bf[TN];
+#pragma unroll
+        for (int i = 0; i < TM; ++i) af[i] = As[buf][kk][ty * TM + i];
+#pragma unroll
+        for (int j = 0; j < TN; ++j) bf[j] = Bs[buf][kk][tx * TN + j];
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+          for (int j = 0; j < TN; ++j) acc[i][j] = fma(af[i], bf[j], acc[i][j]);
+      }
+      if (more) {
+        store_tiles(buf ^ 1);
+        __syncthreads();
+        buf ^= 1;
+      }
+    }
+  }
+
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    int m = m0 + ty * TM + i;
+    if (m >= a.M) continue;
+    double r = alpha * (rs ? rs[m] : 1.0);
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      int n = n0 + tx * TN + j;
+      if (n >= a.N) continue;
+      double v = acc[i][j] * r;
+      if (cs) v *= cs[n];
+      if (a.addIdentity && m == n) v += 1.0;
+      C[(long long)m * a.ldc + n] = v;
+    }
+  }
+  }  // batch loop
+}
+
+cudaError_t gemm_f64(const GemmArgs& a, cudaStream_t st) {
+  if (a.batch <= 0 || a.M <= 0 || a.N <= 0) return cudaSuccess;
+  const int zb = a.batch < 65535 ? a.batch : 65535;   // grid z limit; the kernel loops
+  if (a.M >= 96 && a.N >= 96) {
+    constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4;
+    dim3 grid((a.N + BN - 1) / BN, (a.M + BM - 1) / BM, zb);
+    gemm_f64_kernel<BM, BN, BK, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, st>>>(a);
+  } else {
+    constexpr int BM = 32, BN = 32, BK = 16, TM = 4, TN = 4;
+    dim3 grid((a.N + BN - 1) / BN, (a.M + BM - 1) / BM, zb);
+    gemm_f64_kernel<BM, BN, BK, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, st>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace dqmc

@@ -1,0 +1,178 @@
+// LU with partial pivoting and multi-right-hand-side solve, one CTA per
+// instance.  Every inverse the inversion schemes write (X^{-1}, the bracket
+// of Eq. (inversion_loh), the middle matrix of Eq. (inversion_tdgf_loh)) is
+// evaluated as a solve with this kernel, never as an explicit inverse.
+//
+// The augmented matrix [opA(A) | opR(R)] (N x (N + nrhs), row-major, in the
+// L2-resident workspace) is eliminated column by column with row pivoting
+// (largest |a_rj|, lowest row on ties); one thread owns one column, so each
+// rank-1 update streams rows that are contiguous across the threads of a
+// warp.  Back substitution then runs without any synchronisation: each
+// right-hand-side column belongs to one thread.  log|det| and the sign of
+// det(opA(A)) come out of the pivots.
+#include "common.cuh"
+
+namespace dqmc {
+
+template <int NT>
+__global__ void __launch_bounds__(NT) lu_kernel(const LuArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int N = a.N, nr = a.nrhs, Wd = N + nr;
+  double* lbuf = reinterpret_cast<double*>(smem_raw);   // multipliers of the current column
+  double* dinv = lbuf + N;                              // 1 / u_jj
+  __shared__ unsigned long long sk[32];
+  __shared__ int si[32];
+  __shared__ int s_flag, s_sign;
+  __shared__ double s_lad;
+
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+
+  for (int b = blockIdx.x; b < a.batch; b += gridDim.x) {
+    const double* __restrict__ A = a.A + (long long)b * a.sA;
+    double* __restrict__ W = a.W + (long long)b * a.sW;
+    if (tid == 0) { s_flag = 0; s_sign = 1; s_lad = 0.0; }
+
+    // ---- load [opA(A) | opR(R)] ------------------------------------------
+    for (long long e = tid; e < (long long)N * N; e += NT) {
+      int r = (int)(e / N), c = (int)(e % N);
+      // read contiguous memory: for transA the contiguous index is the row of W
+      double v = a.transA ? A[(long long)c * N + r] : A[e];
+      W[(long long)r * Wd + c] = v;
+    }
+    if (a.Rdiag) {
+      const double* Rd = a.Rdiag + (long long)b * a.sRdiag;
+      for (long long e = tid; e < (long long)N * nr; e += NT) {
+        int r = (int)(e / nr), c = (int)(e % nr);
+        double v = 0.0;
+        if (r == c) v = a.invRdiag ? 1.0 / Rd[r] : Rd[r];
+        W[(long long)r * Wd + N + c] = v;
+      }
+    } else {
+      const double* R = a.R + (long long)b * a.sR;
+      for (long long e = tid; e < (long long)N * nr; e += NT) {
+        int r, c;
+        double v;
+        if (!a.transR) { r = (int)(e / nr); c = (int)(e % nr); v = R[(long long)r * a.ldr + c]; }
+        else { c = (int)(e / N); r = (int)(e % N); v = R[(long long)c * a.ldr + r]; }
+        W[(long long)r * Wd + N + c] = v;
+      }
+    }
+    __syncthreads();
+
+    // ---- elimination with partial pivoting -------------------------------
+    for (int j = 0; j < N; ++j) {
+      unsigned long long key = 0ull;   // |a_rj| bits (sign cleared), ordered like the values
+      int idx = 0x7fffffff;
+      for (int r = j + tid; r < N; r += NT) {
+        unsigned long long k2 =
+            (unsigned long long)__double_as_longlong(W[(long long)r * Wd + j]) & 0x7fffffffffffffffull;
+        if (k2 > key || (k2 == key && r < idx)) { key = k2; idx = r; }
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        unsigned long long k2 = __shfl_down_sync(0xffffffffu, key, off);
+        int i2 = __shfl_down_sync(0xffffffffu, idx, off);
+        if (k2 > key || (k2 == key && i2 < idx)) { key = k2; idx = i2; }
+      }
+      if (lane == 0) { sk[wid] = key; si[wid] = idx; }
+      __syncthreads();
+      if (wid == 0) {
+        key = lane < NT / 32 ? sk[lane] : 0ull;
+        idx = lane < NT / 32 ? si[lane] : 0x7fffffff;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+          unsigned long long k2 = __shfl_down_sync(0xffffffffu, key, off);
+          int i2 = __shfl_down_sync(0xffffffffu, idx, off);
+          if (k2 > key || (k2 == key && i2 < idx)) { key = k2; idx = i2; }
+        }
+        if (lane == 0) { sk[0] = key; si[0] = idx; }
+      }
+      __syncthreads();
+      int p = si[0];
+      if (p < j || p >= N) p = j;
+      if (p != j) {
+        for (int c = tid; c < Wd; c += NT) {
+          double t = W[(long long)j * Wd + c];
+          W[(long long)j * Wd + c] = W[(long long)p * Wd + c];
+          W[(long long)p * Wd + c] = t;
+        }
+      }
+      __syncthreads();
+      const double piv = W[(long long)j * Wd + j];
+      const double inv = piv != 0.0 ? 1.0 / piv : 0.0;
+      if (tid == 0) {
+        if (piv == 0.0) s_flag |= DQMC_STATUS_SINGULAR;
+        if (p != j) s_sign = -s_sign;
+        if (piv < 0.0) s_sign = -s_sign;
+        s_lad += log(fabs(piv));
+        dinv[j] = inv;
+      }
+      for (int r = j + 1 + tid; r < N; r += NT) lbuf[r] = W[(long long)r * Wd + j] * inv;
+      __syncthreads();
+      for (int c = j + 1 + tid; c < Wd; c += NT) {
+        double* col = W + c;
+        const double pj = col[(long long)j * Wd];
+        if (pj == 0.0) continue;
+        int r = j + 1;
+        for (; r + 1 < N; r += 2) {
+          col[(long long)r * Wd] = fma(-lbuf[r], pj, col[(long long)r * Wd]);
+          col[(long long)(r + 1) * Wd] = fma(-lbuf[r + 1], pj, col[(long long)(r + 1) * Wd]);
+        }
+        if (r < N) col[(long long)r * Wd] = fma(-lbuf[r], pj, col[(long long)r * Wd]);
+      }
+      __syncthreads();
+    }
+
+    // ---- back substitution, one thread per right-hand side ---------------
+    double* __restrict__ Z = a.Z + (long long)b * a.sZ;
+    for (int c = tid; c < nr; c += NT) {
+      double* col = W + N + c;
+      for (int i = N - 1; i >= 0; --i) {
+        const double* urow = W + (long long)i * Wd;
+        double s0 = col[(long long)i * Wd], s1 = 0.0;
+        int m = i + 1;
+        for (; m + 1 < N; m += 2) {
+          s0 = fma(-urow[m], col[(long long)m * Wd], s0);
+          s1 = fma(-urow[m + 1], col[(long long)(m + 1) * Wd], s1);
+        }
+        if (m < N) s0 = fma(-urow[m], col[(long long)m * Wd], s0);
+        col[(long long)i * Wd] = (s0 + s1) * dinv[i];
+      }
+    }
+    __syncthreads();
+    for (long long e = tid; e < (long long)N * nr; e += NT) {
+      if (!a.transZ) {
+        int r = (int)(e / nr), c = (int)(e % nr);
+        Z[(long long)r * a.ldz + c] = W[(long long)r * Wd + N + c];
+      } else {
+        int c = (int)(e / N), r = (int)(e % N);
+        Z[(long long)c * a.ldz + r] = W[(long long)r * Wd + N + c];
+      }
+    }
+    if (tid == 0) {
+      if (a.logabsdet) a.logabsdet[b] = s_lad;
+      if (a.sign) a.sign[b] = s_sign;
+      if (s_flag && a.status) atomicOr(&a.status[b / a.status_div], s_flag);
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t lu_solve_f64(const LuArgs& a, cudaStream_t st) {
+  if (a.batch <= 0 || a.N <= 0) return cudaSuccess;
+  size_t sm = (size_t)a.N * 2 * sizeof(double) + 16;
+  int grid = a.batch < (1 << 30) ? a.batch : (1 << 30);
+  if (a.N + a.nrhs <= 64) {
+    cudaFuncSetAttribute(lu_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    lu_kernel<64><<<grid, 64, sm, st>>>(a);
+  } else if (a.N + a.nrhs <= 256) {
+    cudaFuncSetAttribute(lu_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    lu_kernel<256><<<grid, 256, sm, st>>>(a);
+  } else {
+    cudaFuncSetAttribute(lu_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    lu_kernel<512><<<grid, 512, sm, st>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace dqmc
