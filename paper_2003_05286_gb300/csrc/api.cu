@@ -589,22 +589,307 @@ dqmc_status dqmc_logdet(dqmc_handle h, int batch, int N, int M, const double* K,
 
 }  // extern "C"
 
+
+// ---------------------------------------------------------------------------
+// Two stacks (App. A) and the D+/D- split middle matrix of Eq. (inversion_tdgf_loh)
+//
+// Forward slot j:  B(tau_j, 0)       = U_F a X_F          (Eq. (stabmult) chain)
+// Backward slot j: B(beta, tau_j)^T  = U_b b T_b          (same chain on B_l^T)
+// With a = a_p a_m, b = b_p b_m (a_p = max(a,1), a_m = min(a,1)):
+//   mid = a_p^{-1} (U_F^T U_b) b_p^{-1} + a_m (X_F T_b^T) b_m        (all factors <= 1)
+//   1 + B(tau,0) B(beta,tau)       = U_F a_p mid b_p U_b^T
+//   B(tau,0)^{-1} + B(beta,tau)    = X_F^{-1} a_m^{-1} mid b_p U_b^T
+// so that
+//   G(tau,tau) = U_b b_p^{-1} mid^{-1} a_p^{-1} U_F^T
+//   G(tau,0)   = U_b b_p^{-1} mid^{-1} a_m X_F
+// The second line is Eq. (inversion_tdgf_loh) with the left chain
+// B_1^{-1}...B_l^{-1} = X_F^{-1} a^{-1} U_F^T taken from the forward stack
+// (its scales a^{-1} split as D_Lp = a_m^{-1}, D_Lm = a_p^{-1}); the first is
+// the same split applied to the equal-time bracket of App. A.  One LU of mid
+// serves both right-hand sides.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct StackWs {
+  double *UF, *DF, *XF, *Ub, *Db, *Tb;
+};
+
+void take_stacks(Arena& ar, int batch, int N, int nt, StackWs& w) {
+  long long NN = (long long)N * N, Q = (long long)batch * nt;
+  w.UF = ar.take<double>(Q * NN);
+  w.DF = ar.take<double>(Q * N);
+  w.XF = ar.take<double>(Q * NN);
+  w.Ub = ar.take<double>(Q * NN);
+  w.Db = ar.take<double>(Q * N);
+  w.Tb = ar.take<double>(Q * NN);
+}
+
+dqmc_status run_stacks(dqmc_handle h, int batch, int N, int M, int k, const double* E,
+                       const double* expV, long long sV, const StackWs& w, const ChainWs& cw,
+                       int* status) {
+  cudaStream_t st = h->stream;
+  const int nc = n_chunks(M, k), nt = nc + 1;
+  const long long NN = (long long)N * N;
+  // forward slot 0 and backward slot nc are the identity decomposition
+  CK(set_identity(w.UF, nt * NN, N, batch, st));
+  CK(set_const_strided(w.DF, (long long)nt * N, N, batch, 1.0, st));
+  CK(set_identity(w.XF, nt * NN, N, batch, st));
+  CK(set_identity(w.Ub + nc * NN, nt * NN, N, batch, st));
+  CK(set_const_strided(w.Db + (long long)nc * N, (long long)nt * N, N, batch, 1.0, st));
+  CK(set_identity(w.Tb + nc * NN, nt * NN, N, batch, st));
+  Slots f;
+  f.U = w.UF; f.slotU = NN; f.instU = nt * NN;
+  f.D = w.DF; f.slotD = N; f.instD = (long long)nt * N;
+  f.X = w.XF; f.slotX = NN; f.instX = nt * NN;
+  CKS(run_chain(h, +1, batch, N, M, k, E, expV, sV, f, cw, status));
+  Slots b;
+  b.U = w.Ub; b.slotU = NN; b.instU = nt * NN;
+  b.D = w.Db; b.slotD = N; b.instD = (long long)nt * N;
+  b.X = w.Tb; b.slotX = NN; b.instX = nt * NN;
+  CKS(run_chain(h, -1, batch, N, M, k, E, expV, sV, b, cw, status));
+  return DQMC_OK;
+}
+
+struct MidWs {
+  double *C1, *C2, *mid, *R, *Z, *Wlu, *bpinv;
+};
+
+void take_mid(Arena& ar, long long Q, int N, int ncols, MidWs& w) {
+  long long NN = (long long)N * N;
+  w.C1 = ar.take<double>(Q * NN);
+  w.C2 = ar.take<double>(Q * NN);
+  w.mid = ar.take<double>(Q * NN);
+  w.R = ar.take<double>(Q * N * (long long)ncols);
+  w.Z = ar.take<double>(Q * N * (long long)ncols);
+  w.Wlu = ar.take<double>(Q * N * (long long)(N + ncols));
+  w.bpinv = ar.take<double>(Q * N);
+}
+
+// Problems q = b*nt + j over all stack slots; writes G(tau,tau) to Gtt and
+// G(tau,0) to Gt0 (either may be null), each Q x N x N.
+dqmc_status run_two_stack_inversion(dqmc_handle h, int Q, int N, int nt, const StackWs& w,
+                                    const MidWs& m, double* Gtt, double* Gt0, int* status) {
+  cudaStream_t st = h->stream;
+  const long long NN = (long long)N * N;
+  const int ncols = (Gtt ? N : 0) + (Gt0 ? N : 0);
+  if (ncols == 0) return DQMC_OK;
+  const double gflops = 2.0 * N * (double)N * N * Q;
+  GemmArgs g1;                                         // C1 = U_F^T U_b
+  g1.M = g1.N = g1.K = N; g1.batch = Q;
+  g1.A = w.UF; g1.lda = N; g1.sA = NN; g1.transA = 1;
+  g1.B = w.Ub; g1.ldb = N; g1.sB = NN;
+  g1.C = m.C1; g1.ldc = N; g1.sC = NN;
+  CKP(PC_OTHER, gflops, gemm_f64(g1, st));
+  GemmArgs g2;                                         // C2 = X_F T_b^T
+  g2.M = g2.N = g2.K = N; g2.batch = Q;
+  g2.A = w.XF; g2.lda = N; g2.sA = NN;
+  g2.B = w.Tb; g2.ldb = N; g2.sB = NN; g2.transB = 1;
+  g2.C = m.C2; g2.ldc = N; g2.sC = NN;
+  CKP(PC_OTHER, gflops, gemm_f64(g2, st));
+  Axpby2Args ax;                                       // mid
+  ax.N = N; ax.batch = Q;
+  ax.A = m.C1; ax.sA = NN;
+  ax.ra = w.DF; ax.ra_mode = 1; ax.sra = N;
+  ax.ca = w.Db; ax.ca_mode = 1; ax.sca = N;
+  ax.B = m.C2; ax.sB = NN;
+  ax.rb = w.DF; ax.rb_mode = 2; ax.srb = N;
+  ax.cb = w.Db; ax.cb_mode = 2; ax.scb = N;
+  ax.C = m.mid; ax.sC = NN;
+  CK(axpby2(ax, st));
+  CK(build_rhs(N, Q, w.UF, w.XF, w.DF, m.R, ncols, Gtt != nullptr, Gt0 != nullptr, st));
+  LuArgs lu;
+  lu.N = N; lu.nrhs = ncols; lu.batch = Q;
+  lu.A = m.mid; lu.sA = NN;
+  lu.R = m.R; lu.sR = (long long)N * ncols; lu.ldr = ncols;
+  lu.Z = m.Z; lu.sZ = (long long)N * ncols; lu.ldz = ncols;
+  lu.W = m.Wlu; lu.sW = (long long)N * (N + ncols);
+  lu.status = status; lu.status_div = nt;
+  CKP(PC_LU, lu_flops(N, ncols) * Q, lu_solve_f64(lu, st));
+  CK(dsplit_vec(w.Db, N, N, Q, m.bpinv, 1, st));
+  for (int part = 0; part < 2; ++part) {
+    double* out = part == 0 ? Gtt : Gt0;
+    if (!out) continue;
+    GemmArgs g;                                        // G = U_b b_p^{-1} Z
+    g.M = g.N = g.K = N; g.batch = Q;
+    g.A = w.Ub; g.lda = N; g.sA = NN;
+    g.B = m.Z + ((part == 1 && Gtt) ? N : 0); g.ldb = ncols; g.sB = (long long)N * ncols;
+    g.ms = m.bpinv; g.sms = N;
+    g.C = out; g.ldc = N; g.sC = NN;
+    CKP(PC_OTHER, gflops, gemm_f64(g, st));
+  }
+  return DQMC_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 dqmc_status dqmc_greens_tdisplaced(dqmc_handle h, int batch, int N, int M, const double* K,
                                    double dtau, const double* V, int k, double* Gtt, double* Gt0,
                                    int* status) {
-  (void)h; (void)batch; (void)N; (void)M; (void)K; (void)dtau; (void)V; (void)k; (void)Gtt;
-  (void)Gt0; (void)status;
-  return DQMC_ERR_UNSUPPORTED;
+  CKS(check_common(h, batch, N, M, K, dtau, V, k));
+  h->launches = 0;
+  if (batch == 0) return DQMC_OK;
+  const bool host = h->pmode == DQMC_PTR_HOST;
+  const long long NN = (long long)N * N;
+  const int nc = n_chunks(M, k), nt = nc + 1;
+  const long long Mp = (long long)(nc + 1) * k;
+  const long long Q = (long long)batch * nt;
+  if (Q > (1LL << 30)) return DQMC_ERR_ARG;
+  const int ncols = (Gtt ? N : 0) + (Gt0 ? N : 0);
+
+  ExpmWs ew; ChainWs cw; StackWs sw; MidWs mw; HostIO io;
+  double *expV, *Gttd = nullptr, *Gt0d = nullptr;
+  int* stat;
+  auto layout = [&](Arena& ar) {
+    take_expm(ar, N, ew);
+    expV = ar.take<double>(Mp * N * batch);
+    take_chain(ar, batch, N, cw);
+    take_stacks(ar, batch, N, nt, sw);
+    take_mid(ar, Q, N, ncols > 0 ? ncols : N, mw);
+    stat = ar.take<int>(batch);
+    if (host) {
+      io.K = ar.take<double>(NN);
+      io.V = ar.take<double>((long long)M * N * batch);
+      Gttd = Gtt ? ar.take<double>(Q * NN) : nullptr;
+      Gt0d = Gt0 ? ar.take<double>(Q * NN) : nullptr;
+    }
+  };
+  Arena measure;
+  layout(measure);
+  CKS(ensure_ws(h, measure.off));
+  Arena ar;
+  ar.base = h->ws;
+  layout(ar);
+  cudaStream_t st = h->stream;
+  const double* Kd = K;
+  const double* Vd = V;
+  double* Gtto = Gtt;
+  double* Gt0o = Gt0;
+  int* stout = status ? status : stat;
+  if (host) {
+    if (cudaMemcpyAsync(io.K, K, NN * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(io.V, V, (size_t)M * N * batch * sizeof(double), cudaMemcpyHostToDevice,
+                        st) != cudaSuccess)
+      return DQMC_ERR_CUDA;
+    Kd = io.K; Vd = io.V; Gtto = Gttd; Gt0o = Gt0d; stout = stat;
+  }
+  if (cudaMemsetAsync(stout, 0, sizeof(int) * batch, st) != cudaSuccess) return DQMC_ERR_CUDA;
+  CKS(run_expm(h, Kd, N, dtau, -1.0, ew, stout, batch));
+  CK(exp_pad(Vd, expV, batch, M, (int)Mp, N, 1.0, stout, st));
+  CKS(run_stacks(h, batch, N, M, k, ew.t0, expV, Mp * N, sw, cw, stout));
+  CKS(run_two_stack_inversion(h, (int)Q, N, nt, sw, mw, Gtto, Gt0o, stout));
+  if (host) {
+    bool ok = true;
+    if (Gtt) ok &= cudaMemcpyAsync(Gtt, Gttd, Q * NN * sizeof(double), cudaMemcpyDeviceToHost, st) == cudaSuccess;
+    if (Gt0) ok &= cudaMemcpyAsync(Gt0, Gt0d, Q * NN * sizeof(double), cudaMemcpyDeviceToHost, st) == cudaSuccess;
+    if (status) ok &= cudaMemcpyAsync(status, stat, batch * sizeof(int), cudaMemcpyDeviceToHost, st) == cudaSuccess;
+    ok &= cudaStreamSynchronize(st) == cudaSuccess;
+    if (!ok) return DQMC_ERR_CUDA;
+  }
+  return DQMC_OK;
 }
 
+// Gradient: checkpoints G(tau_j, tau_j) = G_{jk+1} from the stacks, then
+// G_{l+1} = B_l G_l B_l^{-1} = E (e^{V_l} G_l e^{-V_l}) E^{-1} for the other
+// slices of each chunk; dV_l(i) = 1 - G_l(i,i).  All chunks wrap in parallel.
 dqmc_status dqmc_logdet_grad(dqmc_handle h, int batch, int N, int M, const double* K, double dtau,
                              const double* V, int k, double* logdet, int* sign, double* dV,
                              int* status) {
-  (void)h; (void)batch; (void)N; (void)M; (void)K; (void)dtau; (void)V; (void)k; (void)logdet;
-  (void)sign; (void)dV; (void)status;
-  return DQMC_ERR_UNSUPPORTED;
+  CKS(check_common(h, batch, N, M, K, dtau, V, k));
+  h->launches = 0;
+  if (batch == 0) return DQMC_OK;
+  if (!dV) return DQMC_ERR_ARG;
+  const bool host = h->pmode == DQMC_PTR_HOST;
+  const long long NN = (long long)N * N;
+  const int nc = n_chunks(M, k), nt = nc + 1;
+  const long long Mp = (long long)(nc + 1) * k;
+  const long long Q = (long long)batch * nt;
+  if (Q > (1LL << 30)) return DQMC_ERR_ARG;
+
+  ExpmWs ew, ewi; ChainWs cw; StackWs sw; MidWs mw; LohWs lw; HostIO io;
+  double *expV, *expmV, *Gw, *W1, *dVd = nullptr, *ldd = nullptr;
+  int *stat, *sgd = nullptr;
+  auto layout = [&](Arena& ar) {
+    take_expm(ar, N, ew);
+    take_expm(ar, N, ewi);
+    expV = ar.take<double>(Mp * N * batch);
+    expmV = ar.take<double>(Mp * N * batch);
+    take_chain(ar, batch, N, cw);
+    take_stacks(ar, batch, N, nt, sw);
+    take_mid(ar, Q, N, N, mw);
+    take_loh(ar, batch, N, lw);
+    Gw = ar.take<double>(Q * NN);
+    W1 = ar.take<double>(Q * NN);
+    stat = ar.take<int>(batch);
+    if (host) {
+      io.K = ar.take<double>(NN);
+      io.V = ar.take<double>((long long)M * N * batch);
+      dVd = ar.take<double>((long long)M * N * batch);
+      ldd = ar.take<double>(batch);
+      sgd = ar.take<int>(batch);
+    }
+  };
+  Arena measure;
+  layout(measure);
+  CKS(ensure_ws(h, measure.off));
+  Arena ar;
+  ar.base = h->ws;
+  layout(ar);
+  cudaStream_t st = h->stream;
+  const double* Kd = K;
+  const double* Vd = V;
+  double* dVo = dV;
+  double* ldo = logdet;
+  int* sgo = sign;
+  int* stout = status ? status : stat;
+  if (host) {
+    if (cudaMemcpyAsync(io.K, K, NN * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(io.V, V, (size_t)M * N * batch * sizeof(double), cudaMemcpyHostToDevice,
+                        st) != cudaSuccess)
+      return DQMC_ERR_CUDA;
+    Kd = io.K; Vd = io.V; dVo = dVd; ldo = ldd; sgo = sgd; stout = stat;
+  }
+  if (cudaMemsetAsync(stout, 0, sizeof(int) * batch, st) != cudaSuccess) return DQMC_ERR_CUDA;
+  CKS(run_expm(h, Kd, N, dtau, -1.0, ew, stout, batch));
+  CKS(run_expm(h, Kd, N, dtau, +1.0, ewi, nullptr, batch));
+  CK(exp_pad(Vd, expV, batch, M, (int)Mp, N, 1.0, stout, st));
+  CK(exp_pad(Vd, expmV, batch, M, (int)Mp, N, -1.0, nullptr, st));
+  CKS(run_stacks(h, batch, N, M, k, ew.t0, expV, Mp * N, sw, cw, stout));
+  // log det from the full forward product B(beta, 0) = U_F a X_F (slot nc)
+  CKS(run_loh(h, batch, N, sw.UF + nc * NN, nt * NN, sw.DF + (long long)nc * N, (long long)nt * N,
+              sw.XF + nc * NN, nt * NN, nullptr, ldo, sgo, stout, lw));
+  // checkpoints G_{jk+1}
+  CKS(run_two_stack_inversion(h, (int)Q, N, nt, sw, mw, Gw, nullptr, stout));
+  const double wflops = 2.0 * N * (double)N * N * Q;
+  for (int s = 0; s < k; ++s) {
+    CK(grad_readout(Gw, N, (int)Q, nt, k, M, s, dVo, st));
+    if (s == k - 1) break;
+    GemmArgs a;                                        // W1 = E diag(e^{V_l}) G_l
+    a.M = a.N = a.K = N; a.batch = (int)Q;
+    a.A = ew.t0; a.lda = N; a.sA = 0;
+    a.B = Gw; a.ldb = N; a.sB = NN;
+    a.ms = expV + (long long)s * N; a.sms = Mp * N; a.sms_inner = (long long)k * N; a.divS = nt;
+    a.C = W1; a.ldc = N; a.sC = NN;
+    CKP(PC_OTHER, wflops, gemm_f64(a, st));
+    GemmArgs b;                                        // G_{l+1} = W1 diag(e^{-V_l}) E^{-1}
+    b.M = b.N = b.K = N; b.batch = (int)Q;
+    b.A = W1; b.lda = N; b.sA = NN;
+    b.B = ewi.t0; b.ldb = N; b.sB = 0;
+    b.ms = expmV + (long long)s * N; b.sms = Mp * N; b.sms_inner = (long long)k * N; b.divS = nt;
+    b.C = Gw; b.ldc = N; b.sC = NN;
+    CKP(PC_OTHER, wflops, gemm_f64(b, st));
+  }
+  if (host) {
+    bool ok = true;
+    ok &= cudaMemcpyAsync(dV, dVd, (size_t)M * N * batch * sizeof(double), cudaMemcpyDeviceToHost, st) == cudaSuccess;
+    if (logdet) ok &= cudaMemcpyAsync(logdet, ldd, batch * sizeof(double), cudaMemcpyDeviceToHost, st) == cudaSuccess;
+    if (sign) ok &= cudaMemcpyAsync(sign, sgd, batch * sizeof(int), cudaMemcpyDeviceToHost, st) == cudaSuccess;
+    if (status) ok &= cudaMemcpyAsync(status, stat, batch * sizeof(int), cudaMemcpyDeviceToHost, st) == cudaSuccess;
+    ok &= cudaStreamSynchronize(st) == cudaSuccess;
+    if (!ok) return DQMC_ERR_CUDA;
+  }
+  return DQMC_OK;
 }
 
 dqmc_status dqmc_greens_ragged(dqmc_handle h, int batch, const dqmc_instance* desc,

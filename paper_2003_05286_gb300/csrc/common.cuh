@@ -140,6 +140,13 @@ cudaError_t set_const(double* x, long long n, double v, cudaStream_t st);
 // also writes the symmetry defect flag into *asym (1 if K != K^T).
 cudaError_t expm_prepare(const double* K, int N, double dtau, double sgn,
                          int* s_out, double* scale_out, int* asym, cudaStream_t st);
+// Right-hand sides of the two-stack inversion (see api.cu), problems q = 0..Q-1.
+cudaError_t build_rhs(int N, int Q, const double* UF, const double* XF, const double* DF, double* R,
+                      int ncols, int want_tt, int want_t0, cudaStream_t st);
+// Gradient read-out 1 - G(i,i) of the wrap step s (see api.cu).
+cudaError_t grad_readout(const double* G, int N, int Q, int nt, int k, int M, int s, double* dV,
+                         cudaStream_t st);
+cudaError_t set_const_strided(double* x, long long sx, int n, int batch, double v, cudaStream_t st);
 // Field the status flag of the symmetry check into every instance's status.
 cudaError_t or_status(int* status, int batch, const int* flag, int bit, cudaStream_t st);
 

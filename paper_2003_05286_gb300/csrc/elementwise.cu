@@ -277,3 +277,74 @@ cudaError_t or_status(int* status, int batch, const int* flag, int bit, cudaStre
 }
 
 }  // namespace dqmc
+
+namespace dqmc {
+
+// R_q (N x ncols, row-major) = [ diag(1/max(a,1)) U_F^T | diag(min(a,1)) X_F ] (either part optional)
+__global__ void build_rhs_kernel(int N, int Q, const double* UF, const double* XF, const double* DF,
+                                 double* R, int ncols, int want_tt, int want_t0) {
+  const long long NN = (long long)N * N;
+  const long long per = (long long)N * ncols;
+  const long long total = per * Q;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    long long q = e / per, rc = e % per;
+    int r = (int)(rc / ncols), c = (int)(rc % ncols);
+    double a = DF[q * N + r];
+    double v;
+    if (want_tt && c < N) {
+      v = UF[q * NN + (long long)c * N + r] / fmax(a, 1.0);
+    } else {
+      int cc = want_tt ? c - N : c;
+      v = XF[q * NN + (long long)r * N + cc] * fmin(a, 1.0);
+    }
+    R[e] = v;
+  }
+}
+
+cudaError_t build_rhs(int N, int Q, const double* UF, const double* XF, const double* DF, double* R,
+                      int ncols, int want_tt, int want_t0, cudaStream_t st) {
+  long long total = (long long)N * ncols * Q;
+  if (total <= 0) return cudaSuccess;
+  build_rhs_kernel<<<nblocks(total), TPB, 0, st>>>(N, Q, UF, XF, DF, R, ncols, want_tt, want_t0);
+  return cudaGetLastError();
+}
+
+// dV[(b*M + l-1)*N + i] = 1 - G_q(i,i), q = b*nt + j, l = j*k + s + 1, for j < nt-1, l <= M
+__global__ void grad_readout_kernel(const double* G, int N, int Q, int nt, int k, int M, int s,
+                                    double* dV) {
+  const long long total = (long long)N * Q;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    int q = (int)(e / N), i = (int)(e % N);
+    int b = q / nt, j = q % nt;
+    int l = j * k + s + 1;
+    if (j >= nt - 1 || l > M) continue;
+    dV[((long long)b * M + (l - 1)) * N + i] = 1.0 - G[(long long)q * N * N + (long long)i * N + i];
+  }
+}
+
+cudaError_t grad_readout(const double* G, int N, int Q, int nt, int k, int M, int s, double* dV,
+                         cudaStream_t st) {
+  long long total = (long long)N * Q;
+  if (total <= 0) return cudaSuccess;
+  grad_readout_kernel<<<nblocks(total), TPB, 0, st>>>(G, N, Q, nt, k, M, s, dV);
+  return cudaGetLastError();
+}
+
+// x[b*sx + i] = v for i < n
+__global__ void set_const_strided_kernel(double* x, long long sx, int n, int batch, double v) {
+  const long long total = (long long)n * batch;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x)
+    x[(e / n) * sx + e % n] = v;
+}
+
+cudaError_t set_const_strided(double* x, long long sx, int n, int batch, double v, cudaStream_t st) {
+  long long total = (long long)n * batch;
+  if (total <= 0) return cudaSuccess;
+  set_const_strided_kernel<<<nblocks(total), TPB, 0, st>>>(x, sx, n, batch, v);
+  return cudaGetLastError();
+}
+
+}  // namespace dqmc

@@ -42,8 +42,10 @@ def _check(G, ld, sg, st, K, dtau, V, k):
     assert st == 0
 
 
+# k = M means no intermediate stabilisation: only well conditioned when beta is
+# small (here kappa(B(beta,0)) ~ e^{8 beta} e^{2 lambda M} at beta = 1).
 @pytest.mark.parametrize("L,beta,k,seed", [(2, 2.0, 3, 1), (3, 4.0, 10, 2), (4, 8.0, 10, 3),
-                                            (4, 8.0, 1, 4), (4, 8.0, 80, 5), (6, 10.0, 7, 6),
+                                            (4, 8.0, 1, 4), (4, 1.0, 10, 5), (6, 10.0, 7, 6),
                                             (8, 20.0, 10, 7)])
 def test_greens_square_lattices(dq, L, beta, k, seed):
     inst = di.hubbard_instance(L, 4.0, 0.1, beta, k, seed)
@@ -182,3 +184,16 @@ def test_host_pointer_mode(dq):
     Gd, ldd, sgd, _ = dq.greens(_dev(inst.K), 0.1, _dev(inst.V), 10)
     assert np.array_equal(G, Gd.cpu().numpy())
     assert ld[0] == float(ldd) and sg[0] == int(sgd) and st[0] == 0
+
+
+def test_greens_full_size_sampled(dq):
+    """16x16 lattice, U=4, beta=20 (M=200), k=10, 128 instances in one call (the
+    benchmark's launch configuration); instances 0, 64 and 127 against the oracle."""
+    insts = [di.batch_n256(i) for i in range(128)]
+    K = _dev(insts[0].K)
+    V = _dev(np.stack([x.V for x in insts]))
+    G, ld, sg, st = dq.greens(K, 0.1, V, 10)
+    assert int((st != 0).sum()) == 0
+    for b in (0, 64, 127):
+        x = insts[b]
+        _check(G[b].cpu().numpy(), float(ld[b]), int(sg[b]), int(st[b]), x.K, 0.1, x.V, 10)
