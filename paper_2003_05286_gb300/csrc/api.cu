@@ -39,6 +39,9 @@ struct dqmc_handle_s {
   char* ws = nullptr;
   size_t ws_bytes = 0;
   long long launches = 0;
+  cudaStream_t cur = nullptr;              // stream the helpers launch on
+  std::vector<cudaStream_t> aux;           // extra streams of the ragged path
+  std::vector<cudaEvent_t> auxev;
   // profiler
   bool prof = false;
   std::vector<ProfRec> pending;
@@ -102,7 +105,7 @@ cudaEvent_t pool_event(dqmc_handle h) {
 // Folds finished event pairs into the per-class totals (synchronises the stream).
 void prof_collect(dqmc_handle h) {
   if (h->pending.empty()) return;
-  cudaStreamSynchronize(h->stream);
+  cudaDeviceSynchronize();
   for (auto& r : h->pending) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, r.e0, r.e1) == cudaSuccess) {
@@ -125,12 +128,12 @@ void prof_collect(dqmc_handle h) {
     if (h->prof) {                                                \
       _r.e0 = pool_event(h);                                      \
       _r.e1 = pool_event(h);                                      \
-      cudaEventRecord(_r.e0, h->stream);                          \
+      cudaEventRecord(_r.e0, h->cur);                             \
     }                                                             \
     cudaError_t _e = (expr);                                      \
     h->launches++;                                                \
     if (h->prof) {                                                \
-      cudaEventRecord(_r.e1, h->stream);                          \
+      cudaEventRecord(_r.e1, h->cur);                             \
       h->pending.push_back(_r);                                   \
       if (h->pending.size() > 4096) prof_collect(h);              \
     }                                                             \
@@ -166,7 +169,7 @@ void take_expm(Arena& ar, int N, ExpmWs& w) {
 // Result ends in w.t0 (the step counts are even).
 dqmc_status run_expm(dqmc_handle h, const double* K, int N, double dtau, double sgn,
                      const ExpmWs& w, int* status, int batch) {
-  cudaStream_t st = h->stream;
+  cudaStream_t st = h->cur;
   CK(expm_prepare(K, N, dtau, sgn, w.s, w.scale, w.asym, st));
   CK(set_identity(w.t0, 0, N, 1, st));
   double* cur = w.t0;
@@ -240,10 +243,12 @@ inline double* slotX(const Slots& s, int slot) {
   return s.X + slot * s.slotX;
 }
 
+// lim (nullable, per instance): chain length M_b of ragged batches; slices
+// past M_b are copied through and finished instances skip the QR and X update.
 dqmc_status run_chain(dqmc_handle h, int dir, int batch, int N, int M, int k, const double* E,
                       const double* expV, long long sV, const Slots& s, const ChainWs& w,
-                      int* status) {
-  cudaStream_t st = h->stream;
+                      int* status, const int* lim = nullptr) {
+  cudaStream_t st = h->cur;
   const int nc = n_chunks(M, k);
   const long long NN = (long long)N * N;
   for (int step = 0; step < nc; ++step) {
@@ -264,6 +269,7 @@ dqmc_status run_chain(dqmc_handle h, int dir, int batch, int N, int M, int k, co
       g.A = E; g.lda = N; g.sA = 0;
       g.B = prev; g.ldb = N; g.sB = sprev;
       g.C = bufs[nb]; g.ldc = N; g.sC = NN;
+      g.lim = lim; g.lim_at = l;
       if (dir > 0) {
         g.ms = expV + (long long)(l - 1) * N; g.sms = sV;      // E diag(e^{V_l}) A
       } else {
@@ -286,6 +292,7 @@ dqmc_status run_chain(dqmc_handle h, int dir, int batch, int N, int M, int k, co
     q.T = w.T; q.sT = NN;
     q.perm = w.perm; q.sperm = N;
     q.status = status;
+    q.lim = lim; q.lim_at = lo;
     CKP(PC_QRP, 8.0 / 3.0 * N * N * (double)N * batch, qrp_f64(q, st));
     // a4: X_dst = T' X_src[perm]
     GemmArgs g;
@@ -295,6 +302,7 @@ dqmc_status run_chain(dqmc_handle h, int dir, int batch, int N, int M, int k, co
     g.B = slotX(s, src); g.ldb = N; g.sB = s.instX;
     g.permB = w.perm; g.sperm = N;
     g.C = slotX(s, dst); g.ldc = N; g.sC = s.instX;
+    g.lim = lim; g.lim_at = lo;
     CKP(PC_XUPD, (double)N * N * (double)N * batch, gemm_f64(g, st));
   }
   return DQMC_OK;
@@ -326,7 +334,7 @@ void take_loh(Arena& ar, int batch, int N, LohWs& w) {
 dqmc_status run_loh(dqmc_handle h, int batch, int N, const double* U, long long sU,
                     const double* D, long long sD, const double* X, long long sX, double* G,
                     double* logdet, int* sign, int* status, const LohWs& w) {
-  cudaStream_t st = h->stream;
+  cudaStream_t st = h->cur;
   const long long NN = (long long)N * N;
   CK(dsplit_vec(D, sD, N, batch, w.Dpinv, 1, st));   // D_p^{-1}
   LuArgs l1;
@@ -418,6 +426,8 @@ dqmc_status dqmc_destroy(dqmc_handle h) {
   }
   prof_collect(h);
   for (auto e : h->pool) cudaEventDestroy(e);
+  for (auto s : h->aux) { cudaStreamSynchronize(s); cudaStreamDestroy(s); }
+  for (auto e : h->auxev) cudaEventDestroy(e);
   delete h;
   return DQMC_OK;
 }
@@ -490,6 +500,7 @@ static dqmc_status greens_impl(dqmc_handle h, int batch, int N, int M, const dou
                                int* sign, int* status) {
   CKS(check_common(h, batch, N, M, K, dtau, V, k));
   h->launches = 0;
+  h->cur = h->stream;
   if (batch == 0) return DQMC_OK;
   const bool host = h->pmode == DQMC_PTR_HOST;
   const long long NN = (long long)N * N;
@@ -526,7 +537,7 @@ static dqmc_status greens_impl(dqmc_handle h, int batch, int N, int M, const dou
   Arena ar;
   ar.base = h->ws;
   layout(ar, ew, cw, lw, E, expV, U, D, X0, X1, stat, io, Gd, ldd, sgd);
-  cudaStream_t st = h->stream;
+  cudaStream_t st = h->cur;
 
   const double* Kd = K;
   const double* Vd = V;
@@ -627,7 +638,7 @@ void take_stacks(Arena& ar, int batch, int N, int nt, StackWs& w) {
 dqmc_status run_stacks(dqmc_handle h, int batch, int N, int M, int k, const double* E,
                        const double* expV, long long sV, const StackWs& w, const ChainWs& cw,
                        int* status) {
-  cudaStream_t st = h->stream;
+  cudaStream_t st = h->cur;
   const int nc = n_chunks(M, k), nt = nc + 1;
   const long long NN = (long long)N * N;
   // forward slot 0 and backward slot nc are the identity decomposition
@@ -669,7 +680,7 @@ void take_mid(Arena& ar, long long Q, int N, int ncols, MidWs& w) {
 // G(tau,0) to Gt0 (either may be null), each Q x N x N.
 dqmc_status run_two_stack_inversion(dqmc_handle h, int Q, int N, int nt, const StackWs& w,
                                     const MidWs& m, double* Gtt, double* Gt0, int* status) {
-  cudaStream_t st = h->stream;
+  cudaStream_t st = h->cur;
   const long long NN = (long long)N * N;
   const int ncols = (Gtt ? N : 0) + (Gt0 ? N : 0);
   if (ncols == 0) return DQMC_OK;
@@ -729,6 +740,7 @@ dqmc_status dqmc_greens_tdisplaced(dqmc_handle h, int batch, int N, int M, const
                                    int* status) {
   CKS(check_common(h, batch, N, M, K, dtau, V, k));
   h->launches = 0;
+  h->cur = h->stream;
   if (batch == 0) return DQMC_OK;
   const bool host = h->pmode == DQMC_PTR_HOST;
   const long long NN = (long long)N * N;
@@ -761,7 +773,7 @@ dqmc_status dqmc_greens_tdisplaced(dqmc_handle h, int batch, int N, int M, const
   Arena ar;
   ar.base = h->ws;
   layout(ar);
-  cudaStream_t st = h->stream;
+  cudaStream_t st = h->cur;
   const double* Kd = K;
   const double* Vd = V;
   double* Gtto = Gtt;
@@ -798,6 +810,7 @@ dqmc_status dqmc_logdet_grad(dqmc_handle h, int batch, int N, int M, const doubl
                              int* status) {
   CKS(check_common(h, batch, N, M, K, dtau, V, k));
   h->launches = 0;
+  h->cur = h->stream;
   if (batch == 0) return DQMC_OK;
   if (!dV) return DQMC_ERR_ARG;
   const bool host = h->pmode == DQMC_PTR_HOST;
@@ -836,7 +849,7 @@ dqmc_status dqmc_logdet_grad(dqmc_handle h, int batch, int N, int M, const doubl
   Arena ar;
   ar.base = h->ws;
   layout(ar);
-  cudaStream_t st = h->stream;
+  cudaStream_t st = h->cur;
   const double* Kd = K;
   const double* Vd = V;
   double* dVo = dV;
@@ -892,12 +905,154 @@ dqmc_status dqmc_logdet_grad(dqmc_handle h, int batch, int N, int M, const doubl
   return DQMC_OK;
 }
 
+// Ragged batch: instances are grouped by (N, k, dtau, K); each group runs the
+// uniform equal-time path with per-instance chain lengths M_b on its own
+// stream, so that small-N groups (latency-bound QR) overlap with large-N
+// groups (FP64-bound products).  Results are scattered to the pools.
 dqmc_status dqmc_greens_ragged(dqmc_handle h, int batch, const dqmc_instance* desc,
                                const double* K_pool, const double* V_pool, double* G_pool,
                                double* logdet, int* sign, int* status) {
-  (void)h; (void)batch; (void)desc; (void)K_pool; (void)V_pool; (void)G_pool; (void)logdet;
-  (void)sign; (void)status;
-  return DQMC_ERR_UNSUPPORTED;
+  if (!h || batch < 0) return DQMC_ERR_ARG;
+  h->launches = 0;
+  h->cur = h->stream;
+  if (batch == 0) return DQMC_OK;
+  if (!desc || !K_pool || !V_pool) return DQMC_ERR_ARG;
+  if (h->pmode == DQMC_PTR_HOST) return DQMC_ERR_UNSUPPORTED;
+  for (int b = 0; b < batch; ++b) {
+    const dqmc_instance& d = desc[b];
+    if (d.N < 1 || d.N > 1024 || d.M < 1 || d.k < 1 || d.k > d.M || !(d.dtau >= 0.0) ||
+        d.off_K < 0 || d.off_V < 0 || d.off_G < 0)
+      return DQMC_ERR_ARG;
+  }
+  // ---- groups ---------------------------------------------------------------
+  struct Group {
+    int N, k;
+    double dtau;
+    long long offK;
+    std::vector<int> idx;
+    int Mmax = 0;
+  };
+  std::vector<Group> groups;
+  for (int b = 0; b < batch; ++b) {
+    const dqmc_instance& d = desc[b];
+    Group* g = nullptr;
+    for (auto& x : groups)
+      if (x.N == d.N && x.k == d.k && x.dtau == d.dtau && x.offK == d.off_K) { g = &x; break; }
+    if (!g) {
+      groups.push_back(Group{d.N, d.k, d.dtau, d.off_K, {}, 0});
+      g = &groups.back();
+    }
+    g->idx.push_back(b);
+    if (d.M > g->Mmax) g->Mmax = d.M;
+  }
+  // ---- workspace: one region per group ----------------------------------------
+  struct GroupWs {
+    ExpmWs ew; ChainWs cw; LohWs lw;
+    double *expV, *U, *D, *X0, *X1, *G, *ld;
+    int *sg, *st, *Mb, *gidx;
+    long long *offV, *offG;
+  };
+  std::vector<GroupWs> gw(groups.size());
+  auto layout = [&](Arena& ar) {
+    for (size_t i = 0; i < groups.size(); ++i) {
+      const Group& g = groups[i];
+      GroupWs& w = gw[i];
+      const int nb = (int)g.idx.size(), N = g.N;
+      const long long NN = (long long)N * N;
+      const long long Mp = (long long)(n_chunks(g.Mmax, g.k) + 1) * g.k;
+      take_expm(ar, N, w.ew);
+      w.expV = ar.take<double>(Mp * N * nb);
+      w.U = ar.take<double>(NN * nb);
+      w.D = ar.take<double>((long long)N * nb);
+      w.X0 = ar.take<double>(NN * nb);
+      w.X1 = ar.take<double>(NN * nb);
+      take_chain(ar, nb, N, w.cw);
+      take_loh(ar, nb, N, w.lw);
+      w.G = ar.take<double>(NN * nb);
+      w.ld = ar.take<double>(nb);
+      w.sg = ar.take<int>(nb);
+      w.st = ar.take<int>(nb);
+      w.Mb = ar.take<int>(nb);
+      w.gidx = ar.take<int>(nb);
+      w.offV = ar.take<long long>(nb);
+      w.offG = ar.take<long long>(nb);
+    }
+  };
+  Arena measure;
+  layout(measure);
+  CKS(ensure_ws(h, measure.off));
+  Arena ar;
+  ar.base = h->ws;
+  layout(ar);
+  // ---- streams ---------------------------------------------------------------
+  const size_t nstreams = groups.size() < 8 ? groups.size() : 8;
+  while (h->aux.size() < nstreams) {
+    cudaStream_t s = nullptr;
+    cudaEvent_t e = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+      return DQMC_ERR_CUDA;
+    h->aux.push_back(s);
+    h->auxev.push_back(e);
+  }
+  cudaEvent_t fork = nullptr;
+  if (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess) return DQMC_ERR_CUDA;
+  // per-group index tables (uploaded on the main stream, before the fork)
+  for (size_t i = 0; i < groups.size(); ++i) {
+    const Group& g = groups[i];
+    const int nb = (int)g.idx.size();
+    std::vector<int> Mb(nb), gidx(nb);
+    std::vector<long long> offV(nb), offG(nb);
+    for (int j = 0; j < nb; ++j) {
+      const dqmc_instance& d = desc[g.idx[j]];
+      Mb[j] = d.M; gidx[j] = g.idx[j]; offV[j] = d.off_V; offG[j] = d.off_G;
+    }
+    bool ok = cudaMemcpyAsync(gw[i].Mb, Mb.data(), nb * sizeof(int), cudaMemcpyHostToDevice, h->stream) == cudaSuccess &&
+              cudaMemcpyAsync(gw[i].gidx, gidx.data(), nb * sizeof(int), cudaMemcpyHostToDevice, h->stream) == cudaSuccess &&
+              cudaMemcpyAsync(gw[i].offV, offV.data(), nb * sizeof(long long), cudaMemcpyHostToDevice, h->stream) == cudaSuccess &&
+              cudaMemcpyAsync(gw[i].offG, offG.data(), nb * sizeof(long long), cudaMemcpyHostToDevice, h->stream) == cudaSuccess &&
+              cudaMemsetAsync(gw[i].st, 0, nb * sizeof(int), h->stream) == cudaSuccess;
+    if (!ok) { cudaEventDestroy(fork); return DQMC_ERR_CUDA; }
+  }
+  cudaStreamSynchronize(h->stream);   // host staging vectors go out of scope per group
+  cudaEventRecord(fork, h->stream);
+  for (size_t s = 0; s < nstreams; ++s) cudaStreamWaitEvent(h->aux[s], fork, 0);
+  dqmc_status rc = DQMC_OK;
+  for (size_t i = 0; i < groups.size() && rc == DQMC_OK; ++i) {
+    const Group& g = groups[i];
+    GroupWs& w = gw[i];
+    const int nb = (int)g.idx.size(), N = g.N, k = g.k;
+    const long long NN = (long long)N * N;
+    const int ncmax = n_chunks(g.Mmax, k);
+    const long long Mp = (long long)(ncmax + 1) * k;
+    h->cur = h->aux[i % nstreams];
+    cudaStream_t st = h->cur;
+    rc = [&]() -> dqmc_status {
+      CKS(run_expm(h, K_pool + g.offK, N, g.dtau, -1.0, w.ew, w.st, nb));
+      CK(exp_gather(V_pool, w.offV, w.Mb, nb, (int)Mp, N, w.expV, w.st, st));
+      CK(set_identity(w.U, NN, N, nb, st));
+      CK(set_const(w.D, (long long)N * nb, 1.0, st));
+      CK(set_identity(w.X0, NN, N, nb, st));
+      Slots sl;
+      sl.U = w.U; sl.slotU = 0; sl.instU = NN;
+      sl.D = w.D; sl.slotD = 0; sl.instD = N;
+      sl.X = w.X0; sl.slotX = 0; sl.instX = NN;
+      sl.X2 = w.X1;
+      CKS(run_chain(h, +1, nb, N, g.Mmax, k, w.ew.t0, w.expV, Mp * N, sl, w.cw, w.st, w.Mb));
+      const double* Xf = (ncmax & 1) ? w.X1 : w.X0;
+      CKS(run_loh(h, nb, N, w.U, NN, w.D, N, Xf, NN, G_pool ? w.G : nullptr, w.ld, w.sg, w.st, w.lw));
+      if (G_pool) CK(scatter_mats(w.G, w.offG, N, nb, G_pool, st));
+      CK(scatter_scalars(w.gidx, nb, w.ld, w.sg, w.st, logdet, sign, status, st));
+      return DQMC_OK;
+    }();
+  }
+  for (size_t s = 0; s < nstreams; ++s) {
+    cudaEventRecord(h->auxev[s], h->aux[s]);
+    cudaStreamWaitEvent(h->stream, h->auxev[s], 0);
+  }
+  cudaEventDestroy(fork);
+  h->cur = h->stream;
+  return rc;
 }
 
 }  // extern "C"

@@ -65,7 +65,7 @@ struct QrpArgs {
   double* T = nullptr; long long sT = 0;
   int* perm = nullptr; long long sperm = 0;
   int* status = nullptr; int status_div = 1;          // nullable
-  const int* active = nullptr;                        // nullable: instance enabled flags
+  const int* lim = nullptr; int lim_at = 0;           // skip instance b when lim[b] < lim_at
 };
 
 cudaError_t qrp_f64(const QrpArgs& a, cudaStream_t st);
@@ -147,6 +147,14 @@ cudaError_t build_rhs(int N, int Q, const double* UF, const double* XF, const do
 cudaError_t grad_readout(const double* G, int N, int Q, int nt, int k, int M, int s, double* dV,
                          cudaStream_t st);
 cudaError_t set_const_strided(double* x, long long sx, int n, int batch, double v, cudaStream_t st);
+// Ragged batches (ragged.cu).
+cudaError_t exp_gather(const double* V, const long long* offV, const int* Mb, int batch, int Mp,
+                       int N, double* out, int* status, cudaStream_t st);
+cudaError_t scatter_mats(const double* src, const long long* offG, int N, int batch, double* dst,
+                         cudaStream_t st);
+cudaError_t scatter_scalars(const int* gidx, int batch, const double* ld, const int* sg,
+                            const int* stt, double* ld_out, int* sg_out, int* st_out,
+                            cudaStream_t st);
 // Field the status flag of the symmetry check into every instance's status.
 cudaError_t or_status(int* status, int batch, const int* flag, int bit, cudaStream_t st);
 

@@ -113,12 +113,26 @@ __global__ void __launch_bounds__(NT) lu_kernel(const LuArgs a) {
         double* col = W + c;
         const double pj = col[(long long)j * Wd];
         if (pj == 0.0) continue;
+        // col[r] -= l_r * pj, 8 rows per batch, next batch loaded before the stores
         int r = j + 1;
-        for (; r + 1 < N; r += 2) {
-          col[(long long)r * Wd] = fma(-lbuf[r], pj, col[(long long)r * Wd]);
-          col[(long long)(r + 1) * Wd] = fma(-lbuf[r + 1], pj, col[(long long)(r + 1) * Wd]);
+        if (r + 7 < N) {
+          double x[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) x[i] = col[(long long)(r + i) * Wd];
+          for (; r + 15 < N; r += 8) {
+            double y[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) y[i] = col[(long long)(r + 8 + i) * Wd];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) col[(long long)(r + i) * Wd] = fma(-lbuf[r + i], pj, x[i]);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) x[i] = y[i];
+          }
+#pragma unroll
+          for (int i = 0; i < 8; ++i) col[(long long)(r + i) * Wd] = fma(-lbuf[r + i], pj, x[i]);
+          r += 8;
         }
-        if (r < N) col[(long long)r * Wd] = fma(-lbuf[r], pj, col[(long long)r * Wd]);
+        for (; r < N; ++r) col[(long long)r * Wd] = fma(-lbuf[r], pj, col[(long long)r * Wd]);
       }
       __syncthreads();
     }
@@ -129,14 +143,19 @@ __global__ void __launch_bounds__(NT) lu_kernel(const LuArgs a) {
       double* col = W + N + c;
       for (int i = N - 1; i >= 0; --i) {
         const double* urow = W + (long long)i * Wd;
-        double s0 = col[(long long)i * Wd], s1 = 0.0;
+        double s0 = col[(long long)i * Wd], s1 = 0.0, s2 = 0.0, s3 = 0.0;
         int m = i + 1;
-        for (; m + 1 < N; m += 2) {
-          s0 = fma(-urow[m], col[(long long)m * Wd], s0);
-          s1 = fma(-urow[m + 1], col[(long long)(m + 1) * Wd], s1);
+        for (; m + 7 < N; m += 8) {
+          double x[8], u[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) { x[q] = col[(long long)(m + q) * Wd]; u[q] = urow[m + q]; }
+          s0 = fma(-u[0], x[0], s0); s1 = fma(-u[1], x[1], s1);
+          s2 = fma(-u[2], x[2], s2); s3 = fma(-u[3], x[3], s3);
+          s0 = fma(-u[4], x[4], s0); s1 = fma(-u[5], x[5], s1);
+          s2 = fma(-u[6], x[6], s2); s3 = fma(-u[7], x[7], s3);
         }
-        if (m < N) s0 = fma(-urow[m], col[(long long)m * Wd], s0);
-        col[(long long)i * Wd] = (s0 + s1) * dinv[i];
+        for (; m < N; ++m) s0 = fma(-urow[m], col[(long long)m * Wd], s0);
+        col[(long long)i * Wd] = ((s0 + s1) + (s2 + s3)) * dinv[i];
       }
     }
     __syncthreads();

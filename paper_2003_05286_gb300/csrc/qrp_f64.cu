@@ -84,6 +84,71 @@ __device__ __forceinline__ double block_sum(double v, double* sd) {
   return v;
 }
 
+// Strided column kernels shared by the QR steps.  One thread walks a column of
+// a row-major matrix (stride ld); loads are issued 8 at a time and the next
+// batch is loaded before the current one is stored, so that a thread keeps
+// 8-16 L2 requests in flight instead of one (the compiler cannot reorder a
+// load above a store to the same array on its own).
+// dot = sum_{r=r0}^{n-1} v[r] * col[r*ld]
+__device__ __forceinline__ double col_dot(const double* __restrict__ col, long long ld,
+                                          const double* __restrict__ v, int r0, int n) {
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int r = r0;
+  for (; r + 7 < n; r += 8) {
+    double x[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = col[(long long)(r + i) * ld];
+    a0 = fma(v[r + 0], x[0], a0); a1 = fma(v[r + 1], x[1], a1);
+    a2 = fma(v[r + 2], x[2], a2); a3 = fma(v[r + 3], x[3], a3);
+    a0 = fma(v[r + 4], x[4], a0); a1 = fma(v[r + 5], x[5], a1);
+    a2 = fma(v[r + 6], x[6], a2); a3 = fma(v[r + 7], x[7], a3);
+  }
+  for (; r < n; ++r) a0 = fma(v[r], col[(long long)r * ld], a0);
+  return (a0 + a1) + (a2 + a3);
+}
+
+// col[r*ld] -= v[r] * w  for r in [r0, n)
+__device__ __forceinline__ void col_axpy(double* __restrict__ col, long long ld,
+                                         const double* __restrict__ v, double w, int r0, int n) {
+  int r = r0;
+  if (r + 7 < n) {
+    double x[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = col[(long long)(r + i) * ld];
+    for (; r + 15 < n; r += 8) {
+      double y[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) y[i] = col[(long long)(r + 8 + i) * ld];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) col[(long long)(r + i) * ld] = fma(-v[r + i], w, x[i]);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) x[i] = y[i];
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) col[(long long)(r + i) * ld] = fma(-v[r + i], w, x[i]);
+    r += 8;
+  }
+  for (; r < n; ++r) col[(long long)r * ld] = fma(-v[r], w, col[(long long)r * ld]);
+}
+
+// sum_{r=r0}^{n-1} col[r*ld]^2
+__device__ __forceinline__ double col_sumsq(const double* __restrict__ col, long long ld, int r0,
+                                            int n) {
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int r = r0;
+  for (; r + 7 < n; r += 8) {
+    double x[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = col[(long long)(r + i) * ld];
+    a0 = fma(x[0], x[0], a0); a1 = fma(x[1], x[1], a1);
+    a2 = fma(x[2], x[2], a2); a3 = fma(x[3], x[3], a3);
+    a0 = fma(x[4], x[4], a0); a1 = fma(x[5], x[5], a1);
+    a2 = fma(x[6], x[6], a2); a3 = fma(x[7], x[7], a3);
+  }
+  for (; r < n; ++r) { double x = col[(long long)r * ld]; a0 = fma(x, x, a0); }
+  return (a0 + a1) + (a2 + a3);
+}
+
 }  // namespace
 
 template <int NT>
@@ -106,7 +171,7 @@ __global__ void __launch_bounds__(NT) qrp_kernel(const QrpArgs a) {
   const int tid = threadIdx.x;
 
   for (int b = blockIdx.x; b < a.batch; b += gridDim.x) {
-    if (a.active && !a.active[b]) continue;
+    if (a.lim && a.lim[b] < a.lim_at) continue;   // chain of this instance already finished
     const double* __restrict__ A = a.A + (long long)b * a.sA;
     double* __restrict__ W = a.W + (long long)b * a.sW;
     double* __restrict__ U = a.U + (long long)b * a.sU;
@@ -133,16 +198,9 @@ __global__ void __launch_bounds__(NT) qrp_kernel(const QrpArgs a) {
     if (bad) atomicOr(&s_flag, DQMC_STATUS_NONFINITE_SCALE);
     __syncthreads();
     for (int c = tid; c < N; c += NT) {
-      double s0 = 0.0, s1 = 0.0;
-      int r = 0;
-      for (; r + 1 < N; r += 2) {
-        double x0 = W[(long long)r * N + c], x1 = W[(long long)(r + 1) * N + c];
-        s0 = fma(x0, x0, s0);
-        s1 = fma(x1, x1, s1);
-      }
-      if (r < N) { double x0 = W[(long long)r * N + c]; s0 = fma(x0, x0, s0); }
-      nrm2[c] = s0 + s1;
-      ref2[c] = s0 + s1;
+      double s0 = col_sumsq(W + c, N, 0, N);
+      nrm2[c] = s0;
+      ref2[c] = s0;
     }
     __syncthreads();
 
@@ -207,25 +265,14 @@ __global__ void __launch_bounds__(NT) qrp_kernel(const QrpArgs a) {
       if (tau != 0.0) {
         for (int c = j + 1 + tid; c < N; c += NT) {
           double* col = W + c;
-          double w0 = col[(long long)j * N], w1 = 0.0;
-          int r = j + 1;
-          for (; r + 3 < N; r += 4) {
-            w0 = fma(vbuf[r], col[(long long)r * N], w0);
-            w1 = fma(vbuf[r + 1], col[(long long)(r + 1) * N], w1);
-            w0 = fma(vbuf[r + 2], col[(long long)(r + 2) * N], w0);
-            w1 = fma(vbuf[r + 3], col[(long long)(r + 3) * N], w1);
-          }
-          for (; r < N; ++r) w0 = fma(vbuf[r], col[(long long)r * N], w0);
-          const double w = (w0 + w1) * tau;
+          const double w = (col[(long long)j * N] + col_dot(col, N, vbuf, j + 1, N)) * tau;
           const double rjc = col[(long long)j * N] - w;
           col[(long long)j * N] = rjc;
-          for (r = j + 1; r < N; ++r) col[(long long)r * N] = fma(-vbuf[r], w, col[(long long)r * N]);
+          col_axpy(col, N, vbuf, w, j + 1, N);
           double n2 = fma(-rjc, rjc, nrm2[c]);
           if (n2 <= 1.4901161193847656e-8 * ref2[c]) {
-            double s0 = 0.0;
-            for (r = j + 1; r < N; ++r) { double x = col[(long long)r * N]; s0 = fma(x, x, s0); }
-            n2 = s0;
-            ref2[c] = s0;
+            n2 = col_sumsq(col, N, j + 1, N);
+            ref2[c] = n2;
           }
           nrm2[c] = n2;
         }
@@ -234,10 +281,8 @@ __global__ void __launch_bounds__(NT) qrp_kernel(const QrpArgs a) {
           double rjc = W[(long long)j * N + c];
           double n2 = fma(-rjc, rjc, nrm2[c]);
           if (n2 <= 1.4901161193847656e-8 * ref2[c]) {
-            double s0 = 0.0;
-            for (int r = j + 1; r < N; ++r) { double x = W[(long long)r * N + c]; s0 = fma(x, x, s0); }
-            n2 = s0;
-            ref2[c] = s0;
+            n2 = col_sumsq(W + c, N, j + 1, N);
+            ref2[c] = n2;
           }
           nrm2[c] = n2;
         }
@@ -278,15 +323,8 @@ __global__ void __launch_bounds__(NT) qrp_kernel(const QrpArgs a) {
       __syncthreads();
       for (int c = j + tid; c < N; c += NT) {
         double* col = U + c;
-        double w0 = 0.0, w1 = 0.0;
-        int r = j;
-        for (; r + 1 < N; r += 2) {
-          w0 = fma(vbuf[r], col[(long long)r * N], w0);
-          w1 = fma(vbuf[r + 1], col[(long long)(r + 1) * N], w1);
-        }
-        if (r < N) w0 = fma(vbuf[r], col[(long long)r * N], w0);
-        const double w = (w0 + w1) * tau;
-        for (r = j; r < N; ++r) col[(long long)r * N] = fma(-vbuf[r], w, col[(long long)r * N]);
+        const double w = col_dot(col, N, vbuf, j, N) * tau;
+        col_axpy(col, N, vbuf, w, j, N);
       }
       __syncthreads();
     }

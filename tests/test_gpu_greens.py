@@ -108,7 +108,8 @@ def test_greens_brute_force_small(dq):
     bf = ex.BruteForce(K, 0.1, V)
     Gb, ldb, sb = bf.greens(1)
     G, ld, sg, st = dq.greens(_dev(K), 0.1, _dev(V), 7)
-    assert np.abs(G.cpu().numpy() - bf.to_numpy(Gb)).max() <= GTOL
+    Gx = bf.to_numpy(Gb)     # single-species G of a strong Ising field: |G| ~ 30 here
+    assert np.abs(G.cpu().numpy() - Gx).max() <= GTOL * max(1.0, np.abs(Gx).max())
     assert abs(float(ld) - float(ldb)) <= LTOL * abs(float(ldb))
     assert int(sg) == sb
 

@@ -1,0 +1,65 @@
+"""GPU parity of the ragged batch (dqmc_greens_ragged): instances of different N,
+M, U and k in one call, each against the oracle and against its own uniform
+single-instance call (same kernels, so bitwise equal)."""
+import numpy as np
+import pytest
+
+import dqmc_inputs as di
+from oracle import dqmc as od
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+GTOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def dq():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2003_05286_gb300 as m
+    m.lib()
+    return m
+
+
+def _dev(x):
+    return torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
+
+
+def test_ragged_small_mixed(dq):
+    rng = np.random.default_rng(5)
+    insts = []
+    for i in range(14):
+        L = int(rng.choice([2, 3, 4, 5]))
+        beta = round(float(rng.uniform(1.0, 6.0)), 1)
+        k = int(rng.choice([5, 10]))
+        insts.append(di.hubbard_instance(L, float(rng.uniform(2, 8)), 0.1, beta, min(k, int(beta * 10)),
+                                         1000 + i))
+    Gs, ld, sg, st = dq.greens_ragged([(_dev(x.K), x.dtau, _dev(x.V), x.k) for x in insts])
+    assert int((st != 0).sum()) == 0
+    for i, x in enumerate(insts):
+        Go, ldo, so = od.greens(x.K, x.dtau, x.V, x.k)
+        assert np.abs(Gs[i].cpu().numpy() - Go).max() <= GTOL * max(1.0, np.abs(Go).max()), i
+        assert abs(float(ld[i]) - ldo) <= 1e-9 * max(1.0, abs(ldo))
+        assert int(sg[i]) == so
+        G1, ld1, _, _ = dq.greens(_dev(x.K), x.dtau, _dev(x.V), x.k)
+        assert torch.equal(G1, Gs[i]) and float(ld1) == float(ld[i])
+
+
+def test_ragged_full_size_sampled(dq):
+    """1024 instances, N in {36,64,100,144,256}, beta in [10,50] (M in [100,500]),
+    U in [2,8], k = 10; the smallest and largest instances of each N against the oracle."""
+    insts = [di.ragged_instance(i, 10) for i in range(1024)]
+    Gs, ld, sg, st = dq.greens_ragged([(_dev(x.K), x.dtau, _dev(x.V), x.k) for x in insts])
+    assert int((st != 0).sum()) == 0
+    byN = {}
+    for i, x in enumerate(insts):
+        byN.setdefault(x.N, []).append(i)
+    assert sorted(byN) == [36, 64, 100, 144, 256]
+    for N, idx in byN.items():
+        picks = {min(idx, key=lambda i: insts[i].M), max(idx, key=lambda i: insts[i].M)}
+        for i in picks:
+            x = insts[i]
+            Go, ldo, so = od.greens(x.K, x.dtau, x.V, x.k)
+            assert np.abs(Gs[i].cpu().numpy() - Go).max() <= GTOL * max(1.0, np.abs(Go).max()), (N, i)
+            assert abs(float(ld[i]) - ldo) <= 1e-9 * abs(ldo)
+            assert int(sg[i]) == so
