@@ -245,67 +245,166 @@ inline double* slotX(const Slots& s, int slot) {
 
 // lim (nullable, per instance): chain length M_b of ragged batches; slices
 // past M_b are copied through and finished instances skip the QR and X update.
-dqmc_status run_chain(dqmc_handle h, int dir, int batch, int N, int M, int k, const double* E,
-                      const double* expV, long long sV, const Slots& s, const ChainWs& w,
-                      int* status, const int* lim = nullptr) {
+// a1 for chunk c: k slice products into the chunk buffers; *out = last product.
+dqmc_status chunk_products(dqmc_handle h, int dir, int batch, int N, int M, int k, int c,
+                           const double* E, const double* expV, long long sV, const Slots& s,
+                           const ChainWs& w, const int* lim, const double** out) {
   cudaStream_t st = h->cur;
-  const int nc = n_chunks(M, k);
   const long long NN = (long long)N * N;
-  for (int step = 0; step < nc; ++step) {
-    const int c = dir > 0 ? step : nc - 1 - step;
-    const int src = dir > 0 ? c : c + 1;
-    const int dst = dir > 0 ? c + 1 : c;
-    const int lo = c * k + 1;
-    const int hi = (c + 1) * k < M ? (c + 1) * k : M;
-    const double* prev = slotU(s, src);
-    long long sprev = s.instU;
-    double* bufs[2] = {w.C0, w.C1};
-    int nb = 0;
-    for (int i = 0; i <= hi - lo; ++i) {
-      const int l = dir > 0 ? lo + i : hi - i;
-      GemmArgs g;
-      g.M = g.N = g.K = N;
-      g.batch = batch;
-      g.A = E; g.lda = N; g.sA = 0;
-      g.B = prev; g.ldb = N; g.sB = sprev;
-      g.C = bufs[nb]; g.ldc = N; g.sC = NN;
-      g.lim = lim; g.lim_at = l;
-      if (dir > 0) {
-        g.ms = expV + (long long)(l - 1) * N; g.sms = sV;      // E diag(e^{V_l}) A
-      } else {
-        g.transA = 1;                                          // diag(e^{V_l}) E^T A
-        g.rs = expV + (long long)(l - 1) * N; g.srs = sV;
-      }
-      CKP(PC_CHAIN, 2.0 * N * N * (double)N * batch, gemm_f64(g, st));
-      prev = bufs[nb];
-      sprev = NN;
-      nb ^= 1;
-    }
-    // a2-a3: (A) diag(D_src) -> U' D' T'
-    QrpArgs q;
-    q.N = N; q.batch = batch;
-    q.A = prev; q.sA = NN;
-    q.Din = slotD(s, src); q.sDin = s.instD;
-    q.W = w.W; q.sW = NN;
-    q.U = slotU(s, dst); q.sU = s.instU;
-    q.D = slotD(s, dst); q.sD = s.instD;
-    q.T = w.T; q.sT = NN;
-    q.perm = w.perm; q.sperm = N;
-    q.status = status;
-    q.lim = lim; q.lim_at = lo;
-    CKP(PC_QRP, 8.0 / 3.0 * N * N * (double)N * batch, qrp_f64(q, st));
-    // a4: X_dst = T' X_src[perm]
+  const int src = dir > 0 ? c : c + 1;
+  const int lo = c * k + 1;
+  const int hi = (c + 1) * k < M ? (c + 1) * k : M;
+  const double* prev = slotU(s, src);
+  long long sprev = s.instU;
+  double* bufs[2] = {w.C0, w.C1};
+  int nb = 0;
+  for (int i = 0; i <= hi - lo; ++i) {
+    const int l = dir > 0 ? lo + i : hi - i;
     GemmArgs g;
     g.M = g.N = g.K = N;
     g.batch = batch;
-    g.A = w.T; g.lda = N; g.sA = NN; g.upperA = 1;
-    g.B = slotX(s, src); g.ldb = N; g.sB = s.instX;
-    g.permB = w.perm; g.sperm = N;
-    g.C = slotX(s, dst); g.ldc = N; g.sC = s.instX;
-    g.lim = lim; g.lim_at = lo;
-    CKP(PC_XUPD, (double)N * N * (double)N * batch, gemm_f64(g, st));
+    g.A = E; g.lda = N; g.sA = 0;
+    g.B = prev; g.ldb = N; g.sB = sprev;
+    g.C = bufs[nb]; g.ldc = N; g.sC = NN;
+    g.lim = lim; g.lim_at = l;
+    if (dir > 0) {
+      g.ms = expV + (long long)(l - 1) * N; g.sms = sV;      // E diag(e^{V_l}) A
+    } else {
+      g.transA = 1;                                          // diag(e^{V_l}) E^T A
+      g.rs = expV + (long long)(l - 1) * N; g.srs = sV;
+    }
+    CKP(PC_CHAIN, 2.0 * N * N * (double)N * batch, gemm_f64(g, st));
+    prev = bufs[nb];
+    sprev = NN;
+    nb ^= 1;
+  }
+  *out = prev;
+  return DQMC_OK;
+}
+
+// a2-a4 for chunk c: (A) diag(D_src) -> U' D' T' (pivoted QR), X_dst = T' X_src[perm].
+dqmc_status chunk_refactor(dqmc_handle h, int dir, int batch, int N, int k, int c,
+                           const double* A, const Slots& s, const ChainWs& w, int* status,
+                           const int* lim) {
+  cudaStream_t st = h->cur;
+  const long long NN = (long long)N * N;
+  const int src = dir > 0 ? c : c + 1;
+  const int dst = dir > 0 ? c + 1 : c;
+  const int lo = c * k + 1;
+  QrpArgs q;
+  q.N = N; q.batch = batch;
+  q.A = A; q.sA = NN;
+  q.Din = slotD(s, src); q.sDin = s.instD;
+  q.W = w.W; q.sW = NN;
+  q.U = slotU(s, dst); q.sU = s.instU;
+  q.D = slotD(s, dst); q.sD = s.instD;
+  q.T = w.T; q.sT = NN;
+  q.perm = w.perm; q.sperm = N;
+  q.status = status;
+  q.lim = lim; q.lim_at = lo;
+  CKP(PC_QRP, 8.0 / 3.0 * N * N * (double)N * batch, qrp_f64(q, st));
+  GemmArgs g;
+  g.M = g.N = g.K = N;
+  g.batch = batch;
+  g.A = w.T; g.lda = N; g.sA = NN; g.upperA = 1;
+  g.B = slotX(s, src); g.ldb = N; g.sB = s.instX;
+  g.permB = w.perm; g.sperm = N;
+  g.C = slotX(s, dst); g.ldc = N; g.sC = s.instX;
+  g.lim = lim; g.lim_at = lo;
+  CKP(PC_XUPD, (double)N * N * (double)N * batch, gemm_f64(g, st));
+  return DQMC_OK;
+}
+
+// lim (nullable, per instance): chain length M_b of ragged batches; slices
+// past M_b are copied through and finished instances skip the QR and X update.
+dqmc_status run_chain(dqmc_handle h, int dir, int batch, int N, int M, int k, const double* E,
+                      const double* expV, long long sV, const Slots& s, const ChainWs& w,
+                      int* status, const int* lim = nullptr) {
+  const int nc = n_chunks(M, k);
+  for (int step = 0; step < nc; ++step) {
+    const int c = dir > 0 ? step : nc - 1 - step;
+    const double* A = nullptr;
+    CKS(chunk_products(h, dir, batch, N, M, k, c, E, expV, sV, s, w, lim, &A));
+    CKS(chunk_refactor(h, dir, batch, N, k, c, A, s, w, status, lim));
   }
   return DQMC_OK;
+}
+
+dqmc_status ensure_aux(dqmc_handle h, size_t n) {
+  while (h->aux.size() < n) {
+    cudaStream_t s = nullptr;
+    cudaEvent_t e = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+      return DQMC_ERR_CUDA;
+    h->aux.push_back(s);
+    h->auxev.push_back(e);
+  }
+  return DQMC_OK;
+}
+
+// Two halves of a batch on two streams, staggered by one product phase:
+//   stream 0:  P_A(0) R_A(0)        P_A(1) R_A(1) ...
+//   stream 1:         P_B(0) R_B(0)        P_B(1) ...
+// The product phases P (FP64-pipe bound, all SMs) run one after another,
+// and each half's pivoted QR R (latency bound, one CTA per instance) runs
+// concurrently with the other half's products, filling the FP64 pipe cycles
+// the QR leaves idle.  Caller provides per-half slots/workspaces; the main
+// stream is forked before and joined after.
+struct ChainJob {
+  int dir = +1, batch = 0;
+  const double* expV = nullptr;
+  long long sV = 0;
+  Slots s;
+  ChainWs w;
+  int* status = nullptr;
+};
+
+// Pipelining can be switched off with DQMC_PIPELINE=0 (for A/B timing).
+bool pipeline_enabled() {
+  const char* e = getenv("DQMC_PIPELINE");
+  return !(e && e[0] == '0');
+}
+
+dqmc_status run_chain_pair(dqmc_handle h, const ChainJob job[2], int N, int M, int k,
+                           const double* E) {
+  CKS(ensure_aux(h, 2));
+  cudaStream_t main = h->stream;
+  cudaEvent_t fork = h->auxev[0];
+  cudaEventRecord(fork, main);
+  cudaStreamWaitEvent(h->aux[0], fork, 0);
+  cudaStreamWaitEvent(h->aux[1], fork, 0);
+  cudaEvent_t ev[2];
+  if (cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming) != cudaSuccess) return DQMC_ERR_CUDA;
+  if (cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming) != cudaSuccess) {
+    cudaEventDestroy(ev[0]);
+    return DQMC_ERR_CUDA;
+  }
+  const int nc = n_chunks(M, k);
+  dqmc_status rc = DQMC_OK;
+  for (int step = 0; step < nc && rc == DQMC_OK; ++step) {
+    for (int half = 0; half < 2 && rc == DQMC_OK; ++half) {
+      const ChainJob& J = job[half];
+      const int c = J.dir > 0 ? step : nc - 1 - step;
+      h->cur = h->aux[half];
+      // products of this half wait for the other half's previous product phase
+      if (half == 0 && step > 0) cudaStreamWaitEvent(h->cur, ev[1], 0);
+      if (half == 1) cudaStreamWaitEvent(h->cur, ev[0], 0);
+      const double* A = nullptr;
+      rc = chunk_products(h, J.dir, J.batch, N, M, k, c, E, J.expV, J.sV, J.s, J.w, nullptr, &A);
+      if (rc != DQMC_OK) break;
+      cudaEventRecord(ev[half], h->cur);
+      rc = chunk_refactor(h, J.dir, J.batch, N, k, c, A, J.s, J.w, J.status, nullptr);
+    }
+  }
+  for (int half = 0; half < 2; ++half) {
+    cudaEventRecord(h->auxev[half], h->aux[half]);
+    cudaStreamWaitEvent(main, h->auxev[half], 0);
+  }
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  h->cur = main;
+  return rc;
 }
 
 // ---------------------------------------------------------------------------
@@ -571,7 +670,27 @@ static dqmc_status greens_impl(dqmc_handle h, int batch, int N, int M, const dou
   s.D = D; s.slotD = 0; s.instD = N;
   s.X = X0; s.slotX = 0; s.instX = NN;
   s.X2 = X1;
-  CKS(run_chain(h, +1, batch, N, M, k, E, expV, Mp * N, s, cw, stout));
+  if (batch >= 8 && pipeline_enabled()) {
+    // two half-batches, QR of one overlapping the products of the other
+    const int bA = batch / 2;
+    ChainJob J[2];
+    for (int half = 0; half < 2; ++half) {
+      const long long o = half ? bA : 0;
+      J[half].dir = +1;
+      J[half].batch = half ? batch - bA : bA;
+      J[half].expV = expV + o * Mp * N;
+      J[half].sV = Mp * N;
+      J[half].s = s;
+      J[half].s.U += o * NN; J[half].s.D += o * N; J[half].s.X += o * NN; J[half].s.X2 += o * NN;
+      J[half].w = cw;
+      J[half].w.C0 += o * NN; J[half].w.C1 += o * NN; J[half].w.W += o * NN; J[half].w.T += o * NN;
+      J[half].w.perm += o * N;
+      J[half].status = stout + o;
+    }
+    CKS(run_chain_pair(h, J, N, M, k, E));
+  } else {
+    CKS(run_chain(h, +1, batch, N, M, k, E, expV, Mp * N, s, cw, stout));
+  }
   const double* Xf = (nc & 1) ? X1 : X0;
   CKS(run_loh(h, batch, N, U, NN, D, N, Xf, NN, Gout, ldout, sgout, stout, lw));
 
@@ -637,7 +756,7 @@ void take_stacks(Arena& ar, int batch, int N, int nt, StackWs& w) {
 
 dqmc_status run_stacks(dqmc_handle h, int batch, int N, int M, int k, const double* E,
                        const double* expV, long long sV, const StackWs& w, const ChainWs& cw,
-                       int* status) {
+                       const ChainWs& cw2, int* status) {
   cudaStream_t st = h->cur;
   const int nc = n_chunks(M, k), nt = nc + 1;
   const long long NN = (long long)N * N;
@@ -652,12 +771,22 @@ dqmc_status run_stacks(dqmc_handle h, int batch, int N, int M, int k, const doub
   f.U = w.UF; f.slotU = NN; f.instU = nt * NN;
   f.D = w.DF; f.slotD = N; f.instD = (long long)nt * N;
   f.X = w.XF; f.slotX = NN; f.instX = nt * NN;
-  CKS(run_chain(h, +1, batch, N, M, k, E, expV, sV, f, cw, status));
   Slots b;
   b.U = w.Ub; b.slotU = NN; b.instU = nt * NN;
   b.D = w.Db; b.slotD = N; b.instD = (long long)nt * N;
   b.X = w.Tb; b.slotX = NN; b.instX = nt * NN;
-  CKS(run_chain(h, -1, batch, N, M, k, E, expV, sV, b, cw, status));
+  if (pipeline_enabled()) {
+    // the forward and backward chains are independent: run them as a pair
+    ChainJob J[2];
+    J[0].dir = +1; J[0].batch = batch; J[0].expV = expV; J[0].sV = sV; J[0].s = f; J[0].w = cw;
+    J[0].status = status;
+    J[1].dir = -1; J[1].batch = batch; J[1].expV = expV; J[1].sV = sV; J[1].s = b; J[1].w = cw2;
+    J[1].status = status;
+    CKS(run_chain_pair(h, J, N, M, k, E));
+  } else {
+    CKS(run_chain(h, +1, batch, N, M, k, E, expV, sV, f, cw, status));
+    CKS(run_chain(h, -1, batch, N, M, k, E, expV, sV, b, cw, status));
+  }
   return DQMC_OK;
 }
 
@@ -750,13 +879,14 @@ dqmc_status dqmc_greens_tdisplaced(dqmc_handle h, int batch, int N, int M, const
   if (Q > (1LL << 30)) return DQMC_ERR_ARG;
   const int ncols = (Gtt ? N : 0) + (Gt0 ? N : 0);
 
-  ExpmWs ew; ChainWs cw; StackWs sw; MidWs mw; HostIO io;
+  ExpmWs ew; ChainWs cw, cw2; StackWs sw; MidWs mw; HostIO io;
   double *expV, *Gttd = nullptr, *Gt0d = nullptr;
   int* stat;
   auto layout = [&](Arena& ar) {
     take_expm(ar, N, ew);
     expV = ar.take<double>(Mp * N * batch);
     take_chain(ar, batch, N, cw);
+    take_chain(ar, batch, N, cw2);
     take_stacks(ar, batch, N, nt, sw);
     take_mid(ar, Q, N, ncols > 0 ? ncols : N, mw);
     stat = ar.take<int>(batch);
@@ -789,7 +919,7 @@ dqmc_status dqmc_greens_tdisplaced(dqmc_handle h, int batch, int N, int M, const
   if (cudaMemsetAsync(stout, 0, sizeof(int) * batch, st) != cudaSuccess) return DQMC_ERR_CUDA;
   CKS(run_expm(h, Kd, N, dtau, -1.0, ew, stout, batch));
   CK(exp_pad(Vd, expV, batch, M, (int)Mp, N, 1.0, stout, st));
-  CKS(run_stacks(h, batch, N, M, k, ew.t0, expV, Mp * N, sw, cw, stout));
+  CKS(run_stacks(h, batch, N, M, k, ew.t0, expV, Mp * N, sw, cw, cw2, stout));
   CKS(run_two_stack_inversion(h, (int)Q, N, nt, sw, mw, Gtto, Gt0o, stout));
   if (host) {
     bool ok = true;
@@ -820,7 +950,7 @@ dqmc_status dqmc_logdet_grad(dqmc_handle h, int batch, int N, int M, const doubl
   const long long Q = (long long)batch * nt;
   if (Q > (1LL << 30)) return DQMC_ERR_ARG;
 
-  ExpmWs ew, ewi; ChainWs cw; StackWs sw; MidWs mw; LohWs lw; HostIO io;
+  ExpmWs ew, ewi; ChainWs cw, cw2; StackWs sw; MidWs mw; LohWs lw; HostIO io;
   double *expV, *expmV, *Gw, *W1, *dVd = nullptr, *ldd = nullptr;
   int *stat, *sgd = nullptr;
   auto layout = [&](Arena& ar) {
@@ -829,6 +959,7 @@ dqmc_status dqmc_logdet_grad(dqmc_handle h, int batch, int N, int M, const doubl
     expV = ar.take<double>(Mp * N * batch);
     expmV = ar.take<double>(Mp * N * batch);
     take_chain(ar, batch, N, cw);
+    take_chain(ar, batch, N, cw2);
     take_stacks(ar, batch, N, nt, sw);
     take_mid(ar, Q, N, N, mw);
     take_loh(ar, batch, N, lw);
@@ -868,7 +999,7 @@ dqmc_status dqmc_logdet_grad(dqmc_handle h, int batch, int N, int M, const doubl
   CKS(run_expm(h, Kd, N, dtau, +1.0, ewi, nullptr, batch));
   CK(exp_pad(Vd, expV, batch, M, (int)Mp, N, 1.0, stout, st));
   CK(exp_pad(Vd, expmV, batch, M, (int)Mp, N, -1.0, nullptr, st));
-  CKS(run_stacks(h, batch, N, M, k, ew.t0, expV, Mp * N, sw, cw, stout));
+  CKS(run_stacks(h, batch, N, M, k, ew.t0, expV, Mp * N, sw, cw, cw2, stout));
   // log det from the full forward product B(beta, 0) = U_F a X_F (slot nc)
   CKS(run_loh(h, batch, N, sw.UF + nc * NN, nt * NN, sw.DF + (long long)nc * N, (long long)nt * N,
               sw.XF + nc * NN, nt * NN, nullptr, ldo, sgo, stout, lw));
@@ -986,15 +1117,7 @@ dqmc_status dqmc_greens_ragged(dqmc_handle h, int batch, const dqmc_instance* de
   layout(ar);
   // ---- streams ---------------------------------------------------------------
   const size_t nstreams = groups.size() < 8 ? groups.size() : 8;
-  while (h->aux.size() < nstreams) {
-    cudaStream_t s = nullptr;
-    cudaEvent_t e = nullptr;
-    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
-      return DQMC_ERR_CUDA;
-    h->aux.push_back(s);
-    h->auxev.push_back(e);
-  }
+  CKS(ensure_aux(h, nstreams));
   cudaEvent_t fork = nullptr;
   if (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess) return DQMC_ERR_CUDA;
   // per-group index tables (uploaded on the main stream, before the fork)

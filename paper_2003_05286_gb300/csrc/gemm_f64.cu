@@ -14,7 +14,9 @@
 namespace dqmc {
 
 template <int BM, int BN, int BK, int TM, int TN>
-__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+// At most 168 registers: a 256-thread CTA then leaves room on its SM for one
+// pivoted-QR CTA of the other half-batch (the two run concurrently).
+__global__ void __maxnreg__(168)
 gemm_f64_kernel(const GemmArgs a) {
   constexpr int NTX = BN / TN;
   constexpr int NT = (BM / TM) * NTX;
