@@ -63,10 +63,30 @@ def parse():
 
 def make_inputs(wl: dict, rank: int, batch: int):
     """K and the (batch, M, N) fields of this rank's instances (disjoint seeds per rank)."""
-    insts = [di.hubbard_instance(wl["L"], wl["U"], wl["dtau"], wl["beta"], wl["k"],
-                                 di.instance_seed(wl["config"], rank * batch + i))
-             for i in range(batch)]
+    insts = [di.hubbard_instance(wl["L"], wl["U"], wl["dtau"], wl["beta"], wl["k"], sd)
+             for sd in rank_seeds(wl, rank, batch)]
     return insts[0].K, np.stack([x.V for x in insts]), insts
+
+
+def rank_seeds(wl: dict, rank: int, batch: int) -> list[int]:
+    """Seeds of this rank's instances: rank r owns instances [r*batch, (r+1)*batch)."""
+    return [di.instance_seed(wl["config"], rank * batch + i) for i in range(batch)]
+
+
+def reduce_max(x: float, device=None) -> float:
+    """Max over ranks of a local time (identity outside torch.distributed)."""
+    import torch
+    import torch.distributed as tdist
+    if not (tdist.is_available() and tdist.is_initialized()):
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(batch: int, world: int, steps: int, max_ms: float) -> float:
+    """Whole-job Green's functions per second: all ranks' instances / slowest rank's time."""
+    return batch * world * steps / (max_ms / 1e3)
 
 
 def flops_per_greens(N: int, M: int, k: int) -> float:
@@ -253,15 +273,12 @@ def run_gpu(args, wl, rank, world):
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     tot_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([tot_ms], device=dev)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        tot_ms = float(t.item())
+    tot_ms = reduce_max(tot_ms, dev)
     chain_ms, chain_n, chain_flops = h.profile_read(h.PROF_CHAIN)
     h.profile(False)
     bad = int((st != 0).sum().item())
 
-    value = batch * world * args.steps / (tot_ms / 1e3)
+    value = job_value(batch, world, args.steps, tot_ms)
     fl = flops_per_greens(N, M, k)
 
     # ---- end to end through the C ABI with host buffers ----------------------
@@ -296,10 +313,7 @@ def run_gpu(args, wl, rank, world):
             e2e_step()                      # returns after the outputs are in host memory
             ts.append(time.perf_counter() - t0)
         e2e_s = sum(ts) / len(ts)
-        if dist:
-            t = torch.tensor([e2e_s], device=dev)
-            tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = reduce_max(e2e_s, dev)
         e2e = {"value": batch * world / e2e_s, "unit": "G/s",
                "h2d_bytes_per_step": int(Kh.numel() * 8 + Vh.numel() * 8),
                "d2h_bytes_per_step": int(Gh.numel() * 8 + batch * (8 + 4 + 4)),
