@@ -55,7 +55,8 @@ typedef enum {
   DQMC_ERR_NONFINITE = 4,  /* (status bit) NaN/Inf in an input or a result */
   DQMC_ERR_SINGULAR = 5,   /* (status bit) exactly singular pivot */
   DQMC_ERR_TIMEOUT = 6,    /* a bounded device-side wait gave up */
-  DQMC_ERR_UNSUPPORTED = 7 /* configuration not built into this library */
+  DQMC_ERR_UNSUPPORTED = 7, /* configuration not built into this library */
+  DQMC_ERR_SCRATCH = 8      /* dqmc_greens_noalloc: problem needs more than its fixed scratch */
 } dqmc_status;
 
 /* Bits of the per-instance device status word. */
@@ -156,6 +157,35 @@ dqmc_status dqmc_greens_ragged(dqmc_handle h, int batch, const dqmc_instance* de
                                const double* K_pool, const double* V_pool,
                                double* G_pool, double* logdet, int* sign,
                                int* status);
+
+/* Allocation-free variant of dqmc_greens, for callers that cannot allocate
+ * device memory (an application or pool that owns the whole device budget, a
+ * plugin that must not go around its host's allocator, a process with a fixed
+ * footprint).  The paper has no counterpart: this is a deployment variant.
+ *
+ * Same computation and arguments as dqmc_greens (device pointers only; the
+ * caller passes inputs and outputs), but there is no handle: the call runs on
+ * `stream` (a cudaStream_t, NULL = legacy default stream) of the current
+ * device, and every intermediate lives in a file-scope device array of
+ * 32 MiB (32 * 2^20 bytes) that each GPU loading the library holds until the
+ * process exits.  The call issues no cudaMalloc, cudaFree or other allocating
+ * routine.
+ *   - Size limit: about batch * 8 * (N*(ceil(M/k)+1)*k + 11*N*N) + 16*N*N bytes must
+ *     fit in 32 MiB (e.g. N=256, M=200, k=10: batch <= 5; N=64, M=400:
+ *     batch <= 58).  Larger problems return DQMC_ERR_SCRATCH before anything
+ *     is launched.
+ *   - First call on a device: it resolves the array's device address
+ *     (cudaGetSymbolAddress) once for the current device; make that first call
+ *     before any stream capture on the device.
+ *   - Every call shares the one array, which keeps the previous call's
+ *     contents; the call clears what must start at zero itself.  Calls that
+ *     overlap on the GPU (other streams, other host threads) race on the array
+ *     and must be serialised by the caller.
+ * The chain runs unpipelined on the one stream, so it is slower than
+ * dqmc_greens for large batches. */
+dqmc_status dqmc_greens_noalloc(void* stream, int batch, int N, int M, const double* K,
+                                double dtau, const double* V, int k, double* G, double* logdet,
+                                int* sign, int* status);
 
 #ifdef __cplusplus
 }

@@ -11,6 +11,7 @@ STATUS_STRINGS = {
     0: "ok", 1: "invalid argument", 2: "CUDA runtime or launch failure",
     3: "device workspace allocation failed", 4: "non-finite value", 5: "singular pivot",
     6: "bounded device wait gave up", 7: "unsupported configuration",
+    8: "problem needs more device scratch than the fixed array holds",
 }
 STATUS_BITS = {
     "NONFINITE_INPUT": 1 << 0, "NONFINITE_SCALE": 1 << 1, "SINGULAR": 1 << 2,
@@ -51,6 +52,7 @@ SIGNATURES = {
     "dqmc_greens_tdisplaced": (_I, [_P, _I, _I, _I, _P, _D, _P, _I, _P, _P, _P]),
     "dqmc_logdet_grad": (_I, [_P, _I, _I, _I, _P, _D, _P, _I, _P, _P, _P, _P]),
     "dqmc_greens_ragged": (_I, [_P, _I, C.POINTER(DqmcInstance), _P, _P, _P, _P, _P, _P]),
+    "dqmc_greens_noalloc": (_I, [_P, _I, _I, _I, _P, _D, _P, _I, _P, _P, _P, _P]),
 }
 
 _lib = None

@@ -587,6 +587,7 @@ const char* dqmc_status_string(dqmc_status s) {
     case DQMC_ERR_SINGULAR: return "singular pivot";
     case DQMC_ERR_TIMEOUT: return "bounded device wait gave up";
     case DQMC_ERR_UNSUPPORTED: return "unsupported configuration";
+    case DQMC_ERR_SCRATCH: return "problem needs more device scratch than the fixed array holds";
   }
   return "unknown status";
 }
@@ -705,6 +706,70 @@ static dqmc_status greens_impl(dqmc_handle h, int batch, int N, int M, const dou
   }
   return DQMC_OK;
 }
+
+}  // extern "C"
+
+// Equal-time path on a caller-supplied device workspace (used by the
+// allocation-free entry point in noalloc.cu).  It runs the same helpers as
+// dqmc_greens with a handle that lives on the host stack, the chain in one
+// stream (no pipelining, so no stream or event is created), and no
+// cudaMalloc: when the problem needs more than ws_bytes it returns
+// DQMC_ERR_SCRATCH before launching anything.
+namespace dqmc {
+dqmc_status greens_on_workspace(void* stream, void* ws, size_t ws_bytes, int batch, int N, int M,
+                                const double* K, double dtau, const double* V, int k, double* G,
+                                double* logdet, int* sign, int* status) {
+  dqmc_handle_s local;
+  dqmc_handle h = &local;
+  h->stream = (cudaStream_t)stream;
+  CKS(check_common(h, batch, N, M, K, dtau, V, k));
+  h->cur = h->stream;
+  if (batch == 0) return DQMC_OK;
+  const long long NN = (long long)N * N;
+  const int nc = n_chunks(M, k);
+  const long long Mp = (long long)(nc + 1) * k;
+  ExpmWs ew; ChainWs cw; LohWs lw;
+  double *expV, *U, *D, *X0, *X1;
+  int* stat;
+  auto layout = [&](Arena& ar) {
+    take_expm(ar, N, ew);
+    expV = ar.take<double>(Mp * N * batch);
+    U = ar.take<double>(NN * batch);
+    D = ar.take<double>((long long)N * batch);
+    X0 = ar.take<double>(NN * batch);
+    X1 = ar.take<double>(NN * batch);
+    take_chain(ar, batch, N, cw);
+    take_loh(ar, batch, N, lw);
+    stat = ar.take<int>(batch);
+  };
+  Arena measure;
+  layout(measure);
+  if (measure.off > ws_bytes) return DQMC_ERR_SCRATCH;
+  Arena ar;
+  ar.base = static_cast<char*>(ws);
+  layout(ar);
+  cudaStream_t st = h->cur;
+  int* stout = status ? status : stat;
+  // the workspace keeps the previous call's contents: zero what accumulates
+  if (cudaMemsetAsync(stout, 0, sizeof(int) * batch, st) != cudaSuccess) return DQMC_ERR_CUDA;
+  CKS(run_expm(h, K, N, dtau, -1.0, ew, stout, batch));
+  CK(exp_pad(V, expV, batch, M, (int)Mp, N, 1.0, stout, st));
+  CK(set_identity(U, NN, N, batch, st));
+  CK(set_const(D, (long long)N * batch, 1.0, st));
+  CK(set_identity(X0, NN, N, batch, st));
+  Slots s;
+  s.U = U; s.slotU = 0; s.instU = NN;
+  s.D = D; s.slotD = 0; s.instD = N;
+  s.X = X0; s.slotX = 0; s.instX = NN;
+  s.X2 = X1;
+  CKS(run_chain(h, +1, batch, N, M, k, ew.t0, expV, Mp * N, s, cw, stout));
+  const double* Xf = (nc & 1) ? X1 : X0;
+  CKS(run_loh(h, batch, N, U, NN, D, N, Xf, NN, G, logdet, sign, stout, lw));
+  return DQMC_OK;
+}
+}  // namespace dqmc
+
+extern "C" {
 
 dqmc_status dqmc_greens(dqmc_handle h, int batch, int N, int M, const double* K, double dtau,
                         const double* V, int k, double* G, double* logdet, int* sign,

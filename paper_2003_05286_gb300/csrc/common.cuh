@@ -159,3 +159,10 @@ cudaError_t scatter_scalars(const int* gidx, int batch, const double* ld, const 
 cudaError_t or_status(int* status, int batch, const int* flag, int bit, cudaStream_t st);
 
 }  // namespace dqmc
+
+namespace dqmc {
+// Equal-time G / log det on a caller-supplied device workspace (api.cu).
+dqmc_status greens_on_workspace(void* stream, void* ws, size_t ws_bytes, int batch, int N, int M,
+                                const double* K, double dtau, const double* V, int k, double* G,
+                                double* logdet, int* sign, int* status);
+}  // namespace dqmc
