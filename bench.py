@@ -58,6 +58,10 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--precision", default="fp64", choices=["fp64", "bf16x3", "bf16x4", "bf16x5", "bf16x6"],
+                   help="chain-product precision of the timed steps (QR and inversions stay FP64)")
+    p.add_argument("--mixed-slices", type=int, default=6,
+                   help="also time the mixed chain with this many BF16 slices (0: skip)")
     return p.parse_args()
 
 
@@ -239,7 +243,8 @@ def run_gpu(args, wl, rank, world):
     K_np, V_np, insts = make_inputs(wl, rank, batch)
     K = torch.tensor(K_np, device=dev)
     V = torch.tensor(V_np, device=dev)
-    h = dq.Handle()
+    prec = 0 if args.precision == "fp64" else int(args.precision[-1])
+    h = dq.Handle(chain_precision=prec)
     h.bind_stream()
 
     def step():
@@ -281,11 +286,40 @@ def run_gpu(args, wl, rank, world):
     value = job_value(batch, world, args.steps, tot_ms)
     fl = flops_per_greens(N, M, k)
 
+    # ---- the same step with the chain products on the tensor cores -----------
+    mixed = None
+    if args.mixed_slices and prec == 0:
+        G64, ld64 = G.clone(), ld.clone()
+        hm = dq.Handle(chain_precision=args.mixed_slices)
+        hm.bind_stream()
+        for _ in range(args.warmup):
+            dq.greens(K, wl["dtau"], V, k, handle=hm)
+        evm = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        if dist:
+            tdist.barrier()
+        torch.cuda.synchronize()
+        for s_ in range(args.steps):
+            flush.fill_(float(s_))
+            evm[s_][0].record()
+            Gm, ldm, sgm, stm = dq.greens(K, wl["dtau"], V, k, handle=hm)
+            evm[s_][1].record()
+        torch.cuda.synchronize()
+        mms = reduce_max(sum(a.elapsed_time(b) for a, b in evm), dev)
+        mixed = {"value": job_value(batch, world, args.steps, mms), "unit": "G/s",
+                 "ms_per_step": mms / args.steps, "chain_precision": f"bf16x{args.mixed_slices}",
+                 "speedup_vs_fp64": tot_ms / mms,
+                 "max_abs_dG_vs_fp64_path": float((Gm - G64).abs().max().item()),
+                 "max_rel_dlogdet_vs_fp64_path": float(((ldm - ld64).abs() / ld64.abs()).max().item()),
+                 "sign_mismatches": int((sgm != sg).sum().item()),
+                 "note": "error against this run's FP64 path, which matches the CPU oracle to 1e-10"}
+        hm.close()
+
     # ---- end to end through the C ABI with host buffers ----------------------
     e2e = None
     if not args.no_e2e:
         import ctypes as C
-        he = dq.Handle()
+        he = dq.Handle(chain_precision=prec)
         he.bind_stream()
         he.set_pointer_mode(True)
         Kh = torch.tensor(K_np).pin_memory()
@@ -334,10 +368,10 @@ def run_gpu(args, wl, rank, world):
         "metric": "greens_functions_per_second", "value": value, "unit": "G/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f64" if prec == 0 else f"bf16x{prec}+f64", "data": "synthetic",
         "config": {"workload": args.workload, "N": N, "M": M, "k": k, "beta": wl["beta"],
                    "U": wl["U"], "dtau": wl["dtau"], "instances_per_gpu": batch,
-                   "chain_precision": "fp64",
+                   "chain_precision": args.precision,
                    "l2": "flushed between timed steps (256 MB write)"},
         "fp64_tflops": fl * batch * world * args.steps / (tot_ms / 1e3) / 1e12,
         "fp64_frac_of_peak": fl * batch * args.steps / (tot_ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
@@ -351,6 +385,7 @@ def run_gpu(args, wl, rank, world):
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
         "e2e": e2e,
+        "mixed": mixed,
         "cpu_baseline": cpu,
         "status_nonzero": bad,
         "wall_s": wall,

@@ -65,12 +65,23 @@ enum dqmc_status_bits {
   DQMC_STATUS_NONFINITE_SCALE = 1 << 1,  /* a D scale overflowed or became NaN */
   DQMC_STATUS_SINGULAR = 1 << 2,         /* an LU pivot or QR diagonal was exactly 0 */
   DQMC_STATUS_NONFINITE_OUTPUT = 1 << 3, /* G or log det is not finite */
-  DQMC_STATUS_BAD_K = 1 << 4             /* K not symmetric/finite, or ||dtau K||_1 > 2048 */
+  DQMC_STATUS_BAD_K = 1 << 4,            /* K not symmetric/finite, or ||dtau K||_1 > 2048 */
+  DQMC_STATUS_TIMEOUT = 1 << 5           /* a bounded wait of a tensor-core kernel gave up */
 };
 
+/* Precision of the k-slice chain products (a mixed-precision option; the
+ * pivoted QR, the D splits and the inversions always run in FP64).
+ * DQMC_CHAIN_BF16Xs: each FP64 operand is cut into s BF16 slices of 7 bits
+ * (error-free splitting with power-of-two row/column scales), the slice
+ * products accumulate exactly in FP32 on the tcgen05 tensor cores and are
+ * recombined in FP64; the product is accurate to about 2^{-7s} of the row x
+ * column scale.  Supported for N <= 256 in dqmc_greens / dqmc_logdet. */
 typedef enum {
-  DQMC_CHAIN_FP64 = 0,  /* k-slice chain products in FP64 (default) */
-  DQMC_CHAIN_BF16X3 = 2 /* chain products on tensor cores from BF16 splits (mixed) */
+  DQMC_CHAIN_FP64 = 0,
+  DQMC_CHAIN_BF16X3 = 3,
+  DQMC_CHAIN_BF16X4 = 4,
+  DQMC_CHAIN_BF16X5 = 5,
+  DQMC_CHAIN_BF16X6 = 6
 } dqmc_chain_prec;
 
 typedef enum { DQMC_PTR_DEVICE = 0, DQMC_PTR_HOST = 1 } dqmc_pointer_mode;

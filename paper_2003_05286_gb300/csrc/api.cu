@@ -225,7 +225,25 @@ struct Slots {
 struct ChainWs {
   double *C0, *C1, *W, *T;
   int* perm;
+  // mixed-precision slice products (oz_s > 0): E slices (shared) and the
+  // per-instance slices of the right operand
+  int oz_s = 0, oz_P128 = 0, oz_PK = 0;
+  __nv_bfloat16 *ozA = nullptr, *ozB = nullptr;
+  int *ozeA = nullptr, *ozeB = nullptr;
 };
+
+inline int pad_to(int n, int m) { return (n + m - 1) / m * m; }
+
+// Mixed-precision buffers of a chain over `batch` instances with s slices.
+void take_ozaki(Arena& ar, int batch, int N, int s, ChainWs& w) {
+  w.oz_s = s;
+  w.oz_P128 = pad_to(N, 128);
+  w.oz_PK = pad_to(N, 64);
+  w.ozA = ar.take<__nv_bfloat16>((long long)s * w.oz_P128 * w.oz_PK);
+  w.ozeA = ar.take<int>(w.oz_P128);
+  w.ozB = ar.take<__nv_bfloat16>((long long)batch * s * w.oz_PK * w.oz_PK);
+  w.ozeB = ar.take<int>((long long)batch * w.oz_PK);
+}
 
 void take_chain(Arena& ar, int batch, int N, ChainWs& w) {
   long long NN = (long long)N * N;
@@ -260,6 +278,19 @@ dqmc_status chunk_products(dqmc_handle h, int dir, int batch, int N, int M, int 
   int nb = 0;
   for (int i = 0; i <= hi - lo; ++i) {
     const int l = dir > 0 ? lo + i : hi - i;
+    if (w.oz_s > 0 && dir > 0 && lim == nullptr) {
+      // a12: B' = diag(e^{V_l}) A split into BF16 slices, then E B' on the tensor cores
+      const int PK = w.oz_PK, sl = w.oz_s;
+      CK(ozaki_split(prev, N, 1, sprev, expV + (long long)(l - 1) * N, sV, N, PK, PK, sl, w.ozB,
+                     (long long)sl * PK * PK, w.ozeB, PK, batch, st));
+      CKP(PC_CHAIN, 2.0 * N * N * (double)N * batch,
+          ozaki_gemm(w.ozA, w.ozeA, w.oz_P128, w.ozB, w.ozeB, PK, PK, PK, sl, N, batch, bufs[nb],
+                     NN, nullptr, st));
+      prev = bufs[nb];
+      sprev = NN;
+      nb ^= 1;
+      continue;
+    }
     GemmArgs g;
     g.M = g.N = g.K = N;
     g.batch = batch;
@@ -569,7 +600,8 @@ dqmc_status dqmc_set_pointer_mode(dqmc_handle h, dqmc_pointer_mode mode) {
 
 dqmc_status dqmc_set_chain_precision(dqmc_handle h, dqmc_chain_prec prec) {
   if (!h) return DQMC_ERR_ARG;
-  if (prec != DQMC_CHAIN_FP64) return DQMC_ERR_UNSUPPORTED;
+  if (prec != DQMC_CHAIN_FP64 && (prec < DQMC_CHAIN_BF16X3 || prec > DQMC_CHAIN_BF16X6))
+    return DQMC_ERR_ARG;
   h->prec = prec;
   return DQMC_OK;
 }
@@ -599,6 +631,7 @@ static dqmc_status greens_impl(dqmc_handle h, int batch, int N, int M, const dou
                                double dtau, const double* V, int k, double* G, double* logdet,
                                int* sign, int* status) {
   CKS(check_common(h, batch, N, M, K, dtau, V, k));
+  if (h->prec != DQMC_CHAIN_FP64 && N > 256) return DQMC_ERR_UNSUPPORTED;
   h->launches = 0;
   h->cur = h->stream;
   if (batch == 0) return DQMC_OK;
@@ -618,6 +651,7 @@ static dqmc_status greens_impl(dqmc_handle h, int batch, int N, int M, const dou
     X0 = ar.take<double>(NN * batch);
     X1 = ar.take<double>(NN * batch);
     take_chain(ar, batch, N, cw);
+    if (h->prec != DQMC_CHAIN_FP64) take_ozaki(ar, batch, N, (int)h->prec, cw);
     take_loh(ar, batch, N, lw);
     st = ar.take<int>(batch);
     if (host) {
@@ -663,6 +697,12 @@ static dqmc_status greens_impl(dqmc_handle h, int batch, int N, int M, const dou
   // exp(V_l) for every slice, padded to Mp slices per instance
   CK(exp_pad(Vd, expV, batch, M, (int)Mp, N, 1.0, stout, st));
 
+  if (cw.oz_s > 0) {
+    // slices of E, shared by every instance and slice: row i of E is a
+    // "column" of the splitter (element (m, i) = E[i][m])
+    CK(ozaki_split(E, 1, N, 0, nullptr, 0, N, cw.oz_P128, cw.oz_PK, cw.oz_s, cw.ozA, 0, cw.ozeA,
+                   0, 1, st));
+  }
   CK(set_identity(U, NN, N, batch, st));
   CK(set_const(D, (long long)N * batch, 1.0, st));
   CK(set_identity(X0, NN, N, batch, st));
@@ -686,6 +726,10 @@ static dqmc_status greens_impl(dqmc_handle h, int batch, int N, int M, const dou
       J[half].w = cw;
       J[half].w.C0 += o * NN; J[half].w.C1 += o * NN; J[half].w.W += o * NN; J[half].w.T += o * NN;
       J[half].w.perm += o * N;
+      if (cw.oz_s > 0) {
+        J[half].w.ozB += o * cw.oz_s * (long long)cw.oz_PK * cw.oz_PK;
+        J[half].w.ozeB += o * cw.oz_PK;
+      }
       J[half].status = stout + o;
     }
     CKS(run_chain_pair(h, J, N, M, k, E));
@@ -933,6 +977,7 @@ dqmc_status dqmc_greens_tdisplaced(dqmc_handle h, int batch, int N, int M, const
                                    double dtau, const double* V, int k, double* Gtt, double* Gt0,
                                    int* status) {
   CKS(check_common(h, batch, N, M, K, dtau, V, k));
+  if (h->prec != DQMC_CHAIN_FP64) return DQMC_ERR_UNSUPPORTED;   // mixed chain: equal time only
   h->launches = 0;
   h->cur = h->stream;
   if (batch == 0) return DQMC_OK;
@@ -1004,6 +1049,7 @@ dqmc_status dqmc_logdet_grad(dqmc_handle h, int batch, int N, int M, const doubl
                              const double* V, int k, double* logdet, int* sign, double* dV,
                              int* status) {
   CKS(check_common(h, batch, N, M, K, dtau, V, k));
+  if (h->prec != DQMC_CHAIN_FP64) return DQMC_ERR_UNSUPPORTED;   // mixed chain: equal time only
   h->launches = 0;
   h->cur = h->stream;
   if (batch == 0) return DQMC_OK;
@@ -1114,6 +1160,7 @@ dqmc_status dqmc_greens_ragged(dqmc_handle h, int batch, const dqmc_instance* de
   if (batch == 0) return DQMC_OK;
   if (!desc || !K_pool || !V_pool) return DQMC_ERR_ARG;
   if (h->pmode == DQMC_PTR_HOST) return DQMC_ERR_UNSUPPORTED;
+  if (h->prec != DQMC_CHAIN_FP64) return DQMC_ERR_UNSUPPORTED;   // mixed chain: uniform batches only
   for (int b = 0; b < batch; ++b) {
     const dqmc_instance& d = desc[b];
     if (d.N < 1 || d.N > 1024 || d.M < 1 || d.k < 1 || d.k > d.M || !(d.dtau >= 0.0) ||

@@ -166,3 +166,16 @@ dqmc_status greens_on_workspace(void* stream, void* ws, size_t ws_bytes, int bat
                                 const double* K, double dtau, const double* V, int k, double* G,
                                 double* logdet, int* sign, int* status);
 }  // namespace dqmc
+
+#include <cuda_bf16.h>
+namespace dqmc {
+// Error-free BF16 slicing and tensor-core slice products (ozaki_tc.cu).
+cudaError_t ozaki_split(const double* X, long long ldm, long long ldj, long long sX,
+                        const double* sc, long long ssc, int N, int PJ, int PM, int s,
+                        __nv_bfloat16* S, long long sS, int* e, long long se, int batch,
+                        cudaStream_t st);
+cudaError_t ozaki_gemm(const __nv_bfloat16* As, const int* eA, int P128, const __nv_bfloat16* Bs,
+                       const int* eB, long long seB, int PN, int PK, int s, int N, int batch,
+                       double* C, long long sC, int* status, cudaStream_t st);
+int oz_groups(int s, int N);
+}  // namespace dqmc

@@ -1,0 +1,491 @@
+// Mixed-precision slice products on the tcgen05 tensor cores.
+//
+// The k-slice chain products (Sec. 2, Eq. (Ztr); a naive chunk between two
+// re-factorisations, Sec. 4.1) may run in reduced precision; the pivoted QR,
+// the D splits and the inversions stay FP64.  Here a product C = E * B' (E =
+// exp(-dtau K), B' = diag(exp V_l) A) is evaluated from BF16 operands by the
+// error-free splitting of Ozaki et al. (Numer. Algorithms 59, 2012):
+//
+//   * every row i of E is scaled by 2^{-eA_i} and every column j of B' by
+//     2^{-eB_j} so that all entries lie in (-1, 1); each scaled entry is cut
+//     into s slices of 7 bits (x = sum_p a_p 2^{-7p} + O(2^{-7s}), a_p integer
+//     in [-127, 127]) -- integers of at most 8 significant bits, exact in BF16;
+//   * a slice product a_p . b_q is a sum of K <= 256 integers below 2^14, so it
+//     is an integer below 2^22 and the FP32 accumulation of the tensor core is
+//     exact; products with the same weight 2^{-7(p+q)} share one TMEM
+//     accumulator as long as at most 4 of them meet (sum < 2^24);
+//   * only p + q <= s + 1 is formed (the rest is below the truncation error);
+//   * the epilogue adds the accumulators in int64 with their relative shifts
+//     and rebuilds the FP64 value by integer exponent arithmetic, so no FP64
+//     pipe time is spent on the products at all.
+//
+// Per CTA: one 128 x 64 output tile of one instance; 4 warps; warp 0 issues the
+// TMA loads of the s A-slice tiles (128 x 32 BF16) and s B-slice tiles
+// (64 x 32 BF16) of a K-block into one of two shared-memory stages (64-byte
+// swizzle), one thread of warp 1 issues the tcgen05.mma (M=128, N=64, K=16,
+// kind::f16 with BF16 inputs, FP32 accumulators in TMEM), and all four warps
+// read the accumulators back (tcgen05.ld 32x32b) for the epilogue.  Every
+// mbarrier wait is bounded (~2 s by the global timer); a CTA that gives up
+// records DQMC_STATUS_TIMEOUT in its instance's status word, waits (bounded)
+// for its own copies, frees its TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+
+namespace dqmc {
+
+namespace {
+
+constexpr int OZ_BM = 128;       // output rows per CTA (TMEM lanes)
+constexpr int OZ_BN = 64;        // output columns per CTA (TMEM columns per accumulator)
+constexpr int OZ_BK = 32;        // K per stage: 32 BF16 = 64 bytes per row (64-byte swizzle)
+constexpr int OZ_STAGES = 2;
+constexpr int OZ_THREADS = 128;
+constexpr int OZ_A_TILE = OZ_BM * OZ_BK * 2;   // 8 KB
+constexpr int OZ_B_TILE = OZ_BN * OZ_BK * 2;   // 4 KB
+constexpr unsigned long long OZ_WAIT_NS = 2000000000ull;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on a phase of an mbarrier; false after OZ_WAIT_NS.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (globaltimer() - t0 > OZ_WAIT_NS) return false;
+  }
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int c0, int c1, int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int c0, int c1, int c2, int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2),
+      "r"(c3)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major tile with 64-byte swizzle:
+// rows of 64 bytes, 8-row groups 512 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);        // start address
+  d |= (uint64_t)1 << 16;                          // leading byte offset (unused when swizzled)
+  d |= (uint64_t)(512 >> 4) << 32;                 // stride byte offset: 8 rows x 64 B
+  d |= (uint64_t)1 << 46;                          // descriptor version
+  d |= (uint64_t)4 << 61;                          // swizzle mode: 64-byte
+  return d;
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N = 64, M = 128.
+__host__ __device__ constexpr uint32_t oz_idesc() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BN >> 3) << 17) |
+         ((uint32_t)(OZ_BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                     uint32_t idesc, uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// 2^e * x for an FP64 x built from an integer, by exponent arithmetic when the
+// result stays normal.
+__device__ __forceinline__ double scale_pow2(double x, int e) {
+  if (x == 0.0) return 0.0;
+  long long bits = __double_as_longlong(x);
+  int ex = (int)((bits >> 52) & 0x7ff) + e;
+  if (ex >= 1 && ex <= 2046) return __longlong_as_double(bits + ((long long)e << 52));
+  return ldexp(x, e);
+}
+
+}  // namespace
+
+// Pair table: up to 21 (p, q) slice pairs with their accumulator group.
+struct OzPairs {
+  int n;                 // number of pairs
+  int ngroups;           // accumulators (<= 8)
+  int s;                 // slices per operand
+  int shift[8];          // left shift (bits) of group g in the int64 combination
+  unsigned char p[24], q[24], g[24], first[24];
+};
+
+__global__ void __launch_bounds__(OZ_THREADS, 1)
+ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                  const OzPairs pr, int N, int nkb, const int* __restrict__ eA,
+                  const int* __restrict__ eB, long long seB, double* __restrict__ C,
+                  long long sC, int* status) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // 1024-byte aligned stage buffers
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  const int s = pr.s;
+  const int stage_bytes = s * (OZ_A_TILE + OZ_B_TILE);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + OZ_STAGES * stage_bytes);
+  uint64_t* full = bars;                    // [OZ_STAGES]
+  uint64_t* empty = bars + OZ_STAGES;       // [OZ_STAGES]
+  uint64_t* done = bars + 2 * OZ_STAGES;    // [1]
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * OZ_STAGES + 1);
+  int* s_fail = reinterpret_cast<int*>(tmem_holder + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int n0 = blockIdx.x * OZ_BN, m0 = blockIdx.y * OZ_BM, b = blockIdx.z;
+  uint32_t tmem_cols = 32;
+  while (tmem_cols < (uint32_t)(pr.ngroups * OZ_BN)) tmem_cols <<= 1;
+
+  if (tid == 0) {
+    for (int i = 0; i < OZ_STAGES; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+    }
+    mbar_init(done, 1);
+    *s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_holder)),
+                 "r"(tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_holder;
+
+  if (warp == 0 && lane == 0) {
+    // ---- producer: TMA loads of the slice tiles of each K-block -----------
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int st = kb % OZ_STAGES;
+      if (kb >= OZ_STAGES && !mbar_wait(&empty[st], ((kb / OZ_STAGES) - 1) & 1)) {
+        atomicOr(s_fail, 1);
+        break;
+      }
+      if (*(volatile int*)s_fail) break;
+      unsigned char* sb = base + st * stage_bytes;
+      mbar_arrive_expect_tx(&full[st], (uint32_t)stage_bytes);
+      for (int p = 0; p < s; ++p)
+        tma_load_3d(sb + p * OZ_A_TILE, &tmA, &full[st], kb * OZ_BK, m0, p);
+      for (int q = 0; q < s; ++q)
+        tma_load_4d(sb + s * OZ_A_TILE + q * OZ_B_TILE, &tmB, &full[st], kb * OZ_BK, n0, q, b);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer ---------------------------------------------------------
+    const uint32_t idesc = oz_idesc();
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int st = kb % OZ_STAGES;
+      if (!mbar_wait(&full[st], (kb / OZ_STAGES) & 1)) {
+        atomicOr(s_fail, 1);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t sa = smem_u32(base + st * stage_bytes);
+      const uint32_t sbB = sa + s * OZ_A_TILE;
+      for (int kk = 0; kk < OZ_BK / 16; ++kk) {
+        for (int i = 0; i < pr.n; ++i) {
+          const uint64_t ad = smem_desc_sw64(sa + pr.p[i] * OZ_A_TILE + kk * 32);
+          const uint64_t bd = smem_desc_sw64(sbB + pr.q[i] * OZ_B_TILE + kk * 32);
+          const uint32_t acc = (kb == 0 && kk == 0 && pr.first[i]) ? 0u : 1u;
+          umma(tmem + pr.g[i] * OZ_BN, ad, bd, idesc, acc);
+        }
+      }
+      umma_commit(&empty[st]);   // frees the stage once these MMAs have read it
+    }
+    umma_commit(done);
+  }
+  __syncthreads();
+
+  // ---- epilogue: accumulators -> int64 combination -> FP64 -----------------
+  bool ok = !*(volatile int*)s_fail && mbar_wait(done, 0);
+  ok = __syncthreads_and(ok) != 0;   // uniform: tcgen05.ld is warp-collective
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const int row = m0 + warp * 32 + lane;
+  const int ea = row < N ? eA[row] : 0;
+  const int* eBb = eB + (long long)b * seB;
+  double* Cb = C + (long long)b * sC;
+  const int shift0 = 7 * (s + 1);
+  if (ok) {
+    for (int c0 = 0; c0 < OZ_BN; c0 += 16) {
+      long long acc[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) acc[j] = 0;
+      for (int g = 0; g < pr.ngroups; ++g) {
+        uint32_t r[16];
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + g * OZ_BN + c0, r);
+        const int sh = pr.shift[g];
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          acc[j] += (long long)__float2ll_rn(__uint_as_float(r[j])) << sh;
+      }
+      if (row < N) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int col = n0 + c0 + j;
+          if (col < N) {
+            const double v = scale_pow2(__ll2double_rn(acc[j]), ea + eBb[col] - shift0);
+            Cb[(long long)row * N + col] = v;
+          }
+        }
+      }
+    }
+  } else if (tid == 0 && status) {
+    atomicOr(&status[b], DQMC_STATUS_TIMEOUT);
+  }
+  // on failure, let in-flight copies land before the CTA exits (bounded)
+  if (!ok && warp == 0 && lane == 0) {
+    for (int i = 0; i < OZ_STAGES; ++i) mbar_wait(&full[i], 0);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(tmem_cols)
+                 : "memory");
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Splitting kernel: X (FP64, element (m, j) at X[m*ldm + j*ldj]) times an
+// optional scale sc[m] -> s BF16 slice planes S[q][j][m] (K-major, PJ x PM per
+// plane, zero padded) and column exponents e[j] with max_m |x_mj| < 2^{e_j}.
+// One CTA per 32 columns j of one instance; 256 threads.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+ozaki_split_kernel(const double* __restrict__ X, long long ldm, long long ldj, long long sX,
+                   const double* __restrict__ sc, long long ssc, int N, int PJ, int PM, int s,
+                   __nv_bfloat16* __restrict__ S, long long sS, int* __restrict__ e,
+                   long long se) {
+  extern __shared__ double tile[];   // [PM][33]
+  __shared__ int emax[8][32];
+  const int b = blockIdx.y;
+  const int j0 = blockIdx.x * 32;
+  const int tid = threadIdx.x, jj = tid & 31, rg = tid >> 5;
+  const double* Xb = X + (long long)b * sX;
+  const double* scb = sc ? sc + (long long)b * ssc : nullptr;
+  const int j = j0 + jj;
+  int mx = -2000;
+  for (int m = rg; m < PM; m += 8) {
+    double v = 0.0;
+    if (m < N && j < N) {
+      v = Xb[(long long)m * ldm + (long long)j * ldj];
+      if (scb) v *= scb[m];
+    }
+    tile[m * 33 + jj] = v;
+    if (v != 0.0) {
+      int ex = (int)((__double_as_longlong(v) >> 52) & 0x7ff);
+      if (ex > mx) mx = ex;
+    }
+  }
+  emax[rg][jj] = mx;
+  __syncthreads();
+  if (tid < 32) {
+    int m2 = emax[0][tid];
+    for (int r = 1; r < 8; ++r) m2 = max(m2, emax[r][tid]);
+    // biased exponent E of the largest entry: max < 2^{E-1022}
+    emax[0][tid] = (m2 == -2000 || m2 == 0) ? 0 : m2 - 1022;
+    if (j0 + tid < PJ) e[(long long)b * se + j0 + tid] = (m2 == -2000 || m2 == 0) ? 0 : m2 - 1022;
+  }
+  __syncthreads();
+  __nv_bfloat16* Sb = S + (long long)b * sS;
+  const long long plane = (long long)PJ * PM;
+  for (int c = 0; c < 32; ++c) {
+    const int jc = j0 + c;
+    if (jc >= PJ) break;
+    const int ecol = emax[0][c];
+    for (int m = tid; m < PM; m += 256) {
+      const double v = tile[m * 33 + c];
+      unsigned long long F = 0;   // |v| 2^{-ecol} * 2^63 (a fraction below 1 in 63 bits)
+      const long long bits = __double_as_longlong(v);
+      const int E = (int)((bits >> 52) & 0x7ff);
+      if (E != 0) {
+        const unsigned long long m53 = ((unsigned long long)bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+        const int sh = E - 1012 - ecol;   // F = m53 * 2^sh, sh <= 10
+        F = sh >= 0 ? (m53 << sh) : (sh > -64 ? (m53 >> (-sh)) : 0ull);
+      }
+      const bool neg = bits < 0;
+      for (int q = 0; q < s; ++q) {
+        int a = (int)((F >> (56 - 7 * q)) & 127ull);   // fraction bits 2^{-7q-1}..2^{-7q-7}
+        if (neg) a = -a;
+        Sb[q * plane + (long long)jc * PM + m] = __int2bfloat16_rn(a);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+OzPairs oz_pairs(int s, int N) {
+  OzPairs pr{};
+  pr.s = s;
+  const int per_group = N <= 256 ? 4 : (N <= 512 ? 2 : 1);
+  const int tmax = s + 1;
+  int n = 0, g = 0;
+  for (int t = 2; t <= tmax; ++t) {
+    int in_group = per_group;   // forces a new group at each t
+    for (int p = 1; p <= s; ++p) {
+      const int q = t - p;
+      if (q < 1 || q > s) continue;
+      if (in_group == per_group) {
+        pr.shift[g] = 7 * (tmax - t);
+        ++g;
+        in_group = 0;
+      }
+      pr.p[n] = (unsigned char)(p - 1);
+      pr.q[n] = (unsigned char)(q - 1);
+      pr.g[n] = (unsigned char)(g - 1);
+      pr.first[n] = in_group == 0;
+      ++in_group;
+      ++n;
+    }
+  }
+  pr.n = n;
+  pr.ngroups = g;
+  return pr;
+}
+
+int oz_groups(int s, int N) { return oz_pairs(s, N).ngroups; }
+
+size_t oz_gemm_smem(int s) {
+  return (size_t)OZ_STAGES * s * (OZ_A_TILE + OZ_B_TILE) + 1024 + 256;
+}
+
+cudaError_t ozaki_split(const double* X, long long ldm, long long ldj, long long sX,
+                        const double* sc, long long ssc, int N, int PJ, int PM, int s,
+                        __nv_bfloat16* S, long long sS, int* e, long long se, int batch,
+                        cudaStream_t st) {
+  size_t sm = (size_t)PM * 33 * sizeof(double);
+  cudaFuncSetAttribute(ozaki_split_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  dim3 grid((PJ + 31) / 32, batch);
+  ozaki_split_kernel<<<grid, 256, sm, st>>>(X, ldm, ldj, sX, sc, ssc, N, PJ, PM, s, S, sS, e, se);
+  return cudaGetLastError();
+}
+
+// C_b = 2^{eA} As * (2^{eB_b} Bs_b)  for b < batch.  As: s planes of P128 x PK
+// (rows i, K contiguous), Bs: per instance s planes of PN x PK (columns j, K
+// contiguous); PK, PN multiples of 64, P128 a multiple of 128.
+cudaError_t ozaki_gemm(const __nv_bfloat16* As, const int* eA, int P128, const __nv_bfloat16* Bs,
+                       const int* eB, long long seB, int PN, int PK, int s, int N, int batch,
+                       double* C, long long sC, int* status, cudaStream_t st) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return cudaErrorNotSupported;
+  CUtensorMap tA, tB;
+  {
+    cuuint64_t dims[3] = {(cuuint64_t)PK, (cuuint64_t)P128, (cuuint64_t)s};
+    cuuint64_t strides[2] = {(cuuint64_t)PK * 2, (cuuint64_t)PK * P128 * 2};
+    cuuint32_t box[3] = {OZ_BK, OZ_BM, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    if (enc(&tA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)As, dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
+  }
+  {
+    cuuint64_t dims[4] = {(cuuint64_t)PK, (cuuint64_t)PN, (cuuint64_t)s, (cuuint64_t)batch};
+    cuuint64_t strides[3] = {(cuuint64_t)PK * 2, (cuuint64_t)PK * PN * 2,
+                             (cuuint64_t)PK * PN * s * 2};
+    cuuint32_t box[4] = {OZ_BK, OZ_BN, 1, 1};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    if (enc(&tB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)Bs, dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
+  }
+  OzPairs pr = oz_pairs(s, N);
+  if (pr.ngroups > 8) return cudaErrorNotSupported;
+  size_t sm = oz_gemm_smem(s);
+  cudaFuncSetAttribute(ozaki_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  dim3 grid((N + OZ_BN - 1) / OZ_BN, (N + OZ_BM - 1) / OZ_BM, batch);
+  ozaki_gemm_kernel<<<grid, OZ_THREADS, sm, st>>>(tA, tB, pr, N, PK / OZ_BK, eA, eB, seB, C, sC,
+                                                  status);
+  return cudaGetLastError();
+}
+
+}  // namespace dqmc
