@@ -58,9 +58,9 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
-    p.add_argument("--precision", default="fp64", choices=["fp64", "bf16x3", "bf16x4", "bf16x5", "bf16x6"],
+    p.add_argument("--precision", default="fp64", choices=["fp64"] + [f"bf16x{i}" for i in range(3, 9)],
                    help="chain-product precision of the timed steps (QR and inversions stay FP64)")
-    p.add_argument("--mixed-slices", type=int, default=6,
+    p.add_argument("--mixed-slices", type=int, default=8,
                    help="also time the mixed chain with this many BF16 slices (0: skip)")
     return p.parse_args()
 

@@ -71,17 +71,20 @@ enum dqmc_status_bits {
 
 /* Precision of the k-slice chain products (a mixed-precision option; the
  * pivoted QR, the D splits and the inversions always run in FP64).
- * DQMC_CHAIN_BF16Xs: each FP64 operand is cut into s BF16 slices of 7 bits
- * (error-free splitting with power-of-two row/column scales), the slice
- * products accumulate exactly in FP32 on the tcgen05 tensor cores and are
- * recombined in FP64; the product is accurate to about 2^{-7s} of the row x
- * column scale.  Supported for N <= 256 in dqmc_greens / dqmc_logdet. */
+ * DQMC_CHAIN_BF16Xs: each FP64 operand is written in s balanced base-128
+ * digits held in BF16 (error-free splitting with power-of-two row/column
+ * scales), the digit products accumulate exactly in FP32 on the tcgen05
+ * tensor cores and are recombined in FP64; a product is accurate to about
+ * N 2^{-7s-1} of (row max x column max), normwise rather than elementwise.
+ * Supported for N <= 256 in dqmc_greens / dqmc_logdet. */
 typedef enum {
   DQMC_CHAIN_FP64 = 0,
   DQMC_CHAIN_BF16X3 = 3,
   DQMC_CHAIN_BF16X4 = 4,
   DQMC_CHAIN_BF16X5 = 5,
-  DQMC_CHAIN_BF16X6 = 6
+  DQMC_CHAIN_BF16X6 = 6,
+  DQMC_CHAIN_BF16X7 = 7,
+  DQMC_CHAIN_BF16X8 = 8
 } dqmc_chain_prec;
 
 typedef enum { DQMC_PTR_DEVICE = 0, DQMC_PTR_HOST = 1 } dqmc_pointer_mode;
@@ -97,6 +100,9 @@ dqmc_status dqmc_destroy(dqmc_handle h);
 dqmc_status dqmc_set_stream(dqmc_handle h, void* stream);
 dqmc_status dqmc_set_pointer_mode(dqmc_handle h, dqmc_pointer_mode mode);
 dqmc_status dqmc_set_chain_precision(dqmc_handle h, dqmc_chain_prec prec);
+/* Tile edge of the FP64 slice products: 0 = chosen by size (default), 32 or
+ * 64.  A tuning knob for the autotuner (paper_2003_05286_gb300/tune.py). */
+dqmc_status dqmc_set_gemm_tile(dqmc_handle h, int tile);
 /* Number of kernel launches issued by the most recent compute call. */
 long long dqmc_last_launch_count(dqmc_handle h);
 /* Bytes of device workspace the handle currently holds. */

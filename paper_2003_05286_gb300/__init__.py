@@ -58,6 +58,9 @@ class Handle:
         s = stream if stream is not None else torch.cuda.current_stream()
         _abi.check(self._lib.dqmc_set_stream(self.h, C.c_void_p(s.cuda_stream)), "dqmc_set_stream")
 
+    def set_gemm_tile(self, tile: int):
+        _abi.check(self._lib.dqmc_set_gemm_tile(self.h, int(tile)), "dqmc_set_gemm_tile")
+
     def set_pointer_mode(self, host: bool):
         _abi.check(self._lib.dqmc_set_pointer_mode(self.h, _abi.PTR_HOST if host else _abi.PTR_DEVICE),
                    "dqmc_set_pointer_mode")

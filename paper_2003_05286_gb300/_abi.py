@@ -40,6 +40,7 @@ SIGNATURES = {
     "dqmc_set_stream": (_I, [_P, _P]),
     "dqmc_set_pointer_mode": (_I, [_P, _I]),
     "dqmc_set_chain_precision": (_I, [_P, _I]),
+    "dqmc_set_gemm_tile": (_I, [_P, _I]),
     "dqmc_last_launch_count": (C.c_longlong, [_P]),
     "dqmc_workspace_bytes": (C.c_longlong, [_P]),
     "dqmc_status_string": (C.c_char_p, [_I]),

@@ -36,6 +36,7 @@ struct dqmc_handle_s {
   cudaStream_t stream = nullptr;
   dqmc_pointer_mode pmode = DQMC_PTR_DEVICE;
   dqmc_chain_prec prec = DQMC_CHAIN_FP64;
+  int gemm_tile = 0;
   char* ws = nullptr;
   size_t ws_bytes = 0;
   long long launches = 0;
@@ -298,6 +299,7 @@ dqmc_status chunk_products(dqmc_handle h, int dir, int batch, int N, int M, int 
     g.B = prev; g.ldb = N; g.sB = sprev;
     g.C = bufs[nb]; g.ldc = N; g.sC = NN;
     g.lim = lim; g.lim_at = l;
+    g.tile = h->gemm_tile;
     if (dir > 0) {
       g.ms = expV + (long long)(l - 1) * N; g.sms = sV;      // E diag(e^{V_l}) A
     } else {
@@ -600,9 +602,15 @@ dqmc_status dqmc_set_pointer_mode(dqmc_handle h, dqmc_pointer_mode mode) {
 
 dqmc_status dqmc_set_chain_precision(dqmc_handle h, dqmc_chain_prec prec) {
   if (!h) return DQMC_ERR_ARG;
-  if (prec != DQMC_CHAIN_FP64 && (prec < DQMC_CHAIN_BF16X3 || prec > DQMC_CHAIN_BF16X6))
+  if (prec != DQMC_CHAIN_FP64 && (prec < DQMC_CHAIN_BF16X3 || prec > DQMC_CHAIN_BF16X8))
     return DQMC_ERR_ARG;
   h->prec = prec;
+  return DQMC_OK;
+}
+
+dqmc_status dqmc_set_gemm_tile(dqmc_handle h, int tile) {
+  if (!h || (tile != 0 && tile != 32 && tile != 64)) return DQMC_ERR_ARG;
+  h->gemm_tile = tile;
   return DQMC_OK;
 }
 

@@ -45,6 +45,7 @@ struct GemmArgs {
   // shared operand can be indexed per group of bdiv problems): pointer of
   // operand X is base + (b / divX) * sX.
   int divA = 1, divB = 1, divC = 1, divS = 1;
+  int tile = 0;   // CTA tile edge: 0 = by size, 32 or 64
 };
 
 cudaError_t gemm_f64(const GemmArgs& a, cudaStream_t st);

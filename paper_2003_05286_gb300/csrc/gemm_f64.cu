@@ -159,7 +159,8 @@ gemm_f64_kernel(const GemmArgs a) {
 cudaError_t gemm_f64(const GemmArgs& a, cudaStream_t st) {
   if (a.batch <= 0 || a.M <= 0 || a.N <= 0) return cudaSuccess;
   const int zb = a.batch < 65535 ? a.batch : 65535;   // grid z limit; the kernel loops
-  if (a.M >= 96 && a.N >= 96) {
+  const bool big = a.tile ? a.tile == 64 : (a.M >= 96 && a.N >= 96);
+  if (big) {
     constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4;
     dim3 grid((a.N + BN - 1) / BN, (a.M + BM - 1) / BM, zb);
     gemm_f64_kernel<BM, BN, BK, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, st>>>(a);

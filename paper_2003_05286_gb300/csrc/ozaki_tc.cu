@@ -7,17 +7,22 @@
 // error-free splitting of Ozaki et al. (Numer. Algorithms 59, 2012):
 //
 //   * every row i of E is scaled by 2^{-eA_i} and every column j of B' by
-//     2^{-eB_j} so that all entries lie in (-1, 1); each scaled entry is cut
-//     into s slices of 7 bits (x = sum_p a_p 2^{-7p} + O(2^{-7s}), a_p integer
-//     in [-127, 127]) -- integers of at most 8 significant bits, exact in BF16;
-//   * a slice product a_p . b_q is a sum of K <= 256 integers below 2^14, so it
-//     is an integer below 2^22 and the FP32 accumulation of the tensor core is
-//     exact; products with the same weight 2^{-7(p+q)} share one TMEM
-//     accumulator as long as at most 4 of them meet (sum < 2^24);
+//     2^{-eB_j} so that all entries lie in (-1/2, 1/2); each scaled entry is
+//     written in s balanced base-128 digits (x = sum_p a_p 2^{-7p} + r,
+//     |r| <= 2^{-7s-1}, a_p integer in [-64, 64], each digit rounded to
+//     nearest and its remainder carried to the next) -- integers of at most 7
+//     significant bits, exact in BF16;
+//   * a digit product a_p . b_q is a sum of K <= 256 integers of magnitude
+//     <= 2^12, so it is an integer below 2^20 and the FP32 accumulation of the
+//     tensor core is exact; products with the same weight 2^{-7(p+q)} share
+//     one TMEM accumulator (up to 16 of them, sum < 2^24);
 //   * only p + q <= s + 1 is formed (the rest is below the truncation error);
-//   * the epilogue adds the accumulators in int64 with their relative shifts
-//     and rebuilds the FP64 value by integer exponent arithmetic, so no FP64
-//     pipe time is spent on the products at all.
+//   * the epilogue adds the accumulators in two int64 partial sums with their
+//     relative shifts and rebuilds the FP64 value with two conversions and
+//     one FMA per output element.
+// The product is accurate to about N 2^{-7s-1} of (row max x column max):
+// normwise, not elementwise -- entries much smaller than their column's
+// largest keep correspondingly fewer digits.
 //
 // Per CTA: one 128 x 64 output tile of one instance; 4 warps; warp 0 issues the
 // TMA loads of the s A-slice tiles (128 x 32 BF16) and s B-slice tiles
@@ -166,13 +171,13 @@ __device__ __forceinline__ double scale_pow2(double x, int e) {
 
 }  // namespace
 
-// Pair table: up to 21 (p, q) slice pairs with their accumulator group.
+// Pair table: up to 36 (p, q) digit pairs (s <= 8) with their accumulator group.
 struct OzPairs {
   int n;                 // number of pairs
   int ngroups;           // accumulators (<= 8)
   int s;                 // slices per operand
-  int shift[8];          // left shift (bits) of group g in the int64 combination
-  unsigned char p[24], q[24], g[24], first[24];
+  int shift[8];          // weight 2^{shift} of group g relative to the lowest kept weight
+  unsigned char p[40], q[40], g[40], first[40];
 };
 
 __global__ void __launch_bounds__(OZ_THREADS, 1)
@@ -272,24 +277,31 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
   const int shift0 = 7 * (s + 1);
   if (ok) {
     for (int c0 = 0; c0 < OZ_BN; c0 += 16) {
-      long long acc[16];
+      // two exact int64 partial sums: weights >= 2^32 (hi, in units of 2^32) and below
+      long long hi[16], lo[16];
 #pragma unroll
-      for (int j = 0; j < 16; ++j) acc[j] = 0;
+      for (int j = 0; j < 16; ++j) { hi[j] = 0; lo[j] = 0; }
       for (int g = 0; g < pr.ngroups; ++g) {
         uint32_t r[16];
         tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + g * OZ_BN + c0, r);
         const int sh = pr.shift[g];
+        if (sh >= 32) {
 #pragma unroll
-        for (int j = 0; j < 16; ++j)
-          acc[j] += (long long)__float2ll_rn(__uint_as_float(r[j])) << sh;
+          for (int j = 0; j < 16; ++j)
+            hi[j] += (long long)__float2ll_rn(__uint_as_float(r[j])) << (sh - 32);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            lo[j] += (long long)__float2ll_rn(__uint_as_float(r[j])) << sh;
+        }
       }
       if (row < N) {
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           const int col = n0 + c0 + j;
           if (col < N) {
-            const double v = scale_pow2(__ll2double_rn(acc[j]), ea + eBb[col] - shift0);
-            Cb[(long long)row * N + col] = v;
+            const double sum = fma(__ll2double_rn(hi[j]), 4294967296.0, __ll2double_rn(lo[j]));
+            Cb[(long long)row * N + col] = scale_pow2(sum, ea + eBb[col] - shift0);
           }
         }
       }
@@ -347,9 +359,10 @@ ozaki_split_kernel(const double* __restrict__ X, long long ldm, long long ldj, l
   if (tid < 32) {
     int m2 = emax[0][tid];
     for (int r = 1; r < 8; ++r) m2 = max(m2, emax[r][tid]);
-    // biased exponent E of the largest entry: max < 2^{E-1022}
-    emax[0][tid] = (m2 == -2000 || m2 == 0) ? 0 : m2 - 1022;
-    if (j0 + tid < PJ) e[(long long)b * se + j0 + tid] = (m2 == -2000 || m2 == 0) ? 0 : m2 - 1022;
+    // biased exponent E of the largest entry: max < 2^{E-1022}, so the scaled
+    // entries x 2^{-(E-1021)} lie in (-1/2, 1/2)
+    emax[0][tid] = (m2 == -2000 || m2 == 0) ? 0 : m2 - 1021;
+    if (j0 + tid < PJ) e[(long long)b * se + j0 + tid] = (m2 == -2000 || m2 == 0) ? 0 : m2 - 1021;
   }
   __syncthreads();
   __nv_bfloat16* Sb = S + (long long)b * sS;
@@ -360,19 +373,20 @@ ozaki_split_kernel(const double* __restrict__ X, long long ldm, long long ldj, l
     const int ecol = emax[0][c];
     for (int m = tid; m < PM; m += 256) {
       const double v = tile[m * 33 + c];
-      unsigned long long F = 0;   // |v| 2^{-ecol} * 2^63 (a fraction below 1 in 63 bits)
+      unsigned long long F = 0;   // |v| 2^{-ecol} * 2^63, below 2^62
       const long long bits = __double_as_longlong(v);
       const int E = (int)((bits >> 52) & 0x7ff);
       if (E != 0) {
         const unsigned long long m53 = ((unsigned long long)bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-        const int sh = E - 1012 - ecol;   // F = m53 * 2^sh, sh <= 10
+        const int sh = E - 1012 - ecol;   // F = m53 * 2^sh, sh <= 9
         F = sh >= 0 ? (m53 << sh) : (sh > -64 ? (m53 >> (-sh)) : 0ull);
       }
-      const bool neg = bits < 0;
+      long long S = bits < 0 ? -(long long)F : (long long)F;
       for (int q = 0; q < s; ++q) {
-        int a = (int)((F >> (56 - 7 * q)) & 127ull);   // fraction bits 2^{-7q-1}..2^{-7q-7}
-        if (neg) a = -a;
-        Sb[q * plane + (long long)jc * PM + m] = __int2bfloat16_rn(a);
+        const int sh = 56 - 7 * q;                      // digit weight 2^{-7(q+1)}
+        const long long d = (S + (1ll << (sh - 1))) >> sh;   // nearest, in [-64, 64]
+        S -= d << sh;
+        Sb[q * plane + (long long)jc * PM + m] = __int2bfloat16_rn((int)d);
       }
     }
   }
@@ -405,7 +419,8 @@ static EncodeTiledFn encode_fn() {
 OzPairs oz_pairs(int s, int N) {
   OzPairs pr{};
   pr.s = s;
-  const int per_group = N <= 256 ? 4 : (N <= 512 ? 2 : 1);
+  // digit products are below N 2^12; 2^24 / (N 2^12) of them fit one FP32 accumulator exactly
+  const int per_group = N <= 256 ? 16 : (N <= 512 ? 8 : 4);
   const int tmax = s + 1;
   int n = 0, g = 0;
   for (int t = 2; t <= tmax; ++t) {
@@ -478,8 +493,9 @@ cudaError_t ozaki_gemm(const __nv_bfloat16* As, const int* eA, int P128, const _
             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return cudaErrorInvalidValue;
   }
+  if (s < 1 || s > 8) return cudaErrorInvalidValue;
   OzPairs pr = oz_pairs(s, N);
-  if (pr.ngroups > 8) return cudaErrorNotSupported;
+  if (pr.ngroups > 8 || pr.n > 40) return cudaErrorNotSupported;
   size_t sm = oz_gemm_smem(s);
   cudaFuncSetAttribute(ozaki_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   dim3 grid((N + OZ_BN - 1) / OZ_BN, (N + OZ_BM - 1) / OZ_BM, batch);

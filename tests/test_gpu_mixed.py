@@ -4,7 +4,7 @@ Only the k-slice products change precision; QR, D splits and inversions stay
 FP64.  The error of G against the FP64 oracle is a property of the slicing
 (about N 2^{-7s} per product, amplified by the chain) and is reported rather
 than pinned by the paper; these tests check that it shrinks with the slice
-count and that six slices reach 1e-8 in G and 1e-9 relative in log det.
+count and that eight slices reach 1e-8 in G and 1e-9 relative in log det.
 """
 import numpy as np
 import pytest
@@ -48,18 +48,18 @@ def _errors(dq, insts, s):
 @pytest.mark.parametrize("L,beta", [(4, 8.0), (8, 10.0), (10, 6.0)])
 def test_mixed_error_decreases_with_slices(dq, L, beta):
     insts = [di.hubbard_instance(L, 4.0, 0.1, beta, 10, 500 + i) for i in range(3)]
-    errs = {s: _errors(dq, insts, s) for s in (3, 4, 5, 6)}
+    errs = {s: _errors(dq, insts, s) for s in (4, 6, 8)}
     print({s: f"dG {e[0]:.2e} dlogdet {e[1]:.2e}" for s, e in errs.items()})
-    assert errs[6][0] <= 1e-8 and errs[6][1] <= 1e-9
-    assert errs[5][0] < errs[3][0]
+    assert errs[8][0] <= 1e-8 and errs[8][1] <= 1e-9
+    assert errs[8][0] < errs[6][0] < errs[4][0]
 
 
 def test_mixed_full_size_sampled(dq):
-    """16x16 lattice, beta = 20, 128 instances, six slices: instances 0 and 127."""
+    """16x16 lattice, beta = 20, 128 instances, eight slices: instances 0 and 127."""
     insts = [di.batch_n256(i) for i in range(128)]
     K = _dev(insts[0].K)
     V = _dev(np.stack([x.V for x in insts]))
-    h = dq.Handle(chain_precision=6)
+    h = dq.Handle(chain_precision=8)
     G, ld, sg, st = dq.greens(K, 0.1, V, 10, handle=h)
     assert int((st != 0).sum()) == 0
     for b in (0, 127):
