@@ -41,8 +41,14 @@ import dqmc_inputs as di  # noqa: E402
 FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12
 
 WORKLOADS = {
+    # equal-time G + log det (the headline workload)
     "n256_beta20": dict(L=16, U=4.0, dtau=0.1, beta=20.0, k=10, batch=128, config=4),
-    "n64_beta40": dict(L=8, U=4.0, dtau=0.1, beta=40.0, k=10, batch=256, config=2),
+    # G(tau_j, tau_j) and G(tau_j, 0) on the k-grid
+    "tdisplaced_n64": dict(L=8, U=4.0, dtau=0.1, beta=40.0, k=10, batch=256, config=2),
+    # log det + gradient for all N*M field entries (continuous field)
+    "grad_n144": dict(L=12, g=1.5, dtau=0.1, beta=20.0, k=10, batch=64, config=5),
+    # 1024 instances of uneven N and M in one call, k autotuned per N
+    "ragged_1024": dict(batch=1024, config=3),
     "n16_beta8": dict(L=4, U=4.0, dtau=0.1, beta=8.0, k=10, batch=1, config=1),
 }
 
@@ -91,6 +97,21 @@ def reduce_max(x: float, device=None) -> float:
 def job_value(batch: int, world: int, steps: int, max_ms: float) -> float:
     """Whole-job Green's functions per second: all ranks' instances / slowest rank's time."""
     return batch * world * steps / (max_ms / 1e3)
+
+
+def flops_per_tdisplaced(N: int, M: int, k: int) -> float:
+    """Two stacks + per grid point: 2 products for the middle matrix, LU with
+    2N right-hand sides, 2 products for G(tau,tau) and G(tau,0)."""
+    nc = -(-M // k)
+    return (2 * (2.0 * M + nc * (8.0 / 3.0 + 1.0)) + (nc + 1) * (4 + 2.0 / 3.0 + 4 + 4)) * N ** 3
+
+
+def flops_per_grad(N: int, M: int, k: int) -> float:
+    """Two stacks + checkpoint G (2 products, LU, 1 product) + k-1 wraps (2 products
+    each) per grid point + the log det."""
+    nc = -(-M // k)
+    return (2 * (2.0 * M + nc * (8.0 / 3.0 + 1.0)) + (nc + 1) * (4 + 2.0 / 3.0 + 2 + 2)
+            + (nc + 1) * (k - 1) * 4 + 2 * (2.0 / 3.0) + 2.0) * N ** 3
 
 
 def flops_per_greens(N: int, M: int, k: int) -> float:
@@ -155,7 +176,7 @@ class ClockSampler:
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("gemm_f64.cu", "common.cuh"):
+    for f in ("gemm_f64.cu",):
         with open(os.path.join(ROOT, "paper_2003_05286_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -193,6 +214,10 @@ def cpu_oracle_rate(insts, seconds: float):
 
 def run_reference(args, wl, rank, world):
     if rank != 0:
+        return
+    if "U" not in wl:
+        print(json.dumps({"impl": "reference", "unavailable":
+                          f"the CPU oracle arm is timed on the equal-time workloads only ({args.workload})"}))
         return
     batch = args.batch or wl["batch"]
     K, V, insts = make_inputs(wl, 0, min(batch, 8))
@@ -393,6 +418,104 @@ def run_gpu(args, wl, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_gpu_other(args, wl, rank, world):
+    """The other workloads: same timing rules, whole-step FP64 roofline."""
+    import torch
+    import paper_2003_05286_gb300 as dq
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    batch = args.batch or wl["batch"]
+    name = args.workload
+    h = dq.Handle()
+    h.bind_stream()
+    extra = {}
+    if name == "ragged_1024":
+        from paper_2003_05286_gb300 import tune
+        insts0 = [di.ragged_params(rank * batch + i) for i in range(batch)]
+        # k per lattice size: tuned on 4 instances at the largest beta of the group
+        kbyL = {}
+        for L in sorted({p[0] for p in insts0}):
+            idx = [i for i, p in enumerate(insts0) if p[0] == L]
+            mx = max(idx, key=lambda i: insts0[i][1])
+            sample = [di.ragged_instance(rank * batch + i, 10) for i in idx[:3] + [mx]]
+            Mmin = min(x.M for x in sample)
+            Ks = torch.tensor(sample[0].K, device=dev)
+            Vs = torch.tensor(np.stack([x.V[:Mmin] for x in sample]), device=dev)
+            best, _ = tune.tune(Ks, 0.1, Vs, candidates=(5, 10, 15, 20), tiles=(0,), ref_k=2, tol=1e-10)
+            kbyL[L] = best["k"]
+        insts = [di.ragged_instance(rank * batch + i, kbyL[p[0]]) for i, p in enumerate(insts0)]
+        extra["k_by_L"] = kbyL
+        items = [(torch.tensor(x.K, device=dev), x.dtau, torch.tensor(x.V, device=dev), x.k) for x in insts]
+        fl = sum(flops_per_greens(x.N, x.M, x.k) for x in insts)
+
+        def step():
+            return dq.greens_ragged(items, handle=h)
+        metric, unit = "greens_functions_per_second", "G/s"
+    else:
+        if name == "grad_n144":
+            insts = [di.gaussian_instance(wl["L"], wl["g"], wl["dtau"], wl["beta"], wl["k"], sd)
+                     for sd in rank_seeds(wl, rank, batch)]
+        else:
+            insts = [di.hubbard_instance(wl["L"], wl["U"], wl["dtau"], wl["beta"], wl["k"], sd)
+                     for sd in rank_seeds(wl, rank, batch)]
+        K = torch.tensor(insts[0].K, device=dev)
+        V = torch.tensor(np.stack([x.V for x in insts]), device=dev)
+        N, M, k = insts[0].N, insts[0].M, wl["k"]
+        if name == "tdisplaced_n64":
+            fl = batch * flops_per_tdisplaced(N, M, k)
+
+            def step():
+                return dq.greens_tdisplaced(K, wl["dtau"], V, k, handle=h)
+            metric, unit = "tdisplaced_sets_per_second", "sets/s"
+        elif name == "grad_n144":
+            fl = batch * flops_per_grad(N, M, k)
+
+            def step():
+                return dq.logdet_grad(K, wl["dtau"], V, k, handle=h)
+            metric, unit = "logdet_gradients_per_second", "grads/s"
+        else:
+            fl = batch * flops_per_greens(N, M, k)
+
+            def step():
+                return dq.greens(K, wl["dtau"], V, k, handle=h)
+            metric, unit = "greens_functions_per_second", "G/s"
+        extra.update(N=N, M=M, k=k)
+    for _ in range(args.warmup):
+        out = step()
+    torch.cuda.synchronize()
+    launches = h.last_launch_count
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clocks = ClockSampler(dev.index)
+    torch.cuda.synchronize()
+    clocks.start()
+    for s_ in range(args.steps):
+        flush.fill_(float(s_))
+        ev[s_][0].record()
+        out = step()
+        ev[s_][1].record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    tot = reduce_max(sum(a.elapsed_time(b) for a, b in ev), dev)
+    st = out[-1]
+    if rank != 0:
+        return
+    ach = fl * args.steps / (tot / 1e3) / 1e12
+    line = {"metric": metric, "value": job_value(batch, world, args.steps, tot), "unit": unit,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": tot / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(workload=name, instances_per_gpu=batch,
+                           l2="flushed between timed steps (256 MB write)", **extra),
+            "roofline": {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                         "kernel": "whole step (all kernels), algorithmic FP64 flops"},
+            "gpu_launches": launches * args.steps, "clocks": clk,
+            "status_nonzero": int((st != 0).sum().item()), "e2e": None, "cpu_baseline": None}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     wl = WORKLOADS[args.workload]
@@ -407,7 +530,10 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         tdist.init_process_group("nccl")
     try:
-        run_gpu(args, wl, rank, world)
+        if args.workload == "n256_beta20":
+            run_gpu(args, wl, rank, world)
+        else:
+            run_gpu_other(args, wl, rank, world)
     finally:
         if world > 1:
             import torch.distributed as tdist

@@ -14,7 +14,8 @@
 
 namespace dqmc {
 
-template <int NT>
+// RPT * NT >= N: rows of the pivot column each thread keeps in registers.
+template <int NT, int RPT>
 __global__ void __launch_bounds__(NT) lu_kernel(const LuArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int N = a.N, nr = a.nrhs, Wd = N + nr;
@@ -60,13 +61,20 @@ __global__ void __launch_bounds__(NT) lu_kernel(const LuArgs a) {
     __syncthreads();
 
     // ---- elimination with partial pivoting -------------------------------
+    // Per column j, three barriers: (1) candidates of the pivot search (the
+    // column is kept in registers), (2) multipliers + row swap, (3) update.
     for (int j = 0; j < N; ++j) {
+      double x[RPT];
       unsigned long long key = 0ull;   // |a_rj| bits (sign cleared), ordered like the values
       int idx = 0x7fffffff;
-      for (int r = j + tid; r < N; r += NT) {
-        unsigned long long k2 =
-            (unsigned long long)__double_as_longlong(W[(long long)r * Wd + j]) & 0x7fffffffffffffffull;
-        if (k2 > key || (k2 == key && r < idx)) { key = k2; idx = r; }
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) {
+        const int r = j + tid + q * NT;
+        x[q] = r < N ? W[(long long)r * Wd + j] : 0.0;
+        if (r < N) {
+          unsigned long long k2 = (unsigned long long)__double_as_longlong(x[q]) & 0x7fffffffffffffffull;
+          if (k2 > key || (k2 == key && r < idx)) { key = k2; idx = r; }
+        }
       }
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) {
@@ -75,31 +83,28 @@ __global__ void __launch_bounds__(NT) lu_kernel(const LuArgs a) {
         if (k2 > key || (k2 == key && i2 < idx)) { key = k2; idx = i2; }
       }
       if (lane == 0) { sk[wid] = key; si[wid] = idx; }
+      const double ajj = W[(long long)j * Wd + j];
       __syncthreads();
-      if (wid == 0) {
-        key = lane < NT / 32 ? sk[lane] : 0ull;
-        idx = lane < NT / 32 ? si[lane] : 0x7fffffff;
+      key = sk[0];
+      idx = si[0];
+      for (int w = 1; w < NT / 32; ++w)
+        if (sk[w] > key || (sk[w] == key && si[w] < idx)) { key = sk[w]; idx = si[w]; }
+      const int p = (idx >= j && idx < N) ? idx : j;
+      const double piv = p == j ? ajj : W[(long long)p * Wd + j];
+      const double inv = piv != 0.0 ? 1.0 / piv : 0.0;
+      // multipliers of rows r > j after the swap (row p then holds the old row j)
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-          unsigned long long k2 = __shfl_down_sync(0xffffffffu, key, off);
-          int i2 = __shfl_down_sync(0xffffffffu, idx, off);
-          if (k2 > key || (k2 == key && i2 < idx)) { key = k2; idx = i2; }
-        }
-        if (lane == 0) { sk[0] = key; si[0] = idx; }
+      for (int q = 0; q < RPT; ++q) {
+        const int r = j + tid + q * NT;
+        if (r > j && r < N) lbuf[r] = (r == p ? ajj : x[q]) * inv;
       }
-      __syncthreads();
-      int p = si[0];
-      if (p < j || p >= N) p = j;
       if (p != j) {
-        for (int c = tid; c < Wd; c += NT) {
+        for (int c = j + tid; c < Wd; c += NT) {
           double t = W[(long long)j * Wd + c];
           W[(long long)j * Wd + c] = W[(long long)p * Wd + c];
           W[(long long)p * Wd + c] = t;
         }
       }
-      __syncthreads();
-      const double piv = W[(long long)j * Wd + j];
-      const double inv = piv != 0.0 ? 1.0 / piv : 0.0;
       if (tid == 0) {
         if (piv == 0.0) s_flag |= DQMC_STATUS_SINGULAR;
         if (p != j) s_sign = -s_sign;
@@ -107,7 +112,6 @@ __global__ void __launch_bounds__(NT) lu_kernel(const LuArgs a) {
         s_lad += log(fabs(piv));
         dinv[j] = inv;
       }
-      for (int r = j + 1 + tid; r < N; r += NT) lbuf[r] = W[(long long)r * Wd + j] * inv;
       __syncthreads();
       for (int c = j + 1 + tid; c < Wd; c += NT) {
         double* col = W + c;
@@ -116,20 +120,20 @@ __global__ void __launch_bounds__(NT) lu_kernel(const LuArgs a) {
         // col[r] -= l_r * pj, 8 rows per batch, next batch loaded before the stores
         int r = j + 1;
         if (r + 7 < N) {
-          double x[8];
+          double y0[8];
 #pragma unroll
-          for (int i = 0; i < 8; ++i) x[i] = col[(long long)(r + i) * Wd];
+          for (int i = 0; i < 8; ++i) y0[i] = col[(long long)(r + i) * Wd];
           for (; r + 15 < N; r += 8) {
             double y[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) y[i] = col[(long long)(r + 8 + i) * Wd];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) col[(long long)(r + i) * Wd] = fma(-lbuf[r + i], pj, x[i]);
+            for (int i = 0; i < 8; ++i) col[(long long)(r + i) * Wd] = fma(-lbuf[r + i], pj, y0[i]);
 #pragma unroll
-            for (int i = 0; i < 8; ++i) x[i] = y[i];
+            for (int i = 0; i < 8; ++i) y0[i] = y[i];
           }
 #pragma unroll
-          for (int i = 0; i < 8; ++i) col[(long long)(r + i) * Wd] = fma(-lbuf[r + i], pj, x[i]);
+          for (int i = 0; i < 8; ++i) col[(long long)(r + i) * Wd] = fma(-lbuf[r + i], pj, y0[i]);
           r += 8;
         }
         for (; r < N; ++r) col[(long long)r * Wd] = fma(-lbuf[r], pj, col[(long long)r * Wd]);
@@ -182,14 +186,14 @@ cudaError_t lu_solve_f64(const LuArgs& a, cudaStream_t st) {
   size_t sm = (size_t)a.N * 2 * sizeof(double) + 16;
   int grid = a.batch < (1 << 30) ? a.batch : (1 << 30);
   if (a.N + a.nrhs <= 64) {
-    cudaFuncSetAttribute(lu_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    lu_kernel<64><<<grid, 64, sm, st>>>(a);
+    cudaFuncSetAttribute(lu_kernel<64, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    lu_kernel<64, 1><<<grid, 64, sm, st>>>(a);
   } else if (a.N + a.nrhs <= 256) {
-    cudaFuncSetAttribute(lu_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    lu_kernel<256><<<grid, 256, sm, st>>>(a);
+    cudaFuncSetAttribute(lu_kernel<256, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    lu_kernel<256, 1><<<grid, 256, sm, st>>>(a);
   } else {
-    cudaFuncSetAttribute(lu_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    lu_kernel<512><<<grid, 512, sm, st>>>(a);
+    cudaFuncSetAttribute(lu_kernel<512, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    lu_kernel<512, 2><<<grid, 512, sm, st>>>(a);
   }
   return cudaGetLastError();
 }

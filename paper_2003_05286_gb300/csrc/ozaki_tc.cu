@@ -17,9 +17,9 @@
 //     tensor core is exact; products with the same weight 2^{-7(p+q)} share
 //     one TMEM accumulator (up to 16 of them, sum < 2^24);
 //   * only p + q <= s + 1 is formed (the rest is below the truncation error);
-//   * the epilogue adds the accumulators in two int64 partial sums with their
-//     relative shifts and rebuilds the FP64 value with two conversions and
-//     one FMA per output element.
+//   * the epilogue adds the accumulators exactly in a 128-bit integer with
+//     their relative shifts and builds the correctly rounded FP64 value with
+//     integer operations, so the FP64 pipe is not used.
 // The product is accurate to about N 2^{-7s-1} of (row max x column max):
 // normwise, not elementwise -- entries much smaller than their column's
 // largest keep correspondingly fewer digits.
@@ -46,7 +46,7 @@ constexpr int OZ_BM = 128;       // output rows per CTA (TMEM lanes)
 constexpr int OZ_BN = 64;        // output columns per CTA (TMEM columns per accumulator)
 constexpr int OZ_BK = 32;        // K per stage: 32 BF16 = 64 bytes per row (64-byte swizzle)
 constexpr int OZ_STAGES = 2;
-constexpr int OZ_THREADS = 128;
+constexpr int OZ_THREADS = 256;   // 8 warps: two per TMEM lane quarter in the epilogue
 constexpr int OZ_A_TILE = OZ_BM * OZ_BK * 2;   // 8 KB
 constexpr int OZ_B_TILE = OZ_BN * OZ_BK * 2;   // 4 KB
 constexpr unsigned long long OZ_WAIT_NS = 2000000000ull;
@@ -148,6 +148,17 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
       : "memory");
 }
 
+__device__ __forceinline__ void tmem_ld8_nowait(uint32_t taddr, uint32_t* r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                 "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
@@ -159,14 +170,57 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// 2^e * x for an FP64 x built from an integer, by exponent arithmetic when the
-// result stays normal.
-__device__ __forceinline__ double scale_pow2(double x, int e) {
-  if (x == 0.0) return 0.0;
-  long long bits = __double_as_longlong(x);
-  int ex = (int)((bits >> 52) & 0x7ff) + e;
-  if (ex >= 1 && ex <= 2046) return __longlong_as_double(bits + ((long long)e << 52));
-  return ldexp(x, e);
+// S * 2^e for a signed 128-bit S, rounded to nearest even, by integer
+// operations only (leading-zero count, shift, exponent assembly); results
+// outside the normal range take the library conversion.
+__device__ __forceinline__ double i128_times_pow2(__int128 S, int e) {
+  if (S == 0) return 0.0;
+  const unsigned long long sign = S < 0 ? (1ull << 63) : 0ull;
+  const unsigned __int128 m = S < 0 ? (unsigned __int128)(-S) : (unsigned __int128)S;
+  const unsigned long long hi = (unsigned long long)(m >> 64), lo = (unsigned long long)m;
+  const int nb = hi ? 128 - __clzll((long long)hi) : 64 - __clzll((long long)lo);
+  unsigned long long mant;
+  int ex = nb - 1 + e;
+  if (nb <= 53) {
+    mant = lo << (53 - nb);
+  } else {
+    const int sh = nb - 53;
+    const unsigned __int128 rem = m & (((unsigned __int128)1 << sh) - 1);
+    const unsigned __int128 half = (unsigned __int128)1 << (sh - 1);
+    mant = (unsigned long long)(m >> sh);
+    if (rem > half || (rem == half && (mant & 1ull))) {
+      if (++mant == (1ull << 53)) { mant >>= 1; ++ex; }
+    }
+  }
+  const int be = ex + 1023;
+  if (be <= 0 || be >= 2047) {
+    return ldexp(ldexp((double)(long long)(m >> 64), 64) + (double)lo, e) * (sign ? -1.0 : 1.0);
+  }
+  return __longlong_as_double((long long)(sign | ((unsigned long long)be << 52) |
+                                          (mant & 0xFFFFFFFFFFFFFull)));
+}
+
+__device__ __forceinline__ double i64_times_pow2(long long S, int e) {
+  if (S == 0) return 0.0;
+  const unsigned long long sign = S < 0 ? (1ull << 63) : 0ull;
+  const unsigned long long m = S < 0 ? (unsigned long long)(-S) : (unsigned long long)S;
+  const int nb = 64 - __clzll((long long)m);           // significant bits of |S|
+  unsigned long long mant;
+  int ex = nb - 1 + e;                                  // |S| 2^e = 1.f x 2^ex
+  if (nb <= 53) {
+    mant = m << (53 - nb);
+  } else {
+    const int sh = nb - 53;
+    const unsigned long long rem = m & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+    mant = m >> sh;
+    if (rem > half || (rem == half && (mant & 1ull))) {
+      if (++mant == (1ull << 53)) { mant >>= 1; ++ex; }
+    }
+  }
+  const int be = ex + 1023;
+  if (be <= 0 || be >= 2047) return ldexp((double)S, e);
+  return __longlong_as_double((long long)(sign | ((unsigned long long)be << 52) |
+                                          (mant & 0xFFFFFFFFFFFFFull)));
 }
 
 }  // namespace
@@ -270,38 +324,43 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
   bool ok = !*(volatile int*)s_fail && mbar_wait(done, 0);
   ok = __syncthreads_and(ok) != 0;   // uniform: tcgen05.ld is warp-collective
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const int row = m0 + warp * 32 + lane;
+  // warp w reads TMEM lanes 32 (w % 4) .. +31 (rows) and columns 32 (w / 4) .. +31
+  const int row = m0 + (warp & 3) * 32 + lane;
+  const int cbase = (warp >> 2) * 32;
   const int ea = row < N ? eA[row] : 0;
   const int* eBb = eB + (long long)b * seB;
   double* Cb = C + (long long)b * sC;
   const int shift0 = 7 * (s + 1);
   if (ok) {
-    for (int c0 = 0; c0 < OZ_BN; c0 += 16) {
-      // two exact int64 partial sums: weights >= 2^32 (hi, in units of 2^32) and below
-      long long hi[16], lo[16];
+    const uint32_t lane_addr = (uint32_t)((warp & 3) * 32) << 16;
+    for (int c0 = cbase; c0 < cbase + 32; c0 += 8) {
+      // exact sum of the groups: hi carries weights >= 2^32 (in units of 2^32)
+      long long hi[8], lo[8];
 #pragma unroll
-      for (int j = 0; j < 16; ++j) { hi[j] = 0; lo[j] = 0; }
-      for (int g = 0; g < pr.ngroups; ++g) {
-        uint32_t r[16];
-        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + g * OZ_BN + c0, r);
+      for (int j = 0; j < 8; ++j) { hi[j] = 0; lo[j] = 0; }
+      uint32_t r[8][8];
+#pragma unroll
+      for (int g = 0; g < 8; ++g)
+        if (g < pr.ngroups) tmem_ld8_nowait(tmem + lane_addr + g * OZ_BN + c0, r[g]);
+      tmem_wait_ld();
+#pragma unroll
+      for (int g = 0; g < 8; ++g) {
+        if (g >= pr.ngroups) break;
         const int sh = pr.shift[g];
-        if (sh >= 32) {
 #pragma unroll
-          for (int j = 0; j < 16; ++j)
-            hi[j] += (long long)__float2ll_rn(__uint_as_float(r[j])) << (sh - 32);
-        } else {
-#pragma unroll
-          for (int j = 0; j < 16; ++j)
-            lo[j] += (long long)__float2ll_rn(__uint_as_float(r[j])) << sh;
+        for (int j = 0; j < 8; ++j) {
+          // |acc| < 2^24: the 32-bit conversion is exact and stays off the FP64 pipe
+          const long long v = (long long)__float2int_rn(__uint_as_float(r[g][j]));
+          if (sh >= 32) hi[j] += v << (sh - 32); else lo[j] += v << sh;
         }
       }
       if (row < N) {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
+        for (int j = 0; j < 8; ++j) {
           const int col = n0 + c0 + j;
           if (col < N) {
-            const double sum = fma(__ll2double_rn(hi[j]), 4294967296.0, __ll2double_rn(lo[j]));
-            Cb[(long long)row * N + col] = scale_pow2(sum, ea + eBb[col] - shift0);
+            const __int128 S = ((__int128)hi[j] << 32) + (__int128)lo[j];
+            Cb[(long long)row * N + col] = i128_times_pow2(S, ea + eBb[col] - shift0);
           }
         }
       }

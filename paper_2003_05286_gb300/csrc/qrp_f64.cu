@@ -38,6 +38,16 @@ __device__ __forceinline__ float log2_wide(double x) {
   return (float)(e - 1023) + __log2f(m);
 }
 
+// ties -> lowest index
+__device__ __forceinline__ void warp_argmax(float& key, int& idx) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    float k2 = __shfl_down_sync(0xffffffffu, key, off);
+    int i2 = __shfl_down_sync(0xffffffffu, idx, off);
+    if (k2 > key || (k2 == key && i2 < idx)) { key = k2; idx = i2; }
+  }
+}
+
 template <int NT>
 __device__ __forceinline__ void block_argmax(float& key, int& idx, float* sk, int* si) {
   // ties -> lowest index
@@ -155,20 +165,24 @@ template <int NT>
 __global__ void __launch_bounds__(NT) qrp_kernel(const QrpArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int N = a.N;
-  double* nrm2 = reinterpret_cast<double*>(smem_raw);   // ||a_c^{(j)}||^2 (unscaled)
-  double* ref2 = nrm2 + N;                              // value at the last recompute
-  double* vbuf = ref2 + N;                              // Householder vector
-  double* taus = vbuf + N;                              // tau_j
-  double* dsc = taus + N;                               // Din, permuted with the columns
-  float* logd = reinterpret_cast<float*>(dsc + N);      // log2 Din
+  // per column c (in pivoted order): squared norm, reference value of the
+  // recompute test, column scale Din and its log2, original column index
+  double* nrm2 = reinterpret_cast<double*>(smem_raw);
+  double* ref2 = nrm2 + N;
+  double* vbuf = ref2 + N;                              // reflector (factorisation) / double buffer (Q)
+  double* vbuf2 = vbuf + N;
+  double* taus = vbuf2 + N;
+  double* dsc = taus + N;
+  float* logd = reinterpret_cast<float*>(dsc + N);
   int* perm = reinterpret_cast<int*>(logd + N);
-  __shared__ float sk[32];
-  __shared__ int si[32];
-  __shared__ double sd[32];
-  __shared__ double s_tau, s_scal;
+  __shared__ float sk[NT / 32];
+  __shared__ int si[NT / 32];
+  __shared__ double sd[NT / 32];
+  __shared__ double s_alpha;
   __shared__ int s_flag;
 
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  constexpr int RPT = 4;   // rows below the diagonal per thread in the reflector pass (N <= 4 NT)
 
   for (int b = blockIdx.x; b < a.batch; b += gridDim.x) {
     if (a.lim && a.lim[b] < a.lim_at) continue;   // chain of this instance already finished
@@ -176,7 +190,7 @@ __global__ void __launch_bounds__(NT) qrp_kernel(const QrpArgs a) {
     double* __restrict__ W = a.W + (long long)b * a.sW;
     double* __restrict__ U = a.U + (long long)b * a.sU;
     double* __restrict__ Dout = a.D + (long long)b * a.sD;
-    double* __restrict__ T = a.T + (long long)b * a.sT;
+    double* __restrict__ T = a.T + (long long)b * a.sT;   // holds v_j (row j) until the end
     int* __restrict__ pout = a.perm + (long long)b * a.sperm;
     const double* Din = a.Din ? a.Din + (long long)b * a.sDin : nullptr;
 
@@ -197,30 +211,68 @@ __global__ void __launch_bounds__(NT) qrp_kernel(const QrpArgs a) {
     }
     if (bad) atomicOr(&s_flag, DQMC_STATUS_NONFINITE_SCALE);
     __syncthreads();
-    for (int c = tid; c < N; c += NT) {
-      double s0 = col_sumsq(W + c, N, 0, N);
-      nrm2[c] = s0;
-      ref2[c] = s0;
+    {
+      float key = -INFINITY;
+      int idx = 0x7fffffff;
+      for (int c = tid; c < N; c += NT) {
+        double s0 = col_sumsq(W + c, N, 0, N);
+        nrm2[c] = s0;
+        ref2[c] = s0;
+        float kc = logd[c] + 0.5f * log2_wide(s0);
+        if (kc > key || (kc == key && c < idx)) { key = kc; idx = c; }
+      }
+      warp_argmax(key, idx);
+      if (lane == 0) { sk[wid] = key; si[wid] = idx; }
     }
     __syncthreads();
 
     for (int j = 0; j < N; ++j) {
-      // ---- pivot -------------------------------------------------------
-      float key = -INFINITY;
-      int idx = 0x7fffffff;
-      for (int c = j + tid; c < N; c += NT) {
-        float kc = logd[c] + 0.5f * log2_wide(nrm2[c]);
-        if (kc > key || (kc == key && c < idx)) { key = kc; idx = c; }
+      // ---- pivot: reduce the per-warp candidates (every thread, same order)
+      float key = sk[0];
+      int idx = si[0];
+      for (int w = 1; w < NT / 32; ++w) {
+        if (sk[w] > key || (sk[w] == key && si[w] < idx)) { key = sk[w]; idx = si[w]; }
       }
-      block_argmax<NT>(key, idx, sk, si);
-      int p = (idx >= j && idx < N) ? idx : j;
-      if (p != j) {
-        for (int r = tid; r < N; r += NT) {
-          double t0 = W[(long long)r * N + j];
-          W[(long long)r * N + j] = W[(long long)r * N + p];
-          W[(long long)r * N + p] = t0;
+      const int p = (idx >= j && idx < N) ? idx : j;
+      // ---- swap columns j and p; the thread that swaps a row below j keeps
+      // the pivot column's entry for the reflector -------------------------
+      double x[RPT];
+      double part = 0.0;
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) {
+        const int r = j + 1 + tid + q * NT;
+        x[q] = 0.0;
+        if (r < N) {
+          double* row = W + (long long)r * N;
+          const double xp = row[p];
+          if (p != j) { row[p] = row[j]; row[j] = xp; }
+          x[q] = xp;
+          part = fma(xp, xp, part);
         }
-        if (tid == 0) {
+      }
+      for (int r = tid; r <= j; r += NT) {   // rows 0..j (R part and the diagonal row)
+        double* row = W + (long long)r * N;
+        const double xp = row[p];
+        if (p != j) { row[p] = row[j]; row[j] = xp; }
+        if (r == j) s_alpha = xp;
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) part += __shfl_down_sync(0xffffffffu, part, off);
+      if (lane == 0) sd[wid] = part;
+      __syncthreads();
+      // ---- reflector ------------------------------------------------------
+      double sigma = 0.0;
+      for (int w = 0; w < NT / 32; ++w) sigma += sd[w];
+      const double alpha = s_alpha;
+      double tau = 0.0, scal = 0.0, beta = alpha;
+      if (sigma > 0.0) {
+        const double nrm = sqrt(fma(alpha, alpha, sigma));
+        beta = alpha >= 0.0 ? -nrm : nrm;
+        tau = (beta - alpha) / beta;
+        scal = 1.0 / (alpha - beta);
+      }
+      if (tid == 0) {
+        if (p != j) {
           double t;
           t = nrm2[j]; nrm2[j] = nrm2[p]; nrm2[p] = t;
           t = ref2[j]; ref2[j] = ref2[p]; ref2[p] = t;
@@ -228,69 +280,73 @@ __global__ void __launch_bounds__(NT) qrp_kernel(const QrpArgs a) {
           float f = logd[j]; logd[j] = logd[p]; logd[p] = f;
           int q = perm[j]; perm[j] = perm[p]; perm[p] = q;
         }
-      }
-      __syncthreads();
-
-      // ---- Householder reflector of column j ---------------------------
-      double part = 0.0;
-      for (int r = j + 1 + tid; r < N; r += NT) {
-        double x = W[(long long)r * N + j];
-        part = fma(x, x, part);
-      }
-      double sigma = block_sum<NT>(part, sd);
-      if (tid == 0) {
-        double alpha = W[(long long)j * N + j];
-        double tau = 0.0, scal = 0.0, beta = alpha;
-        if (sigma > 0.0) {
-          double nrm = sqrt(fma(alpha, alpha, sigma));
-          beta = alpha >= 0.0 ? -nrm : nrm;
-          tau = (beta - alpha) / beta;
-          scal = 1.0 / (alpha - beta);
-        }
         W[(long long)j * N + j] = beta;
         taus[j] = tau;
-        s_tau = tau;
-        s_scal = scal;
+        T[(long long)j * N + j] = 1.0;
       }
-      __syncthreads();
-      const double tau = s_tau, scal = s_scal;
-      for (int r = j + 1 + tid; r < N; r += NT) {
-        double v = W[(long long)r * N + j] * scal;
-        vbuf[r] = v;
-        W[(long long)r * N + j] = v;
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) {
+        const int r = j + 1 + tid + q * NT;
+        if (r < N) {
+          const double v = x[q] * scal;
+          vbuf[r] = v;
+          T[(long long)j * N + r] = v;   // v_j stored contiguously for forming Q
+        }
       }
       __syncthreads();
 
-      // ---- apply to the trailing columns and downdate their norms --------
-      if (tau != 0.0) {
-        for (int c = j + 1 + tid; c < N; c += NT) {
-          double* col = W + c;
-          const double w = (col[(long long)j * N] + col_dot(col, N, vbuf, j + 1, N)) * tau;
-          const double rjc = col[(long long)j * N] - w;
+      // ---- apply to the trailing columns, downdate, next pivot candidates --
+      key = -INFINITY;
+      idx = 0x7fffffff;
+      for (int c = j + 1 + tid; c < N; c += NT) {
+        double* col = W + c;
+        double rjc = col[(long long)j * N];
+        if (tau != 0.0) {
+          const double w = (rjc + col_dot(col, N, vbuf, j + 1, N)) * tau;
+          rjc -= w;
           col[(long long)j * N] = rjc;
           col_axpy(col, N, vbuf, w, j + 1, N);
-          double n2 = fma(-rjc, rjc, nrm2[c]);
-          if (n2 <= 1.4901161193847656e-8 * ref2[c]) {
-            n2 = col_sumsq(col, N, j + 1, N);
-            ref2[c] = n2;
-          }
-          nrm2[c] = n2;
         }
-      } else {
-        for (int c = j + 1 + tid; c < N; c += NT) {
-          double rjc = W[(long long)j * N + c];
-          double n2 = fma(-rjc, rjc, nrm2[c]);
-          if (n2 <= 1.4901161193847656e-8 * ref2[c]) {
-            n2 = col_sumsq(W + c, N, j + 1, N);
-            ref2[c] = n2;
-          }
-          nrm2[c] = n2;
+        double n2 = fma(-rjc, rjc, nrm2[c]);
+        if (n2 <= 1.4901161193847656e-8 * ref2[c]) {
+          n2 = col_sumsq(col, N, j + 1, N);
+          ref2[c] = n2;
+        }
+        nrm2[c] = n2;
+        float kc = logd[c] + 0.5f * log2_wide(n2);
+        if (kc > key || (kc == key && c < idx)) { key = kc; idx = c; }
+      }
+      warp_argmax(key, idx);
+      if (lane == 0) { sk[wid] = key; si[wid] = idx; }
+      __syncthreads();
+    }
+
+    // ---- U = Q = H_0 H_1 ... H_{N-1}, backward accumulation --------------
+    // One barrier per reflector: while step j applies v_j (from one buffer),
+    // the threads also stage v_{j-1} into the other.
+    for (long long e = tid; e < (long long)N * N; e += NT) {
+      int i = (int)(e / N), c = (int)(e % N);
+      U[e] = (i == c) ? 1.0 : 0.0;
+    }
+    for (int r = N - 1 + tid; r < N; r += NT) vbuf[r] = T[(long long)(N - 1) * N + r];
+    __syncthreads();
+    for (int j = N - 1; j >= 0; --j) {
+      double* cur = ((N - 1 - j) & 1) ? vbuf2 : vbuf;
+      double* nxt = ((N - 1 - j) & 1) ? vbuf : vbuf2;
+      if (j > 0)
+        for (int r = j - 1 + tid; r < N; r += NT) nxt[r] = T[(long long)(j - 1) * N + r];
+      const double tau = taus[j];
+      if (tau != 0.0) {
+        for (int c = j + tid; c < N; c += NT) {
+          double* col = U + c;
+          const double w = col_dot(col, N, cur, j, N) * tau;
+          col_axpy(col, N, cur, w, j, N);
         }
       }
       __syncthreads();
     }
 
-    // ---- outputs D, T, perm ----------------------------------------------
+    // ---- outputs D, T, perm (T overwrites the stored reflectors) ---------
     // reuse nrm2 as 1/|r_ii| and ref2 as 1/Din_i
     for (int i = tid; i < N; i += NT) {
       double rii = fabs(W[(long long)i * N + i]);
@@ -309,31 +365,13 @@ __global__ void __launch_bounds__(NT) qrp_kernel(const QrpArgs a) {
       if (c >= i) v = W[e] * nrm2[i] * (dsc[c] * ref2[i]);
       T[e] = v;
     }
-
-    // ---- U = Q = H_0 H_1 ... H_{N-1}, backward accumulation --------------
-    for (long long e = tid; e < (long long)N * N; e += NT) {
-      int i = (int)(e / N), c = (int)(e % N);
-      U[e] = (i == c) ? 1.0 : 0.0;
-    }
     __syncthreads();
-    for (int j = N - 1; j >= 0; --j) {
-      const double tau = taus[j];
-      if (tau == 0.0) continue;   // uniform across the block
-      for (int r = j + tid; r < N; r += NT) vbuf[r] = (r == j) ? 1.0 : W[(long long)r * N + j];
-      __syncthreads();
-      for (int c = j + tid; c < N; c += NT) {
-        double* col = U + c;
-        const double w = col_dot(col, N, vbuf, j, N) * tau;
-        col_axpy(col, N, vbuf, w, j, N);
-      }
-      __syncthreads();
-    }
     if (tid == 0 && s_flag && a.status) atomicOr(&a.status[b / a.status_div], s_flag);
     __syncthreads();
   }
 }
 
-static size_t qrp_smem(int N) { return (size_t)N * (5 * sizeof(double) + sizeof(float) + sizeof(int)) + 16; }
+static size_t qrp_smem(int N) { return (size_t)N * (6 * sizeof(double) + sizeof(float) + sizeof(int)) + 16; }
 
 cudaError_t qrp_f64(const QrpArgs& a, cudaStream_t st) {
   if (a.batch <= 0 || a.N <= 0) return cudaSuccess;
