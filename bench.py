@@ -426,7 +426,8 @@ def run_gpu_other(args, wl, rank, world):
     torch.cuda.set_device(dev)
     batch = args.batch or wl["batch"]
     name = args.workload
-    h = dq.Handle()
+    prec = 0 if args.precision == "fp64" or name == "ragged_1024" else int(args.precision[-1])
+    h = dq.Handle(chain_precision=prec)
     h.bind_stream()
     extra = {}
     if name == "ragged_1024":
@@ -505,8 +506,9 @@ def run_gpu_other(args, wl, rank, world):
     line = {"metric": metric, "value": job_value(batch, world, args.steps, tot), "unit": unit,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": tot / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": dict(workload=name, instances_per_gpu=batch,
+            "vs_baseline": None, "dtype": "f64" if prec == 0 else f"bf16x{prec}+f64",
+            "data": "synthetic",
+            "config": dict(workload=name, instances_per_gpu=batch, chain_precision=prec,
                            l2="flushed between timed steps (256 MB write)", **extra),
             "roofline": {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
                          "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,

@@ -76,7 +76,9 @@ enum dqmc_status_bits {
  * scales), the digit products accumulate exactly in FP32 on the tcgen05
  * tensor cores and are recombined in FP64; a product is accurate to about
  * N 2^{-7s-1} of (row max x column max), normwise rather than elementwise.
- * Supported for N <= 256 in dqmc_greens / dqmc_logdet. */
+ * Supported for N <= 256 in dqmc_greens, dqmc_logdet, dqmc_greens_tdisplaced
+ * and dqmc_logdet_grad (both stacks); dqmc_greens_ragged and N > 256 return
+ * DQMC_ERR_UNSUPPORTED (dqmc_greens_noalloc takes no handle and is FP64). */
 typedef enum {
   DQMC_CHAIN_FP64 = 0,
   DQMC_CHAIN_BF16X3 = 3,

@@ -235,6 +235,16 @@ struct ChainWs {
 
 inline int pad_to(int n, int m) { return (n + m - 1) / m * m; }
 
+// Digit slices of E (forward chain, transposeE = 0) or E^T (backward chain)
+// into a chain workspace's shared A-operand buffers.
+cudaError_t split_E(const double* E, int N, int transposeE, const ChainWs& w, cudaStream_t st) {
+  // row i of the A operand is a "column" of the splitter: element (m, i)
+  return transposeE ? ozaki_split(E, N, 1, 0, nullptr, 0, N, w.oz_P128, w.oz_PK, w.oz_s, w.ozA, 0,
+                                  w.ozeA, 0, 1, st)
+                    : ozaki_split(E, 1, N, 0, nullptr, 0, N, w.oz_P128, w.oz_PK, w.oz_s, w.ozA, 0,
+                                  w.ozeA, 0, 1, st);
+}
+
 // Mixed-precision buffers of a chain over `batch` instances with s slices.
 void take_ozaki(Arena& ar, int batch, int N, int s, ChainWs& w) {
   w.oz_s = s;
@@ -262,8 +272,6 @@ inline double* slotX(const Slots& s, int slot) {
   return s.X + slot * s.slotX;
 }
 
-// lim (nullable, per instance): chain length M_b of ragged batches; slices
-// past M_b are copied through and finished instances skip the QR and X update.
 // a1 for chunk c: k slice products into the chunk buffers; *out = last product.
 dqmc_status chunk_products(dqmc_handle h, int dir, int batch, int N, int M, int k, int c,
                            const double* E, const double* expV, long long sV, const Slots& s,
@@ -279,17 +287,24 @@ dqmc_status chunk_products(dqmc_handle h, int dir, int batch, int N, int M, int 
   int nb = 0;
   for (int i = 0; i <= hi - lo; ++i) {
     const int l = dir > 0 ? lo + i : hi - i;
-    if (w.oz_s > 0 && dir > 0 && lim == nullptr) {
-      // a12: B' = diag(e^{V_l}) A split into BF16 slices, then E B' on the tensor cores
+    if (w.oz_s > 0 && lim == nullptr) {
+      // a12 on the tensor cores.  Forward: B' = diag(e^{V_l}) A, C = E B'.
+      // Backward (B_l^T = diag(e^{V_l}) E^T): C = E^T B' with B' = A scaled by
+      // the previous slice's e^{V}; the last slice's scale is applied below.
       const int PK = w.oz_PK, sl = w.oz_s;
-      CK(ozaki_split(prev, N, 1, sprev, expV + (long long)(l - 1) * N, sV, N, PK, PK, sl, w.ozB,
-                     (long long)sl * PK * PK, w.ozeB, PK, batch, st));
+      const double* sc = nullptr;
+      if (dir > 0) sc = expV + (long long)(l - 1) * N;
+      else if (i > 0) sc = expV + (long long)l * N;       // e^{V_{l+1}}
+      CK(ozaki_split(prev, N, 1, sprev, sc, sV, N, PK, PK, sl, w.ozB, (long long)sl * PK * PK,
+                     w.ozeB, PK, batch, st));
       CKP(PC_CHAIN, 2.0 * N * N * (double)N * batch,
           ozaki_gemm(w.ozA, w.ozeA, w.oz_P128, w.ozB, w.ozeB, PK, PK, PK, sl, N, batch, bufs[nb],
                      NN, nullptr, st));
       prev = bufs[nb];
       sprev = NN;
       nb ^= 1;
+      if (dir < 0 && i == hi - lo)
+        CK(scale_rows(bufs[nb ^ 1], NN, expV + (long long)(l - 1) * N, sV, N, batch, st));
       continue;
     }
     GemmArgs g;
@@ -315,15 +330,13 @@ dqmc_status chunk_products(dqmc_handle h, int dir, int batch, int N, int M, int 
   return DQMC_OK;
 }
 
-// a2-a4 for chunk c: (A) diag(D_src) -> U' D' T' (pivoted QR), X_dst = T' X_src[perm].
-dqmc_status chunk_refactor(dqmc_handle h, int dir, int batch, int N, int k, int c,
-                           const double* A, const Slots& s, const ChainWs& w, int* status,
-                           const int* lim) {
+// a2-a3 for chunk c: (A) diag(D_src) -> U' D' T' (pivoted QR).
+dqmc_status chunk_qr(dqmc_handle h, int dir, int batch, int N, int k, int c, const double* A,
+                     const Slots& s, const ChainWs& w, int* status, const int* lim) {
   cudaStream_t st = h->cur;
   const long long NN = (long long)N * N;
   const int src = dir > 0 ? c : c + 1;
   const int dst = dir > 0 ? c + 1 : c;
-  const int lo = c * k + 1;
   QrpArgs q;
   q.N = N; q.batch = batch;
   q.A = A; q.sA = NN;
@@ -334,8 +347,18 @@ dqmc_status chunk_refactor(dqmc_handle h, int dir, int batch, int N, int k, int 
   q.T = w.T; q.sT = NN;
   q.perm = w.perm; q.sperm = N;
   q.status = status;
-  q.lim = lim; q.lim_at = lo;
+  q.lim = lim; q.lim_at = c * k + 1;
   CKP(PC_QRP, 8.0 / 3.0 * N * N * (double)N * batch, qrp_f64(q, st));
+  return DQMC_OK;
+}
+
+// a4 for chunk c: X_dst = T' X_src[perm].
+dqmc_status chunk_xupdate(dqmc_handle h, int dir, int batch, int N, int k, int c, const Slots& s,
+                          const ChainWs& w, const int* lim) {
+  cudaStream_t st = h->cur;
+  const long long NN = (long long)N * N;
+  const int src = dir > 0 ? c : c + 1;
+  const int dst = dir > 0 ? c + 1 : c;
   GemmArgs g;
   g.M = g.N = g.K = N;
   g.batch = batch;
@@ -343,9 +366,16 @@ dqmc_status chunk_refactor(dqmc_handle h, int dir, int batch, int N, int k, int 
   g.B = slotX(s, src); g.ldb = N; g.sB = s.instX;
   g.permB = w.perm; g.sperm = N;
   g.C = slotX(s, dst); g.ldc = N; g.sC = s.instX;
-  g.lim = lim; g.lim_at = lo;
+  g.lim = lim; g.lim_at = c * k + 1;
   CKP(PC_XUPD, (double)N * N * (double)N * batch, gemm_f64(g, st));
   return DQMC_OK;
+}
+
+dqmc_status chunk_refactor(dqmc_handle h, int dir, int batch, int N, int k, int c,
+                           const double* A, const Slots& s, const ChainWs& w, int* status,
+                           const int* lim) {
+  CKS(chunk_qr(h, dir, batch, N, k, c, A, s, w, status, lim));
+  return chunk_xupdate(h, dir, batch, N, k, c, s, w, lim);
 }
 
 // lim (nullable, per instance): chain length M_b of ragged batches; slices
@@ -705,12 +735,7 @@ static dqmc_status greens_impl(dqmc_handle h, int batch, int N, int M, const dou
   // exp(V_l) for every slice, padded to Mp slices per instance
   CK(exp_pad(Vd, expV, batch, M, (int)Mp, N, 1.0, stout, st));
 
-  if (cw.oz_s > 0) {
-    // slices of E, shared by every instance and slice: row i of E is a
-    // "column" of the splitter (element (m, i) = E[i][m])
-    CK(ozaki_split(E, 1, N, 0, nullptr, 0, N, cw.oz_P128, cw.oz_PK, cw.oz_s, cw.ozA, 0, cw.ozeA,
-                   0, 1, st));
-  }
+  if (cw.oz_s > 0) CK(split_E(E, N, 0, cw, st));   // E slices, shared by all instances
   CK(set_identity(U, NN, N, batch, st));
   CK(set_const(D, (long long)N * batch, 1.0, st));
   CK(set_identity(X0, NN, N, batch, st));
@@ -878,6 +903,10 @@ dqmc_status run_stacks(dqmc_handle h, int batch, int N, int M, int k, const doub
   const int nc = n_chunks(M, k), nt = nc + 1;
   const long long NN = (long long)N * N;
   // forward slot 0 and backward slot nc are the identity decomposition
+  if (cw.oz_s > 0) {
+    CK(split_E(E, N, 0, cw, st));
+    CK(split_E(E, N, 1, cw2, st));
+  }
   CK(set_identity(w.UF, nt * NN, N, batch, st));
   CK(set_const_strided(w.DF, (long long)nt * N, N, batch, 1.0, st));
   CK(set_identity(w.XF, nt * NN, N, batch, st));
@@ -902,7 +931,7 @@ dqmc_status run_stacks(dqmc_handle h, int batch, int N, int M, int k, const doub
     CKS(run_chain_pair(h, J, N, M, k, E));
   } else {
     CKS(run_chain(h, +1, batch, N, M, k, E, expV, sV, f, cw, status));
-    CKS(run_chain(h, -1, batch, N, M, k, E, expV, sV, b, cw, status));
+    CKS(run_chain(h, -1, batch, N, M, k, E, expV, sV, b, cw2, status));
   }
   return DQMC_OK;
 }
@@ -985,7 +1014,7 @@ dqmc_status dqmc_greens_tdisplaced(dqmc_handle h, int batch, int N, int M, const
                                    double dtau, const double* V, int k, double* Gtt, double* Gt0,
                                    int* status) {
   CKS(check_common(h, batch, N, M, K, dtau, V, k));
-  if (h->prec != DQMC_CHAIN_FP64) return DQMC_ERR_UNSUPPORTED;   // mixed chain: equal time only
+  if (h->prec != DQMC_CHAIN_FP64 && N > 256) return DQMC_ERR_UNSUPPORTED;
   h->launches = 0;
   h->cur = h->stream;
   if (batch == 0) return DQMC_OK;
@@ -1005,6 +1034,10 @@ dqmc_status dqmc_greens_tdisplaced(dqmc_handle h, int batch, int N, int M, const
     expV = ar.take<double>(Mp * N * batch);
     take_chain(ar, batch, N, cw);
     take_chain(ar, batch, N, cw2);
+    if (h->prec != DQMC_CHAIN_FP64) {
+      take_ozaki(ar, batch, N, (int)h->prec, cw);
+      take_ozaki(ar, batch, N, (int)h->prec, cw2);
+    }
     take_stacks(ar, batch, N, nt, sw);
     take_mid(ar, Q, N, ncols > 0 ? ncols : N, mw);
     stat = ar.take<int>(batch);
@@ -1057,7 +1090,7 @@ dqmc_status dqmc_logdet_grad(dqmc_handle h, int batch, int N, int M, const doubl
                              const double* V, int k, double* logdet, int* sign, double* dV,
                              int* status) {
   CKS(check_common(h, batch, N, M, K, dtau, V, k));
-  if (h->prec != DQMC_CHAIN_FP64) return DQMC_ERR_UNSUPPORTED;   // mixed chain: equal time only
+  if (h->prec != DQMC_CHAIN_FP64 && N > 256) return DQMC_ERR_UNSUPPORTED;
   h->launches = 0;
   h->cur = h->stream;
   if (batch == 0) return DQMC_OK;
@@ -1079,6 +1112,10 @@ dqmc_status dqmc_logdet_grad(dqmc_handle h, int batch, int N, int M, const doubl
     expmV = ar.take<double>(Mp * N * batch);
     take_chain(ar, batch, N, cw);
     take_chain(ar, batch, N, cw2);
+    if (h->prec != DQMC_CHAIN_FP64) {
+      take_ozaki(ar, batch, N, (int)h->prec, cw);
+      take_ozaki(ar, batch, N, (int)h->prec, cw2);
+    }
     take_stacks(ar, batch, N, nt, sw);
     take_mid(ar, Q, N, N, mw);
     take_loh(ar, batch, N, lw);

@@ -133,6 +133,9 @@ cudaError_t finish_logdet(const double* D, long long sD, int N, int batch, const
 cudaError_t copy_mats(const double* in, long long sin, double* out, long long sout,
                       int N, int batch, int transpose, int divin, int divout,
                       cudaStream_t st);
+// A_b <- diag(v_b) A_b for strided N x N matrices.
+cudaError_t scale_rows(double* A, long long sA, const double* v, long long sv, int N, int batch,
+                       cudaStream_t st);
 // Identity / ones initialisers.
 cudaError_t set_identity(double* A, long long sA, int N, int batch, cudaStream_t st);
 cudaError_t set_const(double* x, long long n, double v, cudaStream_t st);

@@ -195,6 +195,26 @@ cudaError_t copy_mats(const double* in, long long sin, double* out, long long so
   return cudaGetLastError();
 }
 
+// A_b <- diag(v_b) A_b (row i of instance b scaled by v[b*sv + i]).
+__global__ void scale_rows_kernel(double* A, long long sA, const double* v, long long sv, int N,
+                                  int batch) {
+  const long long NN = (long long)N * N, total = NN * batch;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    int b = (int)(e / NN);
+    long long ij = e % NN;
+    A[(long long)b * sA + ij] *= v[(long long)b * sv + ij / N];
+  }
+}
+
+cudaError_t scale_rows(double* A, long long sA, const double* v, long long sv, int N, int batch,
+                       cudaStream_t st) {
+  long long total = (long long)N * N * batch;
+  if (total <= 0) return cudaSuccess;
+  scale_rows_kernel<<<nblocks(total), TPB, 0, st>>>(A, sA, v, sv, N, batch);
+  return cudaGetLastError();
+}
+
 __global__ void set_identity_kernel(double* A, long long sA, int N, int batch) {
   const long long NN = (long long)N * N, total = NN * batch;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;

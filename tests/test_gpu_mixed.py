@@ -70,11 +70,43 @@ def test_mixed_full_size_sampled(dq):
         assert int(sg[b]) == so
 
 
+@pytest.mark.parametrize("L,beta,k,seed", [(4, 4.0, 10, 3), (6, 6.0, 7, 5)])
+def test_mixed_tdisplaced(dq, L, beta, k, seed):
+    """Both stacks of the time-displaced path on the tensor cores (eight slices)."""
+    inst = di.hubbard_instance(L, 4.0, 0.1, beta, k, seed)
+    h = dq.Handle(chain_precision=8)
+    Gtt, Gt0, st = dq.greens_tdisplaced(_dev(inst.K), 0.1, _dev(inst.V), k, handle=h)
+    assert int(st) == 0
+    Ott, Ot0 = od.greens_tdisplaced(inst.K, 0.1, inst.V, k)
+    Gtt, Gt0 = Gtt.cpu().numpy(), Gt0.cpu().numpy()
+    for j in range(Ott.shape[0]):
+        sc = max(1.0, np.abs(Ott[j]).max())
+        assert np.abs(Gtt[j] - Ott[j]).max() <= 1e-8 * sc, j
+        assert np.abs(Gt0[j] - Ot0[j]).max() <= 1e-8 * max(1.0, np.abs(Ot0[j]).max()), j
+    h.close()
+
+
+def test_mixed_grad(dq):
+    inst = di.hubbard_instance(6, 4.0, 0.1, 8.0, 10, 11)
+    h = dq.Handle(chain_precision=8)
+    ld, sg, dV, st = dq.logdet_grad(_dev(inst.K), 0.1, _dev(inst.V), 10, handle=h)
+    assert int(st) == 0
+    dVo = od.logdet_grad(inst.K, 0.1, inst.V, 10)
+    ldo, so = od.logdet(inst.K, 0.1, inst.V, 10)
+    assert np.abs(dV.cpu().numpy() - dVo).max() <= 1e-8
+    assert abs(float(ld) - ldo) <= 1e-9 * abs(ldo)
+    assert int(sg) == so
+    h.close()
+
+
 def test_mixed_rejected_where_not_built(dq):
+    """N above 256 and ragged batches have no tensor-core chain."""
     h = dq.Handle(chain_precision=5)
-    inst = di.hubbard_instance(4, 4.0, 0.1, 2.0, 10, 1)
-    with pytest.raises(RuntimeError):
-        dq.greens_tdisplaced(_dev(inst.K), 0.1, _dev(inst.V), 10, handle=h)
     big = torch.zeros((1, 20, 324), dtype=torch.float64, device="cuda")
     with pytest.raises(RuntimeError):
         dq.greens(_dev(di.square_hopping(18)), 0.1, big, 10, handle=h)
+    with pytest.raises(RuntimeError):
+        dq.greens_tdisplaced(_dev(di.square_hopping(18)), 0.1, big, 10, handle=h)
+    inst = di.hubbard_instance(4, 4.0, 0.1, 2.0, 10, 1)
+    with pytest.raises(RuntimeError):
+        dq.greens_ragged([(_dev(inst.K), 0.1, _dev(inst.V), 10)], handle=h)
