@@ -21,6 +21,9 @@
 // Q is then formed explicitly by backward accumulation of the reflectors.
 // Outputs: U = Q, D_i = |r_ii| Din_{p_i}, T = D^{-1} R (pivoted column order,
 // zeros below the diagonal), perm_i = p_i.
+//
+// Two kernels compute this: qrp_fused_kernel (N <= 256, one pass over the
+// trailing matrix per step) and qrp_kernel (any N, two passes per step).
 #include "common.cuh"
 
 namespace dqmc {
@@ -371,10 +374,365 @@ __global__ void __launch_bounds__(NT) qrp_kernel(const QrpArgs a) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Fused variant for N <= 256: TPC threads per column, one pass per step.
+//
+// The kernel above needs two passes over the trailing matrix per step (the
+// dot products v_j^T a_c, then the rank-1 update), each a chain of dependent
+// L2 round trips for the thread that walks a column.  Here a step is a single
+// pass: while column c is updated with the reflector of step j, the same
+// loaded values are dotted with the reflector of step j+1.  That reflector is
+// known before the pass because the next pivot only needs the downdated norms,
+// and those only need r_jc = a_jc - w_c (v_j has a unit leading entry), not
+// the updated column.  Per step:
+//   (a) every column: w_c = tau_j d_c, r_jc, norm downdate, pivot key, vote;
+//   (b) one warp: the pivot column's updated entries (a_P - v_j w_P), the
+//       reflector v_{j+1}, the swap of columns j+1 and P, R entries of the
+//       pivot column;
+//   (c) every trailing column: a_c -= v_j w_c and d_c = v_{j+1}^T a_c.
+// Two block barriers per step.  TPC threads of a column sit in one warp
+// (lane = column + CPW * row group), so a load instruction of the warp reads
+// TPC rows x CPW consecutive doubles, and the per-column scalars (w, norms,
+// keys) are vector instructions over the warp's columns.  Q is accumulated
+// backwards with the same fused pass (update with v_j, dot with v_{j-1}).
+// ---------------------------------------------------------------------------
+namespace {
+
+// rows r0, r0 + TPC, ... < N of column c of the row-major M (leading dimension
+// N): x_r -= va[r] w (stored if store), returns sum vb[r] x_r over the updated
+// values and sets xpick to the updated value of row rpick if this thread has
+// it.  Loads run one batch of B rows ahead of the stores.
+template <int TPC, int B>
+__device__ __forceinline__ double fused_pass(double* __restrict__ M, int N, int c, int r0,
+                                             const double* va, double w, const double* vb,
+                                             int rpick, double& xpick, bool store) {
+  const int n = r0 < N ? (N - r0 + TPC - 1) / TPC : 0;
+  double acc0 = 0.0, acc1 = 0.0;
+  double xc[B];
+#pragma unroll
+  for (int k = 0; k < B; ++k) xc[k] = k < n ? M[(long long)(r0 + k * TPC) * N + c] : 0.0;
+  for (int i = 0; i < n; i += B) {
+    double xn[B];
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+      const int t = i + B + k;
+      xn[k] = t < n ? M[(long long)(r0 + t * TPC) * N + c] : 0.0;
+    }
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+      if (i + k < n) {
+        const int r = r0 + (i + k) * TPC;
+        const double x = fma(-va[r], w, xc[k]);
+        if (store) M[(long long)r * N + c] = x;
+        if (k & 1) acc1 = fma(vb[r], x, acc1); else acc0 = fma(vb[r], x, acc0);
+        if (r == rpick) xpick = x;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < B; ++k) xc[k] = xn[k];
+  }
+  return acc0 + acc1;
+}
+
+__device__ __forceinline__ double warp_sum_all(double v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
+// ties -> lowest index; every lane ends with the same pair
+__device__ __forceinline__ void warp_argmax_all(float& key, int& idx) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    float k2 = __shfl_xor_sync(0xffffffffu, key, off);
+    int i2 = __shfl_xor_sync(0xffffffffu, idx, off);
+    if (k2 > key || (k2 == key && i2 < idx)) { key = k2; idx = i2; }
+  }
+}
+
+// sum over the TPC threads of a column (lanes l, l + CPW, ...)
+template <int TPC>
+__device__ __forceinline__ double group_sum(double v) {
+#pragma unroll
+  for (int off = 16; off >= 32 / TPC; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
+}  // namespace
+
+template <int NT, int TPC, int NQ>
+__global__ void __launch_bounds__(NT) qrp_fused_kernel(const QrpArgs a) {
+  constexpr int NW = NT / 32, CPW = 32 / TPC, BATCH = 8;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int N = a.N;
+  // per column in pivoted (logical) order; swapped together with the columns
+  double* nrm2 = reinterpret_cast<double*>(smem_raw);
+  double* ref2 = nrm2 + N;
+  double* dsc = ref2 + N;
+  double* wsm = dsc + N;     // w_c of the current step
+  double* taus = wsm + N;
+  double* vA = taus + N;     // reflector buffers: v_j and v_{j+1} (rotating)
+  double* vB = vA + N;
+  float* logd = reinterpret_cast<float*>(vB + N);
+  int* perm = reinterpret_cast<int*>(logd + N);
+  __shared__ float sk[NW];
+  __shared__ int si[NW];
+  __shared__ int s_flag;
+
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int rg = lane / CPW;                   // row group: rows r = rg (mod TPC)
+  const int c = wid * CPW + lane % CPW;        // this thread's column
+  const bool own = c < N;
+  const unsigned FULL = 0xffffffffu;
+
+  for (int b = blockIdx.x; b < a.batch; b += gridDim.x) {
+    if (a.lim && a.lim[b] < a.lim_at) continue;   // chain of this instance already finished
+    const double* __restrict__ A = a.A + (long long)b * a.sA;
+    double* __restrict__ W = a.W + (long long)b * a.sW;
+    double* __restrict__ U = a.U + (long long)b * a.sU;
+    double* __restrict__ Dout = a.D + (long long)b * a.sD;
+    double* __restrict__ T = a.T + (long long)b * a.sT;   // v_j in row j until the end
+    int* __restrict__ pout = a.perm + (long long)b * a.sperm;
+    const double* Din = a.Din ? a.Din + (long long)b * a.sDin : nullptr;
+    const long long NN = (long long)N * N;
+
+    if (tid == 0) s_flag = 0;
+    int bad = 0;
+    for (long long e = tid; e < NN; e += NT) {
+      const double v = A[e];
+      bad |= !isfinite(v);
+      W[e] = v;
+    }
+    for (int cc = tid; cc < N; cc += NT) {
+      const double d = Din ? Din[cc] : 1.0;
+      bad |= !(isfinite(d) && d >= 0.0);
+      dsc[cc] = d;
+      logd[cc] = log2_wide(d);
+      perm[cc] = cc;
+    }
+    __syncthreads();
+    if (bad) atomicOr(&s_flag, DQMC_STATUS_NONFINITE_SCALE);
+
+    // ---- vote: argmax of the keys (ties -> lowest column), then warp 0 forms
+    // the reflector for position jn from column P -------------------------
+    double* vcur = vA;   // v_j
+    double* vnxt = vB;   // v_{j+1}
+    auto vote_and_reflect = [&](float key, int idx, int jn) {
+      warp_argmax(key, idx);
+      if (lane == 0) { sk[wid] = key; si[wid] = idx; }
+      __syncthreads();
+      if (wid == 0) {
+        key = lane < NW ? sk[lane] : -INFINITY;
+        idx = lane < NW ? si[lane] : 0x7fffffff;
+        warp_argmax_all(key, idx);
+        const int P = (idx >= jn && idx < N) ? idx : jn;
+        const int j = jn - 1;
+        const bool upd = j >= 0;
+        const double wP = upd ? wsm[P] : 0.0;
+        double xp[NQ], xo[NQ];
+#pragma unroll
+        for (int k = 0; k < NQ; ++k) {
+          const int r = lane + 32 * k;
+          xp[k] = r < N ? W[(long long)r * N + P] : 0.0;
+          xo[k] = (r < N && P != jn) ? W[(long long)r * N + jn] : 0.0;
+        }
+        double sig = 0.0, alpha = 0.0;
+#pragma unroll
+        for (int k = 0; k < NQ; ++k) {
+          const int r = lane + 32 * k;
+          if (upd && r >= j && r < N) xp[k] = fma(-vcur[r], wP, xp[k]);
+          if (r == jn) alpha = xp[k];
+          if (r > jn && r < N) sig = fma(xp[k], xp[k], sig);
+        }
+        sig = warp_sum_all(sig);
+        alpha = __shfl_sync(FULL, alpha, jn & 31);
+        double tau = 0.0, scal = 0.0, beta = alpha;
+        if (sig > 0.0) {
+          const double nrm = sqrt(fma(alpha, alpha, sig));
+          beta = alpha >= 0.0 ? -nrm : nrm;
+          tau = (beta - alpha) / beta;
+          scal = 1.0 / (alpha - beta);
+        }
+#pragma unroll
+        for (int k = 0; k < NQ; ++k) {
+          const int r = lane + 32 * k;
+          if (r < N) {
+            // column jn <- pivot column: R rows (final above j, updated at j), beta
+            if (r < j) { if (P != jn) W[(long long)r * N + jn] = xp[k]; }
+            else if (r == j) W[(long long)r * N + jn] = xp[k];
+            else if (r == jn) W[(long long)r * N + jn] = beta;
+            // column P <- old column jn, not yet updated by v_j
+            if (P != jn) W[(long long)r * N + P] = xo[k];
+            const double v = r > jn ? xp[k] * scal : (r == jn ? 1.0 : 0.0);
+            vnxt[r] = v;
+            if (r >= jn) T[(long long)jn * N + r] = v;
+          }
+        }
+        if (lane == 0) {
+          taus[jn] = tau;
+          if (P != jn) {
+            double t;
+            t = nrm2[jn]; nrm2[jn] = nrm2[P]; nrm2[P] = t;
+            t = ref2[jn]; ref2[jn] = ref2[P]; ref2[P] = t;
+            t = dsc[jn]; dsc[jn] = dsc[P]; dsc[P] = t;
+            t = wsm[jn]; wsm[jn] = wsm[P]; wsm[P] = t;
+            float f = logd[jn]; logd[jn] = logd[P]; logd[P] = f;
+            int q = perm[jn]; perm[jn] = perm[P]; perm[P] = q;
+          }
+        }
+      }
+      __syncthreads();
+    };
+
+    // ---- norms, first pivot and reflector, first dot products -------------
+    {
+      double ss = 0.0;
+      if (own)
+        for (int r = rg; r < N; r += TPC) {
+          const double x = W[(long long)r * N + c];
+          ss = fma(x, x, ss);
+        }
+      ss = group_sum<TPC>(ss);
+      if (own && rg == 0) { nrm2[c] = ss; ref2[c] = ss; }
+      const float key = own ? logd[c] + 0.5f * log2_wide(ss) : -INFINITY;
+      vote_and_reflect(key, own ? c : 0x7fffffff, 0);
+    }
+    double dc = 0.0, xj = 0.0;   // v_j^T a_c and a_jc (column-uniform)
+    if (own && c > 0) {
+      double xp = 0.0;
+      dc = fused_pass<TPC, BATCH>(W, N, c, rg, vnxt, 0.0, vnxt, 0, xp, false);
+      xj = xp;
+    }
+    dc = group_sum<TPC>(dc);
+    xj = __shfl_sync(FULL, xj, lane % CPW);   // row 0 is in row group 0
+    { double* t = vcur; vcur = vnxt; vnxt = t; }
+
+    // ---- steps j = 0 .. N-2 ------------------------------------------------
+    for (int j = 0; j + 1 < N; ++j) {
+      const double tau = taus[j];
+      const bool act = own && c > j;
+      const double w = tau * dc;
+      const double rjc = xj - w;
+      const double n_old = act ? nrm2[c] : 0.0, r_old = act ? ref2[c] : 0.0;
+      double n2 = fma(-rjc, rjc, n_old);
+      const bool redo = act && n2 <= 1.4901161193847656e-8 * r_old;
+      if (__any_sync(FULL, redo)) {
+        // exact norm of the updated rows below j where the downdate lost too
+        // many digits (the safeguard of LAPACK's xLAQP2)
+        double ex = 0.0;
+        if (redo)
+          for (int r = j + 1 + ((rg - j - 1) % TPC + TPC) % TPC; r < N; r += TPC) {
+            const double x = fma(-vcur[r], w, W[(long long)r * N + c]);
+            ex = fma(x, x, ex);
+          }
+        ex = group_sum<TPC>(ex);
+        if (redo) n2 = ex;
+      }
+      __syncwarp();
+      float key = -INFINITY;
+      int idx = 0x7fffffff;
+      if (act) {
+        if (rg == 0) {
+          wsm[c] = w;
+          nrm2[c] = n2;
+          if (redo) ref2[c] = n2;
+        }
+        key = logd[c] + 0.5f * log2_wide(n2);
+        idx = c;
+      }
+      vote_and_reflect(key, idx, j + 1);
+      // ---- fused pass: update with v_j, dot with v_{j+1} --------------------
+      double dn = 0.0, xn = 0.0;
+      if (own && c > j + 1) {
+        const int r0 = j + ((rg - j) % TPC + TPC) % TPC;   // first row >= j in this row group
+        dn = fused_pass<TPC, BATCH>(W, N, c, r0, vcur, wsm[c], vnxt, j + 1, xn, true);
+      }
+      dn = group_sum<TPC>(dn);
+      xj = __shfl_sync(FULL, xn, (lane % CPW) + CPW * ((j + 1) % TPC));
+      dc = dn;
+      double* t = vcur; vcur = vnxt; vnxt = t;
+    }
+    __syncthreads();
+
+    // ---- Q = H_0 ... H_{N-1} into U, backwards ----------------------------
+    for (long long e = tid; e < NN; e += NT) {
+      const int i = (int)(e / N), cc = (int)(e % N);
+      U[e] = i == cc ? 1.0 : 0.0;
+    }
+    // v_j, v_{j-1} staged one step ahead in three rotating buffers (wsm is
+    // free after the factorisation)
+    auto vq = [&](int k) { return k == 0 ? vA : (k == 1 ? vB : wsm); };
+    for (int r = tid; r < N; r += NT) {
+      vA[r] = r >= N - 1 ? T[(long long)(N - 1) * N + r] : 0.0;
+      if (N >= 2) vB[r] = r >= N - 2 ? T[(long long)(N - 2) * N + r] : 0.0;
+    }
+    __syncthreads();
+    double dq = 1.0;   // v_j^T u_c; column c enters at step c as e_c
+    for (int j = N - 1; j >= 0; --j) {
+      const double* vj = vq((N - 1 - j) % 3);
+      const double* vm = vq((N - j) % 3);
+      if (j >= 2) {
+        double* vs = vq((N + 1 - j) % 3);
+        for (int r = tid; r < N; r += NT) vs[r] = r >= j - 2 ? T[(long long)(j - 2) * N + r] : 0.0;
+      }
+      if (own && c >= j) {
+        if (c == j) dq = 1.0;
+        const double w = taus[j] * dq;
+        const int r0 = j + ((rg - j) % TPC + TPC) % TPC;
+        double xdummy = 0.0;
+        // rows >= j of column c; the dot with v_{j-1} needs no row j-1 (zero
+        // in every column c >= j at this point)
+        dq = fused_pass<TPC, BATCH>(U, N, c, r0, vj, w, j > 0 ? vm : vj, -1, xdummy, true);
+      }
+      dq = group_sum<TPC>(dq);
+      __syncthreads();
+    }
+
+    // ---- outputs D, T, perm (T overwrites the stored reflectors) -----------
+    for (int i = tid; i < N; i += NT) {
+      const double rii = fabs(W[(long long)i * N + i]);
+      const double d = rii * dsc[i];
+      if (!(d > 0.0)) atomicOr(&s_flag, DQMC_STATUS_SINGULAR);
+      if (!isfinite(d)) atomicOr(&s_flag, DQMC_STATUS_NONFINITE_SCALE);
+      Dout[i] = d;
+      nrm2[i] = rii > 0.0 ? 1.0 / rii : 0.0;
+      ref2[i] = dsc[i] > 0.0 ? 1.0 / dsc[i] : 0.0;
+      pout[i] = perm[i];
+    }
+    __syncthreads();
+    for (long long e = tid; e < NN; e += NT) {
+      const int i = (int)(e / N), cc = (int)(e % N);
+      T[e] = cc >= i ? W[e] * nrm2[i] * (dsc[cc] * ref2[i]) : 0.0;
+    }
+    __syncthreads();
+    if (tid == 0 && s_flag && a.status) atomicOr(&a.status[b / a.status_div], s_flag);
+    __syncthreads();
+  }
+}
+
+static size_t qrp_fused_smem(int N) {
+  return (size_t)N * (7 * sizeof(double) + sizeof(float) + sizeof(int)) + 16;
+}
+
+template <int NT, int TPC, int NQ>
+static cudaError_t launch_qrp_fused(const QrpArgs& a, cudaStream_t st) {
+  const size_t sm = qrp_fused_smem(a.N);
+  const int grid = a.batch < (1 << 30) ? a.batch : (1 << 30);
+  cudaError_t e = cudaFuncSetAttribute(qrp_fused_kernel<NT, TPC, NQ>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  qrp_fused_kernel<NT, TPC, NQ><<<grid, NT, sm, st>>>(a);
+  return cudaGetLastError();
+}
+
 static size_t qrp_smem(int N) { return (size_t)N * (6 * sizeof(double) + sizeof(float) + sizeof(int)) + 16; }
 
 cudaError_t qrp_f64(const QrpArgs& a, cudaStream_t st) {
   if (a.batch <= 0 || a.N <= 0) return cudaSuccess;
+  if (a.N <= 32) return launch_qrp_fused<64, 2, 1>(a, st);
+  if (a.N <= 64) return launch_qrp_fused<128, 2, 2>(a, st);
+  if (a.N <= 128) return launch_qrp_fused<256, 2, 4>(a, st);
+  if (a.N <= 256) return launch_qrp_fused<512, 2, 8>(a, st);
   size_t sm = qrp_smem(a.N);
   int grid = a.batch < (1 << 30) ? a.batch : (1 << 30);
   if (a.N <= 32) {
