@@ -231,6 +231,9 @@ struct ChainWs {
   int oz_s = 0, oz_P128 = 0, oz_PK = 0;
   __nv_bfloat16 *ozA = nullptr, *ozB = nullptr;
   int *ozeA = nullptr, *ozeB = nullptr;
+  // per-instance slices of T' for the X update on the tensor cores
+  __nv_bfloat16* ozT = nullptr;
+  int* ozeT = nullptr;
 };
 
 inline int pad_to(int n, int m) { return (n + m - 1) / m * m; }
@@ -254,6 +257,8 @@ void take_ozaki(Arena& ar, int batch, int N, int s, ChainWs& w) {
   w.ozeA = ar.take<int>(w.oz_P128);
   w.ozB = ar.take<__nv_bfloat16>((long long)batch * s * w.oz_PK * w.oz_PK);
   w.ozeB = ar.take<int>((long long)batch * w.oz_PK);
+  w.ozT = ar.take<__nv_bfloat16>((long long)batch * s * w.oz_P128 * w.oz_PK);
+  w.ozeT = ar.take<int>((long long)batch * w.oz_P128);
 }
 
 void take_chain(Arena& ar, int batch, int N, ChainWs& w) {
@@ -298,8 +303,8 @@ dqmc_status chunk_products(dqmc_handle h, int dir, int batch, int N, int M, int 
       CK(ozaki_split(prev, N, 1, sprev, sc, sV, N, PK, PK, sl, w.ozB, (long long)sl * PK * PK,
                      w.ozeB, PK, batch, st));
       CKP(PC_CHAIN, 2.0 * N * N * (double)N * batch,
-          ozaki_gemm(w.ozA, w.ozeA, w.oz_P128, w.ozB, w.ozeB, PK, PK, PK, sl, N, batch, bufs[nb],
-                     NN, nullptr, st));
+          ozaki_gemm(w.ozA, w.ozeA, 0, 0, w.oz_P128, w.ozB, w.ozeB, PK, PK, PK, sl, N, batch,
+                     bufs[nb], NN, nullptr, st));
       prev = bufs[nb];
       sprev = NN;
       nb ^= 1;
@@ -359,6 +364,19 @@ dqmc_status chunk_xupdate(dqmc_handle h, int dir, int batch, int N, int k, int c
   const long long NN = (long long)N * N;
   const int src = dir > 0 ? c : c + 1;
   const int dst = dir > 0 ? c + 1 : c;
+  if (w.oz_s > 0 && lim == nullptr) {
+    // tensor cores: slices of T' (A operand, per instance; row i of T' is a
+    // "column" of the splitter) and of the rows of X_src gathered by perm
+    const int P1 = w.oz_P128, PK = w.oz_PK, sl = w.oz_s;
+    CK(ozaki_split(w.T, 1, N, NN, nullptr, 0, N, P1, PK, sl, w.ozT, (long long)sl * P1 * PK,
+                   w.ozeT, P1, batch, st));
+    CK(ozaki_split(slotX(s, src), N, 1, s.instX, nullptr, 0, N, PK, PK, sl, w.ozB,
+                   (long long)sl * PK * PK, w.ozeB, PK, batch, st, w.perm, N));
+    CKP(PC_XUPD, (double)N * N * (double)N * batch,
+        ozaki_gemm(w.ozT, w.ozeT, (long long)sl * P1 * PK, P1, P1, w.ozB, w.ozeB, PK, PK, PK, sl,
+                   N, batch, slotX(s, dst), s.instX, nullptr, st));
+    return DQMC_OK;
+  }
   GemmArgs g;
   g.M = g.N = g.K = N;
   g.batch = batch;
@@ -762,6 +780,8 @@ static dqmc_status greens_impl(dqmc_handle h, int batch, int N, int M, const dou
       if (cw.oz_s > 0) {
         J[half].w.ozB += o * cw.oz_s * (long long)cw.oz_PK * cw.oz_PK;
         J[half].w.ozeB += o * cw.oz_PK;
+        J[half].w.ozT += o * cw.oz_s * (long long)cw.oz_P128 * cw.oz_PK;
+        J[half].w.ozeT += o * cw.oz_P128;
       }
       J[half].status = stout + o;
     }

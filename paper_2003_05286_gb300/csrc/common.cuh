@@ -177,9 +177,10 @@ namespace dqmc {
 cudaError_t ozaki_split(const double* X, long long ldm, long long ldj, long long sX,
                         const double* sc, long long ssc, int N, int PJ, int PM, int s,
                         __nv_bfloat16* S, long long sS, int* e, long long se, int batch,
-                        cudaStream_t st);
-cudaError_t ozaki_gemm(const __nv_bfloat16* As, const int* eA, int P128, const __nv_bfloat16* Bs,
-                       const int* eB, long long seB, int PN, int PK, int s, int N, int batch,
-                       double* C, long long sC, int* status, cudaStream_t st);
+                        cudaStream_t st, const int* gm = nullptr, long long sgm = 0);
+cudaError_t ozaki_gemm(const __nv_bfloat16* As, const int* eA, long long sA, long long seA,
+                       int P128, const __nv_bfloat16* Bs, const int* eB, long long seB, int PN,
+                       int PK, int s, int N, int batch, double* C, long long sC, int* status,
+                       cudaStream_t st);
 int oz_groups(int s, int N);
 }  // namespace dqmc

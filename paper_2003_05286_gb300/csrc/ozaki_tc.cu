@@ -236,9 +236,9 @@ struct OzPairs {
 
 __global__ void __launch_bounds__(OZ_THREADS, 1)
 ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                  const OzPairs pr, int N, int nkb, const int* __restrict__ eA,
-                  const int* __restrict__ eB, long long seB, double* __restrict__ C,
-                  long long sC, int* status) {
+                  const OzPairs pr, int N, int nkb, const int* __restrict__ eA, long long seA,
+                  int a_batched, const int* __restrict__ eB, long long seB,
+                  double* __restrict__ C, long long sC, int* status) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte aligned stage buffers
   unsigned char* base = reinterpret_cast<unsigned char*>(
@@ -254,6 +254,7 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int n0 = blockIdx.x * OZ_BN, m0 = blockIdx.y * OZ_BM, b = blockIdx.z;
+  const int bA = a_batched ? b : 0;   // instance of the A operand (shared when not batched)
   uint32_t tmem_cols = 32;
   while (tmem_cols < (uint32_t)(pr.ngroups * OZ_BN)) tmem_cols <<= 1;
 
@@ -290,7 +291,7 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
       unsigned char* sb = base + st * stage_bytes;
       mbar_arrive_expect_tx(&full[st], (uint32_t)stage_bytes);
       for (int p = 0; p < s; ++p)
-        tma_load_3d(sb + p * OZ_A_TILE, &tmA, &full[st], kb * OZ_BK, m0, p);
+        tma_load_4d(sb + p * OZ_A_TILE, &tmA, &full[st], kb * OZ_BK, m0, p, bA);
       for (int q = 0; q < s; ++q)
         tma_load_4d(sb + s * OZ_A_TILE + q * OZ_B_TILE, &tmB, &full[st], kb * OZ_BK, n0, q, b);
     }
@@ -327,7 +328,7 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
   // warp w reads TMEM lanes 32 (w % 4) .. +31 (rows) and columns 32 (w / 4) .. +31
   const int row = m0 + (warp & 3) * 32 + lane;
   const int cbase = (warp >> 2) * 32;
-  const int ea = row < N ? eA[row] : 0;
+  const int ea = row < N ? eA[(long long)bA * seA + row] : 0;
   const int* eBb = eB + (long long)b * seB;
   double* Cb = C + (long long)b * sC;
   const int shift0 = 7 * (s + 1);
@@ -382,8 +383,9 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
 }
 
 // ---------------------------------------------------------------------------
-// Splitting kernel: X (FP64, element (m, j) at X[m*ldm + j*ldj]) times an
-// optional scale sc[m] -> s BF16 slice planes S[q][j][m] (K-major, PJ x PM per
+// Splitting kernel: X (FP64, element (m, j) at X[g(m)*ldm + j*ldj], g the
+// optional row gather gm, identity if null) times an optional scale sc[m]
+// -> s BF16 slice planes S[q][j][m] (K-major, PJ x PM per
 // plane, zero padded) and column exponents e[j] with max_m |x_mj| < 2^{e_j}.
 // One CTA per 32 columns j of one instance; 256 threads.
 // ---------------------------------------------------------------------------
@@ -391,7 +393,7 @@ __global__ void __launch_bounds__(256)
 ozaki_split_kernel(const double* __restrict__ X, long long ldm, long long ldj, long long sX,
                    const double* __restrict__ sc, long long ssc, int N, int PJ, int PM, int s,
                    __nv_bfloat16* __restrict__ S, long long sS, int* __restrict__ e,
-                   long long se) {
+                   long long se, const int* __restrict__ gm, long long sgm) {
   extern __shared__ double tile[];   // [PM][33]
   __shared__ int emax[8][32];
   const int b = blockIdx.y;
@@ -399,12 +401,14 @@ ozaki_split_kernel(const double* __restrict__ X, long long ldm, long long ldj, l
   const int tid = threadIdx.x, jj = tid & 31, rg = tid >> 5;
   const double* Xb = X + (long long)b * sX;
   const double* scb = sc ? sc + (long long)b * ssc : nullptr;
+  const int* gmb = gm ? gm + (long long)b * sgm : nullptr;
   const int j = j0 + jj;
   int mx = -2000;
   for (int m = rg; m < PM; m += 8) {
     double v = 0.0;
     if (m < N && j < N) {
-      v = Xb[(long long)m * ldm + (long long)j * ldj];
+      const int mr = gmb ? gmb[m] : m;
+      v = (mr >= 0 && mr < N) ? Xb[(long long)mr * ldm + (long long)j * ldj] : 0.0;
       if (scb) v *= scb[m];
     }
     tile[m * 33 + jj] = v;
@@ -514,29 +518,36 @@ size_t oz_gemm_smem(int s) {
 cudaError_t ozaki_split(const double* X, long long ldm, long long ldj, long long sX,
                         const double* sc, long long ssc, int N, int PJ, int PM, int s,
                         __nv_bfloat16* S, long long sS, int* e, long long se, int batch,
-                        cudaStream_t st) {
+                        cudaStream_t st, const int* gm, long long sgm) {
   size_t sm = (size_t)PM * 33 * sizeof(double);
   cudaFuncSetAttribute(ozaki_split_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   dim3 grid((PJ + 31) / 32, batch);
-  ozaki_split_kernel<<<grid, 256, sm, st>>>(X, ldm, ldj, sX, sc, ssc, N, PJ, PM, s, S, sS, e, se);
+  ozaki_split_kernel<<<grid, 256, sm, st>>>(X, ldm, ldj, sX, sc, ssc, N, PJ, PM, s, S, sS, e, se,
+                                            gm, sgm);
   return cudaGetLastError();
 }
 
-// C_b = 2^{eA} As * (2^{eB_b} Bs_b)  for b < batch.  As: s planes of P128 x PK
-// (rows i, K contiguous), Bs: per instance s planes of PN x PK (columns j, K
-// contiguous); PK, PN multiples of 64, P128 a multiple of 128.
-cudaError_t ozaki_gemm(const __nv_bfloat16* As, const int* eA, int P128, const __nv_bfloat16* Bs,
-                       const int* eB, long long seB, int PN, int PK, int s, int N, int batch,
-                       double* C, long long sC, int* status, cudaStream_t st) {
+// C_b = 2^{eA_b} As_b * (2^{eB_b} Bs_b)  for b < batch.  As: s planes of
+// P128 x PK (rows i, K contiguous) per instance (sA elements apart, eA_b =
+// eA + b seA) or shared by all instances (sA = 0); Bs: per instance s planes of
+// PN x PK (columns j, K contiguous); PK, PN multiples of 64, P128 a multiple of 128.
+cudaError_t ozaki_gemm(const __nv_bfloat16* As, const int* eA, long long sA, long long seA,
+                       int P128, const __nv_bfloat16* Bs, const int* eB, long long seB, int PN,
+                       int PK, int s, int N, int batch, double* C, long long sC, int* status,
+                       cudaStream_t st) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
+  if (sA != 0 && sA < (long long)s * P128 * PK) return cudaErrorInvalidValue;
   CUtensorMap tA, tB;
   {
-    cuuint64_t dims[3] = {(cuuint64_t)PK, (cuuint64_t)P128, (cuuint64_t)s};
-    cuuint64_t strides[2] = {(cuuint64_t)PK * 2, (cuuint64_t)PK * P128 * 2};
-    cuuint32_t box[3] = {OZ_BK, OZ_BM, 1};
-    cuuint32_t es[3] = {1, 1, 1};
-    if (enc(&tA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)As, dims, strides, box, es,
+    const int nA = sA ? batch : 1;
+    const long long strideA = sA ? sA : (long long)s * P128 * PK;
+    cuuint64_t dims[4] = {(cuuint64_t)PK, (cuuint64_t)P128, (cuuint64_t)s, (cuuint64_t)nA};
+    cuuint64_t strides[3] = {(cuuint64_t)PK * 2, (cuuint64_t)PK * P128 * 2,
+                             (cuuint64_t)strideA * 2};
+    cuuint32_t box[4] = {OZ_BK, OZ_BM, 1, 1};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    if (enc(&tA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)As, dims, strides, box, es,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return cudaErrorInvalidValue;
@@ -558,8 +569,8 @@ cudaError_t ozaki_gemm(const __nv_bfloat16* As, const int* eA, int P128, const _
   size_t sm = oz_gemm_smem(s);
   cudaFuncSetAttribute(ozaki_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   dim3 grid((N + OZ_BN - 1) / OZ_BN, (N + OZ_BM - 1) / OZ_BM, batch);
-  ozaki_gemm_kernel<<<grid, OZ_THREADS, sm, st>>>(tA, tB, pr, N, PK / OZ_BK, eA, eB, seB, C, sC,
-                                                  status);
+  ozaki_gemm_kernel<<<grid, OZ_THREADS, sm, st>>>(tA, tB, pr, N, PK / OZ_BK, eA, seA, sA != 0, eB,
+                                                  seB, C, sC, status);
   return cudaGetLastError();
 }
 
