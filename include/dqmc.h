@@ -206,6 +206,19 @@ dqmc_status dqmc_greens_noalloc(void* stream, int batch, int N, int M, const dou
                                 double dtau, const double* V, int k, double* G, double* logdet,
                                 int* sign, int* status);
 
+/* Self-test of the bounded device-side waits.  The paper has no counterpart:
+ * the only waits in the library are the mbarrier waits of the tensor-core
+ * slice product (DQMC_CHAIN_BF16Xs), and each gives up after about 2 s.  This
+ * call launches, on `stream` (a cudaStream_t, NULL = legacy default stream),
+ * one CTA of that product on internal 64 x 64 operands with its operand loads
+ * switched off, so the wait for the first K-block runs out.  The CTA then ORs
+ * DQMC_STATUS_TIMEOUT into *status (one device int, owned by the caller, not
+ * cleared here), waits (bounded) for copies in flight, frees its tensor memory
+ * and exits; the context stays usable.  Asynchronous: synchronise the stream
+ * before reading *status; the launch occupies the device for about 6 s.
+ * Returns DQMC_ERR_ARG for a NULL status, DQMC_ERR_CUDA if the launch fails. */
+dqmc_status dqmc_selftest_wait_timeout(void* stream, int* status);
+
 #ifdef __cplusplus
 }
 #endif

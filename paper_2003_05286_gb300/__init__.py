@@ -19,7 +19,7 @@ import torch
 from . import _abi
 
 __all__ = ["Handle", "greens", "logdet", "greens_tdisplaced", "logdet_grad", "greens_ragged",
-           "LogDet", "n_tau", "lib"]
+           "selftest_wait_timeout", "LogDet", "n_tau", "lib"]
 
 
 def lib():
@@ -221,6 +221,16 @@ def greens_ragged(instances, *, handle: Handle | None = None, device=None):
         N = descs[i].N
         Gs.append(Gp[descs[i].off_G: descs[i].off_G + N * N].view(N, N))
     return Gs, ld, sg, st
+
+
+def selftest_wait_timeout(status: torch.Tensor, stream: torch.cuda.Stream | None = None):
+    """Launch the bounded-wait self-test (dqmc_selftest_wait_timeout); status: a CUDA int32
+    tensor of one element that receives DQMC_STATUS_TIMEOUT.  Asynchronous on the stream."""
+    if not status.is_cuda or status.dtype != torch.int32 or status.numel() < 1:
+        raise ValueError("status must be a CUDA int32 tensor")
+    s = stream if stream is not None else torch.cuda.current_stream()
+    _abi.check(lib().dqmc_selftest_wait_timeout(C.c_void_p(s.cuda_stream), _ptr(status)),
+               "dqmc_selftest_wait_timeout")
 
 
 class LogDet(torch.autograd.Function):

@@ -15,10 +15,10 @@ STATUS_STRINGS = {
 }
 STATUS_BITS = {
     "NONFINITE_INPUT": 1 << 0, "NONFINITE_SCALE": 1 << 1, "SINGULAR": 1 << 2,
-    "NONFINITE_OUTPUT": 1 << 3, "BAD_K": 1 << 4,
+    "NONFINITE_OUTPUT": 1 << 3, "BAD_K": 1 << 4, "TIMEOUT": 1 << 5,
 }
 CHAIN_FP64 = 0
-CHAIN_BF16X3 = 2
+CHAIN_BF16X3 = 3
 PTR_DEVICE = 0
 PTR_HOST = 1
 
@@ -54,6 +54,7 @@ SIGNATURES = {
     "dqmc_logdet_grad": (_I, [_P, _I, _I, _I, _P, _D, _P, _I, _P, _P, _P, _P]),
     "dqmc_greens_ragged": (_I, [_P, _I, C.POINTER(DqmcInstance), _P, _P, _P, _P, _P, _P]),
     "dqmc_greens_noalloc": (_I, [_P, _I, _I, _I, _P, _D, _P, _I, _P, _P, _P, _P]),
+    "dqmc_selftest_wait_timeout": (_I, [_P, _P]),
 }
 
 _lib = None

@@ -280,7 +280,7 @@ inline double* slotX(const Slots& s, int slot) {
 // a1 for chunk c: k slice products into the chunk buffers; *out = last product.
 dqmc_status chunk_products(dqmc_handle h, int dir, int batch, int N, int M, int k, int c,
                            const double* E, const double* expV, long long sV, const Slots& s,
-                           const ChainWs& w, const int* lim, const double** out) {
+                           const ChainWs& w, const int* lim, const double** out, int* status) {
   cudaStream_t st = h->cur;
   const long long NN = (long long)N * N;
   const int src = dir > 0 ? c : c + 1;
@@ -304,7 +304,7 @@ dqmc_status chunk_products(dqmc_handle h, int dir, int batch, int N, int M, int 
                      w.ozeB, PK, batch, st));
       CKP(PC_CHAIN, 2.0 * N * N * (double)N * batch,
           ozaki_gemm(w.ozA, w.ozeA, 0, 0, w.oz_P128, w.ozB, w.ozeB, PK, PK, PK, sl, N, batch,
-                     bufs[nb], NN, nullptr, st));
+                     bufs[nb], NN, status, st));
       prev = bufs[nb];
       sprev = NN;
       nb ^= 1;
@@ -359,7 +359,7 @@ dqmc_status chunk_qr(dqmc_handle h, int dir, int batch, int N, int k, int c, con
 
 // a4 for chunk c: X_dst = T' X_src[perm].
 dqmc_status chunk_xupdate(dqmc_handle h, int dir, int batch, int N, int k, int c, const Slots& s,
-                          const ChainWs& w, const int* lim) {
+                          const ChainWs& w, const int* lim, int* status) {
   cudaStream_t st = h->cur;
   const long long NN = (long long)N * N;
   const int src = dir > 0 ? c : c + 1;
@@ -374,7 +374,7 @@ dqmc_status chunk_xupdate(dqmc_handle h, int dir, int batch, int N, int k, int c
                    (long long)sl * PK * PK, w.ozeB, PK, batch, st, w.perm, N));
     CKP(PC_XUPD, (double)N * N * (double)N * batch,
         ozaki_gemm(w.ozT, w.ozeT, (long long)sl * P1 * PK, P1, P1, w.ozB, w.ozeB, PK, PK, PK, sl,
-                   N, batch, slotX(s, dst), s.instX, nullptr, st));
+                   N, batch, slotX(s, dst), s.instX, status, st));
     return DQMC_OK;
   }
   GemmArgs g;
@@ -393,7 +393,7 @@ dqmc_status chunk_refactor(dqmc_handle h, int dir, int batch, int N, int k, int 
                            const double* A, const Slots& s, const ChainWs& w, int* status,
                            const int* lim) {
   CKS(chunk_qr(h, dir, batch, N, k, c, A, s, w, status, lim));
-  return chunk_xupdate(h, dir, batch, N, k, c, s, w, lim);
+  return chunk_xupdate(h, dir, batch, N, k, c, s, w, lim, status);
 }
 
 // lim (nullable, per instance): chain length M_b of ragged batches; slices
@@ -405,7 +405,7 @@ dqmc_status run_chain(dqmc_handle h, int dir, int batch, int N, int M, int k, co
   for (int step = 0; step < nc; ++step) {
     const int c = dir > 0 ? step : nc - 1 - step;
     const double* A = nullptr;
-    CKS(chunk_products(h, dir, batch, N, M, k, c, E, expV, sV, s, w, lim, &A));
+    CKS(chunk_products(h, dir, batch, N, M, k, c, E, expV, sV, s, w, lim, &A, status));
     CKS(chunk_refactor(h, dir, batch, N, k, c, A, s, w, status, lim));
   }
   return DQMC_OK;
@@ -447,45 +447,57 @@ bool pipeline_enabled() {
   return !(e && e[0] == '0');
 }
 
-dqmc_status run_chain_pair(dqmc_handle h, const ChainJob job[2], int N, int M, int k,
-                           const double* E) {
-  CKS(ensure_aux(h, 2));
+// Number of staggered sub-batches of an equal-time chain: DQMC_PIPELINE=n
+// (2..4) overrides the default (2 for FP64 products, 4 for tensor-core ones).
+int pipeline_jobs(bool mixed) {
+  const char* e = getenv("DQMC_PIPELINE");
+  if (e && e[0] >= '2' && e[0] <= '4' && e[1] == 0) return e[0] - '0';
+  return mixed ? 4 : 2;
+}
+
+dqmc_status run_chain_multi(dqmc_handle h, const ChainJob* job, int nj, int N, int M, int k,
+                            const double* E) {
+  if (nj < 1 || nj > 4) return DQMC_ERR_ARG;
+  CKS(ensure_aux(h, (size_t)nj));
   cudaStream_t main = h->stream;
   cudaEvent_t fork = h->auxev[0];
   cudaEventRecord(fork, main);
-  cudaStreamWaitEvent(h->aux[0], fork, 0);
-  cudaStreamWaitEvent(h->aux[1], fork, 0);
-  cudaEvent_t ev[2];
-  if (cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming) != cudaSuccess) return DQMC_ERR_CUDA;
-  if (cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming) != cudaSuccess) {
-    cudaEventDestroy(ev[0]);
-    return DQMC_ERR_CUDA;
-  }
-  const int nc = n_chunks(M, k);
+  for (int i = 0; i < nj; ++i) cudaStreamWaitEvent(h->aux[i], fork, 0);
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   dqmc_status rc = DQMC_OK;
+  for (int i = 0; i < nj && rc == DQMC_OK; ++i)
+    if (cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming) != cudaSuccess) rc = DQMC_ERR_CUDA;
+  const int nc = n_chunks(M, k);
   for (int step = 0; step < nc && rc == DQMC_OK; ++step) {
-    for (int half = 0; half < 2 && rc == DQMC_OK; ++half) {
-      const ChainJob& J = job[half];
+    for (int i = 0; i < nj && rc == DQMC_OK; ++i) {
+      const ChainJob& J = job[i];
       const int c = J.dir > 0 ? step : nc - 1 - step;
-      h->cur = h->aux[half];
-      // products of this half wait for the other half's previous product phase
-      if (half == 0 && step > 0) cudaStreamWaitEvent(h->cur, ev[1], 0);
-      if (half == 1) cudaStreamWaitEvent(h->cur, ev[0], 0);
+      h->cur = h->aux[i];
+      // product phases run one after another: job i after job i-1 of this
+      // chunk, job 0 after the last job of the previous chunk
+      if (i > 0) cudaStreamWaitEvent(h->cur, ev[i - 1], 0);
+      else if (step > 0) cudaStreamWaitEvent(h->cur, ev[nj - 1], 0);
       const double* A = nullptr;
-      rc = chunk_products(h, J.dir, J.batch, N, M, k, c, E, J.expV, J.sV, J.s, J.w, nullptr, &A);
+      rc = chunk_products(h, J.dir, J.batch, N, M, k, c, E, J.expV, J.sV, J.s, J.w, nullptr, &A,
+                          J.status);
       if (rc != DQMC_OK) break;
-      cudaEventRecord(ev[half], h->cur);
+      cudaEventRecord(ev[i], h->cur);
       rc = chunk_refactor(h, J.dir, J.batch, N, k, c, A, J.s, J.w, J.status, nullptr);
     }
   }
-  for (int half = 0; half < 2; ++half) {
-    cudaEventRecord(h->auxev[half], h->aux[half]);
-    cudaStreamWaitEvent(main, h->auxev[half], 0);
+  for (int i = 0; i < nj; ++i) {
+    cudaEventRecord(h->auxev[i], h->aux[i]);
+    cudaStreamWaitEvent(main, h->auxev[i], 0);
   }
-  cudaEventDestroy(ev[0]);
-  cudaEventDestroy(ev[1]);
+  for (int i = 0; i < nj; ++i)
+    if (ev[i]) cudaEventDestroy(ev[i]);
   h->cur = main;
   return rc;
+}
+
+dqmc_status run_chain_pair(dqmc_handle h, const ChainJob job[2], int N, int M, int k,
+                           const double* E) {
+  return run_chain_multi(h, job, 2, N, M, k, E);
 }
 
 // ---------------------------------------------------------------------------
@@ -762,30 +774,33 @@ static dqmc_status greens_impl(dqmc_handle h, int batch, int N, int M, const dou
   s.D = D; s.slotD = 0; s.instD = N;
   s.X = X0; s.slotX = 0; s.instX = NN;
   s.X2 = X1;
-  if (batch >= 8 && pipeline_enabled()) {
-    // two half-batches, QR of one overlapping the products of the other
-    const int bA = batch / 2;
-    ChainJob J[2];
-    for (int half = 0; half < 2; ++half) {
-      const long long o = half ? bA : 0;
-      J[half].dir = +1;
-      J[half].batch = half ? batch - bA : bA;
-      J[half].expV = expV + o * Mp * N;
-      J[half].sV = Mp * N;
-      J[half].s = s;
-      J[half].s.U += o * NN; J[half].s.D += o * N; J[half].s.X += o * NN; J[half].s.X2 += o * NN;
-      J[half].w = cw;
-      J[half].w.C0 += o * NN; J[half].w.C1 += o * NN; J[half].w.W += o * NN; J[half].w.T += o * NN;
-      J[half].w.perm += o * N;
+  const int nj = pipeline_jobs(cw.oz_s > 0);
+  if (batch >= 4 * nj && pipeline_enabled()) {
+    // nj sub-batches on nj streams, product phases staggered so that the QRs
+    // of some sub-batches run while the others multiply
+    ChainJob J[4];
+    long long o = 0;
+    for (int q = 0; q < nj; ++q) {
+      const int nb = batch / nj + (q < batch % nj ? 1 : 0);
+      J[q].dir = +1;
+      J[q].batch = nb;
+      J[q].expV = expV + o * Mp * N;
+      J[q].sV = Mp * N;
+      J[q].s = s;
+      J[q].s.U += o * NN; J[q].s.D += o * N; J[q].s.X += o * NN; J[q].s.X2 += o * NN;
+      J[q].w = cw;
+      J[q].w.C0 += o * NN; J[q].w.C1 += o * NN; J[q].w.W += o * NN; J[q].w.T += o * NN;
+      J[q].w.perm += o * N;
       if (cw.oz_s > 0) {
-        J[half].w.ozB += o * cw.oz_s * (long long)cw.oz_PK * cw.oz_PK;
-        J[half].w.ozeB += o * cw.oz_PK;
-        J[half].w.ozT += o * cw.oz_s * (long long)cw.oz_P128 * cw.oz_PK;
-        J[half].w.ozeT += o * cw.oz_P128;
+        J[q].w.ozB += o * cw.oz_s * (long long)cw.oz_PK * cw.oz_PK;
+        J[q].w.ozeB += o * cw.oz_PK;
+        J[q].w.ozT += o * cw.oz_s * (long long)cw.oz_P128 * cw.oz_PK;
+        J[q].w.ozeT += o * cw.oz_P128;
       }
-      J[half].status = stout + o;
+      J[q].status = stout + o;
+      o += nb;
     }
-    CKS(run_chain_pair(h, J, N, M, k, E));
+    CKS(run_chain_multi(h, J, nj, N, M, k, E));
   } else {
     CKS(run_chain(h, +1, batch, N, M, k, E, expV, Mp * N, s, cw, stout));
   }

@@ -183,4 +183,7 @@ cudaError_t ozaki_gemm(const __nv_bfloat16* As, const int* eA, long long sA, lon
                        int PK, int s, int N, int batch, double* C, long long sC, int* status,
                        cudaStream_t st);
 int oz_groups(int s, int N);
+// One CTA of ozaki_gemm_kernel whose loads are never issued: its bounded
+// waits run out and it ORs DQMC_STATUS_TIMEOUT into *status (device int).
+cudaError_t ozaki_selftest_timeout(int* status, cudaStream_t st);
 }  // namespace dqmc

@@ -232,6 +232,7 @@ struct OzPairs {
   int s;                 // slices per operand
   int shift[8];          // weight 2^{shift} of group g relative to the lowest kept weight
   unsigned char p[40], q[40], g[40], first[40];
+  int stall;             // self-test only: the producer issues no loads
 };
 
 __global__ void __launch_bounds__(OZ_THREADS, 1)
@@ -281,7 +282,7 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
 
   if (warp == 0 && lane == 0) {
     // ---- producer: TMA loads of the slice tiles of each K-block -----------
-    for (int kb = 0; kb < nkb; ++kb) {
+    for (int kb = 0; kb < (pr.stall ? 0 : nkb); ++kb) {
       const int st = kb % OZ_STAGES;
       if (kb >= OZ_STAGES && !mbar_wait(&empty[st], ((kb / OZ_STAGES) - 1) & 1)) {
         atomicOr(s_fail, 1);
@@ -531,10 +532,11 @@ cudaError_t ozaki_split(const double* X, long long ldm, long long ldj, long long
 // P128 x PK (rows i, K contiguous) per instance (sA elements apart, eA_b =
 // eA + b seA) or shared by all instances (sA = 0); Bs: per instance s planes of
 // PN x PK (columns j, K contiguous); PK, PN multiples of 64, P128 a multiple of 128.
-cudaError_t ozaki_gemm(const __nv_bfloat16* As, const int* eA, long long sA, long long seA,
-                       int P128, const __nv_bfloat16* Bs, const int* eB, long long seB, int PN,
-                       int PK, int s, int N, int batch, double* C, long long sC, int* status,
-                       cudaStream_t st) {
+static cudaError_t ozaki_gemm_impl(const __nv_bfloat16* As, const int* eA, long long sA,
+                                   long long seA, int P128, const __nv_bfloat16* Bs, const int* eB,
+                                   long long seB, int PN, int PK, int s, int N, int batch,
+                                   double* C, long long sC, int* status, cudaStream_t st,
+                                   int stall) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
   if (sA != 0 && sA < (long long)s * P128 * PK) return cudaErrorInvalidValue;
@@ -566,6 +568,7 @@ cudaError_t ozaki_gemm(const __nv_bfloat16* As, const int* eA, long long sA, lon
   if (s < 1 || s > 8) return cudaErrorInvalidValue;
   OzPairs pr = oz_pairs(s, N);
   if (pr.ngroups > 8 || pr.n > 40) return cudaErrorNotSupported;
+  pr.stall = stall;
   size_t sm = oz_gemm_smem(s);
   cudaFuncSetAttribute(ozaki_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   dim3 grid((N + OZ_BN - 1) / OZ_BN, (N + OZ_BM - 1) / OZ_BM, batch);
@@ -574,4 +577,38 @@ cudaError_t ozaki_gemm(const __nv_bfloat16* As, const int* eA, long long sA, lon
   return cudaGetLastError();
 }
 
+cudaError_t ozaki_gemm(const __nv_bfloat16* As, const int* eA, long long sA, long long seA,
+                       int P128, const __nv_bfloat16* Bs, const int* eB, long long seB, int PN,
+                       int PK, int s, int N, int batch, double* C, long long sC, int* status,
+                       cudaStream_t st) {
+  return ozaki_gemm_impl(As, eA, sA, seA, P128, Bs, eB, seB, PN, PK, s, N, batch, C, sC, status,
+                         st, 0);
+}
+
+// Operands of the bounded-wait self-test: one 128 x 64 tile, one slice.
+static __device__ __align__(1024) __nv_bfloat16 g_selftest_A[128 * 64];
+static __device__ __align__(1024) __nv_bfloat16 g_selftest_B[64 * 64];
+static __device__ int g_selftest_e[128];
+static __device__ double g_selftest_C[64 * 64];
+
+cudaError_t ozaki_selftest_timeout(int* status, cudaStream_t st) {
+  void *A = nullptr, *B = nullptr, *e = nullptr, *C = nullptr;
+  cudaError_t r;
+  if ((r = cudaGetSymbolAddress(&A, g_selftest_A)) != cudaSuccess) return r;
+  if ((r = cudaGetSymbolAddress(&B, g_selftest_B)) != cudaSuccess) return r;
+  if ((r = cudaGetSymbolAddress(&e, g_selftest_e)) != cudaSuccess) return r;
+  if ((r = cudaGetSymbolAddress(&C, g_selftest_C)) != cudaSuccess) return r;
+  return ozaki_gemm_impl(static_cast<const __nv_bfloat16*>(A), static_cast<const int*>(e), 0, 0,
+                         128, static_cast<const __nv_bfloat16*>(B), static_cast<const int*>(e), 0,
+                         64, 64, 1, 64, 1, static_cast<double*>(C), 0, status, st, 1);
+}
+
 }  // namespace dqmc
+
+// Self-test of the bounded device-side waits (see include/dqmc.h).
+extern "C" dqmc_status dqmc_selftest_wait_timeout(void* stream, int* status) {
+  if (!status) return DQMC_ERR_ARG;
+  return dqmc::ozaki_selftest_timeout(status, static_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? DQMC_OK
+             : DQMC_ERR_CUDA;
+}
