@@ -40,6 +40,16 @@ import dqmc_inputs as di  # noqa: E402
 # issue rate; a DFMA-only probe on this pool measured 1.20 TFLOP/s at ~2.0 GHz.
 FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12
 
+
+def bf16_peak_tflops():
+    """Measured dense bf16 rate of this machine's GB300 (sustained figure: the tensor-core
+    product runs inside a long step), else the recipe's fallback."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops_sustained"]), "measured (bf16_tflops_sustained)"
+    except Exception:
+        return 1700.0, "fallback (sustained)"
+
 WORKLOADS = {
     # equal-time G + log det (the headline workload)
     "n256_beta20": dict(L=16, U=4.0, dtau=0.1, beta=20.0, k=10, batch=128, config=4),
@@ -305,6 +315,7 @@ def run_gpu(args, wl, rank, world):
     tot_ms = sum(step_ms)
     tot_ms = reduce_max(tot_ms, dev)
     chain_ms, chain_n, chain_flops = h.profile_read(h.PROF_CHAIN)
+    qr_ms, qr_n, qr_flops = h.profile_read(h.PROF_QRP)
     h.profile(False)
     bad = int((st != 0).sum().item())
 
@@ -387,8 +398,28 @@ def run_gpu(args, wl, rank, world):
         cpu = {"value": rate, "unit": "G/s", "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"{n} instance(s) of the {args.workload} workload run one after "
                          f"another in {dt:.1f} s (NumPy/SciPy FP64, BLAS threads = all cores)"}
-    achieved = (chain_flops / (chain_ms / 1e3)) / 1e12 if chain_ms > 0 else None
-    traffic = measured_traffic(args.workload)
+    if prec == 0:
+        # dominant kernel: the FP64 slice product
+        dom_ms, dom_n, dom_flops = chain_ms, chain_n, chain_flops
+        dom_kernel = "gemm_f64_kernel (slice-chain product, 2N^3 x batch flops per launch)"
+        traffic = measured_traffic(args.workload)
+    else:
+        # products on the tensor cores: the FP64 pivoted QR dominates the step
+        dom_ms, dom_n, dom_flops = qr_ms, qr_n, qr_flops
+        dom_kernel = "qrp_fused_kernel (pivoted QR incl. forming Q, 8N^3/3 x batch flops per launch)"
+        traffic = None
+    achieved = (dom_flops / (dom_ms / 1e3)) / 1e12 if dom_ms > 0 else None
+    roof_tensor = None
+    if prec > 0 and chain_ms > 0:
+        pairs = prec * (prec + 1) // 2          # digit pairs p + q <= s + 1
+        t_ach = chain_flops * pairs / (chain_ms / 1e3) / 1e12
+        t_peak, t_src = bf16_peak_tflops()
+        roof_tensor = {"bound": "tensor", "achieved": t_ach, "peak": t_peak, "unit": "TFLOP/s",
+                       "frac": t_ach / t_peak, "traffic": None,
+                       "kernel": f"ozaki_gemm_kernel ({pairs} BF16 digit-pair products of 2N^3 per "
+                                 "slice product and instance)",
+                       "launches": chain_n, "avg_launch_ms": chain_ms / max(chain_n, 1),
+                       "peak_source": t_src}
     line = {
         "metric": "greens_functions_per_second", "value": value, "unit": "G/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -403,10 +434,11 @@ def run_gpu(args, wl, rank, world):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
                      "traffic": traffic,
-                     "kernel": "gemm_f64_kernel (slice-chain product, 2N^3 x batch flops per launch)",
-                     "launches": chain_n, "avg_launch_ms": chain_ms / max(chain_n, 1),
-                     "share_of_step": chain_ms / tot_ms if tot_ms > 0 else None,
+                     "kernel": dom_kernel,
+                     "launches": dom_n, "avg_launch_ms": dom_ms / max(dom_n, 1),
+                     "stream_time_share": dom_ms / tot_ms if tot_ms > 0 else None,
                      "peak_source": "derived: 152 SM x 4 FP64 flop/clk x 2070 MHz"},
+        "roofline_tensor": roof_tensor,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
         "e2e": e2e,
@@ -446,7 +478,10 @@ def run_gpu_other(args, wl, rank, world):
             kbyL[L] = best["k"]
         insts = [di.ragged_instance(rank * batch + i, kbyL[p[0]]) for i, p in enumerate(insts0)]
         extra["k_by_L"] = kbyL
-        items = [(torch.tensor(x.K, device=dev), x.dtau, torch.tensor(x.V, device=dev), x.k) for x in insts]
+        Kby = {}   # one hopping matrix per lattice size, shared by its instances
+        for x in insts:
+            Kby.setdefault(x.N, torch.tensor(x.K, device=dev))
+        items = [(Kby[x.N], x.dtau, torch.tensor(x.V, device=dev), x.k) for x in insts]
         fl = sum(flops_per_greens(x.N, x.M, x.k) for x in insts)
 
         def step():

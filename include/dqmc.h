@@ -165,7 +165,9 @@ dqmc_status dqmc_logdet_grad(dqmc_handle h, int batch, int N, int M,
  * desc is a HOST array of `batch` descriptors; offsets are in doubles into
  * the pools (K_pool holds each instance's N*N hopping matrix at off_K,
  * V_pool its M*N field at off_V, G_pool its N*N output at off_G).
- * logdet/sign/status are indexed by instance and may be NULL. */
+ * Instances with equal (N, k, dtau, off_K) run as one batched chain (their M
+ * may differ): instances with the same hopping matrix should point at one
+ * copy of it.  logdet/sign/status are indexed by instance and may be NULL. */
 typedef struct {
   int N, M, k, pad;
   double dtau;

@@ -192,18 +192,24 @@ def logdet_grad(K, dtau: float, V, k: int, *, handle: Handle | None = None):
 def greens_ragged(instances, *, handle: Handle | None = None, device=None):
     """Ragged batch.  ``instances``: list of (K, dtau, V, k) with CUDA float64 K (N,N), V (M,N).
 
-    Packs the pools on the device and returns (list of G, logdet, sign, status)."""
+    Packs the pools on the device and returns (list of G, logdet, sign, status).
+    Instances that pass the same K tensor are batched together (per N, k, dtau)."""
     device = device or instances[0][0].device
     descs = (_abi.DqmcInstance * len(instances))()
     offK = offV = offG = 0
     Ks, Vs = [], []
+    seenK = {}   # K storage -> pool offset: instances sharing a K tensor share its offset,
+    #              which lets the library batch them (groups are keyed by N, k, dtau, off_K)
     for i, (K, dtau, V, k) in enumerate(instances):
         N = K.shape[0]
         M = V.shape[0]
-        descs[i] = _abi.DqmcInstance(N, M, int(k), 0, float(dtau), offK, offV, offG)
-        Ks.append(K.reshape(-1))
+        key = (K.data_ptr(), tuple(K.shape), tuple(K.stride()))
+        if key not in seenK:
+            seenK[key] = offK
+            Ks.append(K.reshape(-1))
+            offK += N * N
+        descs[i] = _abi.DqmcInstance(N, M, int(k), 0, float(dtau), seenK[key], offV, offG)
         Vs.append(V.reshape(-1))
-        offK += N * N
         offV += M * N
         offG += N * N
     Kp = torch.cat(Ks).to(device=device, dtype=torch.float64).contiguous()

@@ -45,11 +45,34 @@ def test_ragged_small_mixed(dq):
         assert torch.equal(G1, Gs[i]) and float(ld1) == float(ld[i])
 
 
+def test_ragged_shared_K_batches(dq):
+    """Instances that share a K tensor run as one batched chain per (N, k, dtau), with
+    different M inside a batch; each result still equals its own single-instance call."""
+    insts = []
+    for i in range(24):
+        L = (3, 4)[i % 2]
+        beta = 1.0 + 0.5 * (i % 7)
+        insts.append(di.hubbard_instance(L, 4.0, 0.1, beta, 5, 2000 + i))
+    Ks = {L: _dev(di.square_hopping(L)) for L in (3, 4)}
+    items = [(Ks[int(round(x.N ** 0.5))], x.dtau, _dev(x.V), x.k) for x in insts]
+    Gs, ld, sg, st = dq.greens_ragged(items)
+    assert int((st != 0).sum()) == 0
+    for i, x in enumerate(insts):
+        Go, ldo, so = od.greens(x.K, x.dtau, x.V, x.k)
+        assert np.abs(Gs[i].cpu().numpy() - Go).max() <= GTOL * max(1.0, np.abs(Go).max()), i
+        G1, ld1, _, _ = dq.greens(_dev(x.K), x.dtau, _dev(x.V), x.k)
+        assert torch.equal(G1, Gs[i]) and float(ld1) == float(ld[i]), i
+
+
 def test_ragged_full_size_sampled(dq):
     """1024 instances, N in {36,64,100,144,256}, beta in [10,50] (M in [100,500]),
-    U in [2,8], k = 10; the smallest and largest instances of each N against the oracle."""
+    U in [2,8], k = 10, one K per lattice size; the smallest and largest instances of
+    each N against the oracle."""
     insts = [di.ragged_instance(i, 10) for i in range(1024)]
-    Gs, ld, sg, st = dq.greens_ragged([(_dev(x.K), x.dtau, _dev(x.V), x.k) for x in insts])
+    Ks = {}
+    for x in insts:
+        Ks.setdefault(x.N, _dev(x.K))
+    Gs, ld, sg, st = dq.greens_ragged([(Ks[x.N], x.dtau, _dev(x.V), x.k) for x in insts])
     assert int((st != 0).sum()) == 0
     byN = {}
     for i, x in enumerate(insts):
