@@ -59,7 +59,8 @@ WORKLOADS = {
     "grad_n144": dict(L=12, g=1.5, dtau=0.1, beta=20.0, k=10, batch=64, config=5),
     # 1024 instances of uneven N and M in one call, k autotuned per N
     "ragged_1024": dict(batch=1024, config=3),
-    "n16_beta8": dict(L=4, U=4.0, dtau=0.1, beta=8.0, k=10, batch=1, config=1),
+    # one small configuration: launch bound, so recorded once as a CUDA graph and replayed
+    "n16_beta8": dict(L=4, U=4.0, dtau=0.1, beta=8.0, k=10, batch=1, config=1, graphs=True),
 }
 
 
@@ -76,6 +77,8 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--precision", default="fp64", choices=["fp64"] + [f"bf16x{i}" for i in range(3, 9)],
                    help="chain-product precision of the timed steps (QR and inversions stay FP64)")
+    p.add_argument("--graphs", default="auto", choices=["auto", "on", "off"],
+                   help="CUDA-graph mode of the handle (auto: on for the launch-bound workloads)")
     p.add_argument("--mixed-slices", type=int, default=8,
                    help="also time the mixed chain with this many BF16 slices (0: skip)")
     return p.parse_args()
@@ -262,6 +265,10 @@ def run_reference(args, wl, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def use_graphs(args, wl):
+    return args.graphs == "on" or (args.graphs == "auto" and bool(wl.get("graphs")))
+
+
 def run_gpu(args, wl, rank, world):
     import torch
     import paper_2003_05286_gb300 as dq
@@ -279,7 +286,8 @@ def run_gpu(args, wl, rank, world):
     K = torch.tensor(K_np, device=dev)
     V = torch.tensor(V_np, device=dev)
     prec = 0 if args.precision == "fp64" else int(args.precision[-1])
-    h = dq.Handle(chain_precision=prec)
+    graphs = use_graphs(args, wl)
+    h = dq.Handle(chain_precision=prec, graphs=graphs)
     h.bind_stream()
 
     def step():
@@ -427,7 +435,7 @@ def run_gpu(args, wl, rank, world):
         "vs_baseline": None, "dtype": "f64" if prec == 0 else f"bf16x{prec}+f64", "data": "synthetic",
         "config": {"workload": args.workload, "N": N, "M": M, "k": k, "beta": wl["beta"],
                    "U": wl["U"], "dtau": wl["dtau"], "instances_per_gpu": batch,
-                   "chain_precision": args.precision,
+                   "chain_precision": args.precision, "cuda_graphs": graphs,
                    "l2": "flushed between timed steps (256 MB write)"},
         "fp64_tflops": fl * batch * world * args.steps / (tot_ms / 1e3) / 1e12,
         "fp64_frac_of_peak": fl * batch * args.steps / (tot_ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
@@ -459,7 +467,8 @@ def run_gpu_other(args, wl, rank, world):
     batch = args.batch or wl["batch"]
     name = args.workload
     prec = 0 if args.precision == "fp64" or name == "ragged_1024" else int(args.precision[-1])
-    h = dq.Handle(chain_precision=prec)
+    graphs = use_graphs(args, wl)
+    h = dq.Handle(chain_precision=prec, graphs=graphs)
     h.bind_stream()
     extra = {}
     if name == "ragged_1024":
@@ -544,6 +553,7 @@ def run_gpu_other(args, wl, rank, world):
             "vs_baseline": None, "dtype": "f64" if prec == 0 else f"bf16x{prec}+f64",
             "data": "synthetic",
             "config": dict(workload=name, instances_per_gpu=batch, chain_precision=prec,
+                           cuda_graphs=graphs,
                            l2="flushed between timed steps (256 MB write)", **extra),
             "roofline": {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
                          "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,

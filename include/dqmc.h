@@ -102,6 +102,18 @@ dqmc_status dqmc_destroy(dqmc_handle h);
 dqmc_status dqmc_set_stream(dqmc_handle h, void* stream);
 dqmc_status dqmc_set_pointer_mode(dqmc_handle h, dqmc_pointer_mode mode);
 dqmc_status dqmc_set_chain_precision(dqmc_handle h, dqmc_chain_prec prec);
+/* CUDA-graph mode (default off).  When on, a call of dqmc_greens, dqmc_logdet,
+ * dqmc_greens_tdisplaced or dqmc_logdet_grad is recorded by stream capture and
+ * launched as one CUDA graph; the next call with identical arguments (same
+ * pointers, sizes, dtau, k) and settings replays that graph without any
+ * per-kernel launch, which is what makes small problems fast.  The graph
+ * reads its inputs when it runs: write new fields into the same V buffer to
+ * get new results.  A call with different arguments is captured again (the
+ * executable graph is updated in place when its shape allows).  Results are
+ * bitwise identical to graph mode off.  Host pointer mode, the profiler and
+ * dqmc_greens_ragged always run without a graph.  The stream may be the legacy
+ * default stream. */
+dqmc_status dqmc_set_graph_mode(dqmc_handle h, int enable);
 /* Tile edge of the FP64 slice products: 0 = chosen by size (default), 32 or
  * 64.  A tuning knob for the autotuner (paper_2003_05286_gb300/tune.py). */
 dqmc_status dqmc_set_gemm_tile(dqmc_handle h, int tile);

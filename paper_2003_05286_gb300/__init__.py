@@ -34,7 +34,7 @@ def n_tau(M: int, k: int) -> int:
 class Handle:
     """Owns a dqmc_handle (workspace + settings) bound to the current device."""
 
-    def __init__(self, chain_precision: int = _abi.CHAIN_FP64):
+    def __init__(self, chain_precision: int = _abi.CHAIN_FP64, graphs: bool = False):
         self._lib = lib()
         h = C.c_void_p()
         _abi.check(self._lib.dqmc_create(C.byref(h)), "dqmc_create")
@@ -42,6 +42,12 @@ class Handle:
         if chain_precision != _abi.CHAIN_FP64:
             _abi.check(self._lib.dqmc_set_chain_precision(self.h, chain_precision),
                        "dqmc_set_chain_precision")
+        if graphs:
+            self.set_graph_mode(True)
+
+    def set_graph_mode(self, enable: bool):
+        """Record calls as CUDA graphs and replay them for identical arguments."""
+        _abi.check(self._lib.dqmc_set_graph_mode(self.h, int(enable)), "dqmc_set_graph_mode")
 
     def close(self):
         if getattr(self, "h", None):

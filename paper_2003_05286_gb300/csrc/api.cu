@@ -49,6 +49,16 @@ struct dqmc_handle_s {
   std::vector<cudaEvent_t> pool;
   double prof_ms[PC_N] = {0}, prof_flops[PC_N] = {0};
   long long prof_count[PC_N] = {0};
+  // CUDA-graph mode: the last call is kept as an instantiated graph and
+  // replayed when the next call has identical arguments and settings
+  bool graphs = false;
+  bool capturing = false;
+  size_t ws_need = 0;                      // workspace a capture found missing
+  cudaStream_t gstream = nullptr;          // capture stream (the caller's may be the legacy one)
+  cudaGraphExec_t gexec = nullptr;
+  bool gvalid = false;
+  unsigned long long gkey[24] = {0};
+  long long glaunches = 0;
 };
 
 namespace {
@@ -72,6 +82,11 @@ struct Arena {
 
 dqmc_status ensure_ws(dqmc_handle h, size_t bytes) {
   if (bytes <= h->ws_bytes) return DQMC_OK;
+  if (h->capturing) {   // no allocation inside a capture: the caller grows and captures again
+    h->ws_need = bytes;
+    return DQMC_ERR_NOMEM;
+  }
+  h->gvalid = false;    // a captured graph refers to the old workspace
   if (h->ws) {
     cudaStreamSynchronize(h->stream);
     cudaFree(h->ws);
@@ -620,7 +635,16 @@ dqmc_status dqmc_destroy(dqmc_handle h) {
   for (auto e : h->pool) cudaEventDestroy(e);
   for (auto s : h->aux) { cudaStreamSynchronize(s); cudaStreamDestroy(s); }
   for (auto e : h->auxev) cudaEventDestroy(e);
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->gstream) cudaStreamDestroy(h->gstream);
   delete h;
+  return DQMC_OK;
+}
+
+dqmc_status dqmc_set_graph_mode(dqmc_handle h, int enable) {
+  if (!h) return DQMC_ERR_ARG;
+  h->graphs = enable != 0;
+  h->gvalid = false;
   return DQMC_OK;
 }
 
@@ -691,6 +715,98 @@ const char* dqmc_status_string(dqmc_status s) {
   }
   return "unknown status";
 }
+
+// ---------------------------------------------------------------------------
+// CUDA-graph mode.  The call is recorded by stream capture on an internal
+// stream (forks to the pipelining streams are captured as graph branches),
+// instantiated (or the cached executable updated in place when the topology
+// matches) and launched on the caller's stream.  A call whose arguments and
+// settings equal the previous one's is a bare graph launch: the launch cost of
+// the hundreds of small kernels of a small-N problem is paid once.  Inputs
+// are read when the graph runs, so callers that update V in place get fresh
+// results.  Host pointer mode and the profiler run uncaptured.
+// ---------------------------------------------------------------------------
+extern "C++" {
+struct GraphKey {
+  unsigned long long v[24];
+  int n = 0;
+  void add(unsigned long long x) { if (n < 24) v[n++] = x; }
+  void addp(const void* p) { add((unsigned long long)(uintptr_t)p); }
+  void addd(double d) { unsigned long long x; memcpy(&x, &d, 8); add(x); }
+};
+
+template <class F>
+static dqmc_status graph_call(dqmc_handle h, GraphKey key, F&& body) {
+  if (!h->graphs || h->pmode == DQMC_PTR_HOST || h->prof) return body();
+  key.add((unsigned long long)h->prec);
+  key.add((unsigned long long)h->gemm_tile);
+  key.add((unsigned long long)pipeline_enabled() * 16 + (unsigned long long)pipeline_jobs(h->prec != DQMC_CHAIN_FP64));
+  key.addp(h->ws);
+  key.addp(h->stream);
+  bool same = h->gvalid && h->gexec && key.n <= 24;
+  for (int i = 0; same && i < key.n; ++i) same = h->gkey[i] == key.v[i];
+  if (same) {
+    if (cudaGraphLaunch(h->gexec, h->stream) != cudaSuccess) return DQMC_ERR_CUDA;
+    h->launches = h->glaunches;
+    return DQMC_OK;
+  }
+  if (!h->gstream && cudaStreamCreateWithFlags(&h->gstream, cudaStreamNonBlocking) != cudaSuccess)
+    return DQMC_ERR_CUDA;
+  cudaStream_t caller = h->stream;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    h->stream = h->gstream;
+    if (cudaStreamBeginCapture(h->gstream, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+      h->stream = caller;
+      return DQMC_ERR_CUDA;
+    }
+    h->capturing = true;
+    h->ws_need = 0;
+    dqmc_status rc = body();
+    h->capturing = false;
+    cudaGraph_t g = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(h->gstream, &g);
+    h->stream = caller;
+    h->cur = caller;
+    if (rc == DQMC_ERR_NOMEM && h->ws_need) {   // grow outside the capture, then record again
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      CKS(ensure_ws(h, h->ws_need));
+      key.v[key.n - 2] = (unsigned long long)(uintptr_t)h->ws;
+      continue;
+    }
+    if (rc != DQMC_OK || ce != cudaSuccess || !g) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      h->gvalid = false;
+      return rc != DQMC_OK ? rc : DQMC_ERR_CUDA;
+    }
+    bool ok = false;
+    if (h->gexec) {
+      cudaGraphExecUpdateResultInfo info;
+      ok = cudaGraphExecUpdate(h->gexec, g, &info) == cudaSuccess;
+      if (!ok) {
+        cudaGetLastError();
+        cudaGraphExecDestroy(h->gexec);
+        h->gexec = nullptr;
+      }
+    }
+    if (!ok && cudaGraphInstantiate(&h->gexec, g, 0) != cudaSuccess) {
+      cudaGetLastError();
+      cudaGraphDestroy(g);
+      h->gexec = nullptr;
+      h->gvalid = false;
+      return DQMC_ERR_CUDA;
+    }
+    cudaGraphDestroy(g);
+    for (int i = 0; i < key.n; ++i) h->gkey[i] = key.v[i];
+    h->gvalid = true;
+    h->glaunches = h->launches;
+    if (cudaGraphLaunch(h->gexec, h->stream) != cudaSuccess) return DQMC_ERR_CUDA;
+    return DQMC_OK;
+  }
+  return DQMC_ERR_NOMEM;
+}
+}  // extern "C++"
 
 // ---------------------------------------------------------------------------
 // Equal-time G and log det
@@ -883,15 +999,41 @@ dqmc_status greens_on_workspace(void* stream, void* ws, size_t ws_bytes, int bat
 
 extern "C" {
 
+extern "C++" GraphKey key_of(int fn, int batch, int N, int M, const double* K, double dtau,
+                             const double* V, int k);
+extern "C++" GraphKey key_of(int fn, int batch, int N, int M, const double* K, double dtau,
+                             const double* V, int k) {
+  GraphKey key;
+  key.add((unsigned long long)fn);
+  key.add((unsigned long long)batch);
+  key.add((unsigned long long)N);
+  key.add((unsigned long long)M);
+  key.add((unsigned long long)k);
+  key.addd(dtau);
+  key.addp(K);
+  key.addp(V);
+  return key;
+}
+
 dqmc_status dqmc_greens(dqmc_handle h, int batch, int N, int M, const double* K, double dtau,
                         const double* V, int k, double* G, double* logdet, int* sign,
                         int* status) {
-  return greens_impl(h, batch, N, M, K, dtau, V, k, G, logdet, sign, status);
+  if (!h) return DQMC_ERR_ARG;
+  GraphKey key = key_of(1, batch, N, M, K, dtau, V, k);
+  key.addp(G); key.addp(logdet); key.addp(sign); key.addp(status);
+  return graph_call(h, key, [&] {
+    return greens_impl(h, batch, N, M, K, dtau, V, k, G, logdet, sign, status);
+  });
 }
 
 dqmc_status dqmc_logdet(dqmc_handle h, int batch, int N, int M, const double* K, double dtau,
                         const double* V, int k, double* logdet, int* sign, int* status) {
-  return greens_impl(h, batch, N, M, K, dtau, V, k, nullptr, logdet, sign, status);
+  if (!h) return DQMC_ERR_ARG;
+  GraphKey key = key_of(2, batch, N, M, K, dtau, V, k);
+  key.addp(logdet); key.addp(sign); key.addp(status);
+  return graph_call(h, key, [&] {
+    return greens_impl(h, batch, N, M, K, dtau, V, k, nullptr, logdet, sign, status);
+  });
 }
 
 }  // extern "C"
@@ -1045,7 +1187,22 @@ dqmc_status run_two_stack_inversion(dqmc_handle h, int Q, int N, int nt, const S
 
 extern "C" {
 
+static dqmc_status tdisplaced_impl(dqmc_handle h, int batch, int N, int M, const double* K,
+                                   double dtau, const double* V, int k, double* Gtt, double* Gt0,
+                                   int* status);
+
 dqmc_status dqmc_greens_tdisplaced(dqmc_handle h, int batch, int N, int M, const double* K,
+                                   double dtau, const double* V, int k, double* Gtt, double* Gt0,
+                                   int* status) {
+  if (!h) return DQMC_ERR_ARG;
+  GraphKey key = key_of(3, batch, N, M, K, dtau, V, k);
+  key.addp(Gtt); key.addp(Gt0); key.addp(status);
+  return graph_call(h, key, [&] {
+    return tdisplaced_impl(h, batch, N, M, K, dtau, V, k, Gtt, Gt0, status);
+  });
+}
+
+static dqmc_status tdisplaced_impl(dqmc_handle h, int batch, int N, int M, const double* K,
                                    double dtau, const double* V, int k, double* Gtt, double* Gt0,
                                    int* status) {
   CKS(check_common(h, batch, N, M, K, dtau, V, k));
@@ -1121,9 +1278,24 @@ dqmc_status dqmc_greens_tdisplaced(dqmc_handle h, int batch, int N, int M, const
 // Gradient: checkpoints G(tau_j, tau_j) = G_{jk+1} from the stacks, then
 // G_{l+1} = B_l G_l B_l^{-1} = E (e^{V_l} G_l e^{-V_l}) E^{-1} for the other
 // slices of each chunk; dV_l(i) = 1 - G_l(i,i).  All chunks wrap in parallel.
+static dqmc_status grad_impl(dqmc_handle h, int batch, int N, int M, const double* K,
+                             double dtau, const double* V, int k, double* logdet, int* sign,
+                             double* dV, int* status);
+
 dqmc_status dqmc_logdet_grad(dqmc_handle h, int batch, int N, int M, const double* K, double dtau,
                              const double* V, int k, double* logdet, int* sign, double* dV,
                              int* status) {
+  if (!h) return DQMC_ERR_ARG;
+  GraphKey key = key_of(4, batch, N, M, K, dtau, V, k);
+  key.addp(logdet); key.addp(sign); key.addp(dV); key.addp(status);
+  return graph_call(h, key, [&] {
+    return grad_impl(h, batch, N, M, K, dtau, V, k, logdet, sign, dV, status);
+  });
+}
+
+static dqmc_status grad_impl(dqmc_handle h, int batch, int N, int M, const double* K,
+                             double dtau, const double* V, int k, double* logdet, int* sign,
+                             double* dV, int* status) {
   CKS(check_common(h, batch, N, M, K, dtau, V, k));
   if (h->prec != DQMC_CHAIN_FP64 && N > 256) return DQMC_ERR_UNSUPPORTED;
   h->launches = 0;
