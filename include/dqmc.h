@@ -114,8 +114,9 @@ dqmc_status dqmc_set_chain_precision(dqmc_handle h, dqmc_chain_prec prec);
  * dqmc_greens_ragged always run without a graph.  The stream may be the legacy
  * default stream. */
 dqmc_status dqmc_set_graph_mode(dqmc_handle h, int enable);
-/* Tile edge of the FP64 slice products: 0 = chosen by size (default), 32 or
- * 64.  A tuning knob for the autotuner (paper_2003_05286_gb300/tune.py). */
+/* Tile edge of the FP64 products: 0 = chosen by size (default: the edge that
+ * pads N least), 32, 48 or 64.  A tuning knob for the autotuner
+ * (paper_2003_05286_gb300/tune.py); results do not depend on it. */
 dqmc_status dqmc_set_gemm_tile(dqmc_handle h, int tile);
 /* Number of kernel launches issued by the most recent compute call. */
 long long dqmc_last_launch_count(dqmc_handle h);

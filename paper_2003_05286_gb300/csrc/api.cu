@@ -693,7 +693,7 @@ dqmc_status dqmc_set_chain_precision(dqmc_handle h, dqmc_chain_prec prec) {
 }
 
 dqmc_status dqmc_set_gemm_tile(dqmc_handle h, int tile) {
-  if (!h || (tile != 0 && tile != 32 && tile != 64)) return DQMC_ERR_ARG;
+  if (!h || (tile != 0 && tile != 32 && tile != 48 && tile != 64)) return DQMC_ERR_ARG;
   h->gemm_tile = tile;
   return DQMC_OK;
 }

@@ -4,7 +4,7 @@
 // DFMA, 1.05 TFLOP/s with the f64 mma.sync shapes), so every dense product of
 // the method is bound by the FP64 pipe: shared-memory and L2 traffic are
 // tiny next to it.  The kernel is therefore a plain register-tiled DFMA GEMM
-// whose only job is to keep the FP64 pipe busy: 4x4 outputs per thread,
+// whose only job is to keep the FP64 pipe busy: 4x4 (or 3x3) outputs per thread,
 // double-buffered shared-memory tiles filled from registers one K-block
 // ahead, and every diagonal factor of the method (exp(V_l) of the slice
 // matrix, the D+/D- splits, the column scale of Eq. (stabmult)) applied while
@@ -156,19 +156,38 @@ gemm_f64_kernel(const GemmArgs a) {
   }  // batch loop
 }
 
+// Tile edge for an M x N output: the one that pads the least (every FMA of a
+// padded row or column is wasted FP64-pipe time, e.g. 64-tiles on N = 144 do
+// 1.78x the work, 48-tiles exactly 1x); ties go to 64 for large problems and
+// to 32 (more CTAs) for small ones.  The K order is the same for every tile,
+// so the results do not depend on the choice.
+static int pick_tile(int M, int N) {
+  const int prefs_big[3] = {64, 48, 32}, prefs_small[3] = {32, 48, 64};
+  const int* prefs = (M >= 96 && N >= 96) ? prefs_big : prefs_small;
+  int best = prefs[0];
+  double bw = 0.0;
+  for (int i = 0; i < 3; ++i) {
+    const int t = prefs[i];
+    const double w = (double)((M + t - 1) / t * t) * (double)((N + t - 1) / t * t);
+    if (i == 0 || w < bw) { best = t; bw = w; }
+  }
+  return best;
+}
+
+template <int BM, int BN, int TM, int TN>
+static void launch_gemm(const GemmArgs& a, int zb, cudaStream_t st) {
+  constexpr int BK = 16;
+  dim3 grid((a.N + BN - 1) / BN, (a.M + BM - 1) / BM, zb);
+  gemm_f64_kernel<BM, BN, BK, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, st>>>(a);
+}
+
 cudaError_t gemm_f64(const GemmArgs& a, cudaStream_t st) {
   if (a.batch <= 0 || a.M <= 0 || a.N <= 0) return cudaSuccess;
   const int zb = a.batch < 65535 ? a.batch : 65535;   // grid z limit; the kernel loops
-  const bool big = a.tile ? a.tile == 64 : (a.M >= 96 && a.N >= 96);
-  if (big) {
-    constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4;
-    dim3 grid((a.N + BN - 1) / BN, (a.M + BM - 1) / BM, zb);
-    gemm_f64_kernel<BM, BN, BK, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, st>>>(a);
-  } else {
-    constexpr int BM = 32, BN = 32, BK = 16, TM = 4, TN = 4;
-    dim3 grid((a.N + BN - 1) / BN, (a.M + BM - 1) / BM, zb);
-    gemm_f64_kernel<BM, BN, BK, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, st>>>(a);
-  }
+  const int tile = a.tile ? a.tile : pick_tile(a.M, a.N);
+  if (tile == 64) launch_gemm<64, 64, 4, 4>(a, zb, st);        // 256 threads, 4x4 each
+  else if (tile == 48) launch_gemm<48, 48, 3, 3>(a, zb, st);   // 256 threads, 3x3 each
+  else launch_gemm<32, 32, 4, 4>(a, zb, st);                   // 64 threads, 4x4 each
   return cudaGetLastError();
 }
 

@@ -42,7 +42,7 @@ def _time_ms(fn, reps):
 
 
 def tune(K: torch.Tensor, dtau: float, V: torch.Tensor, *, candidates=(5, 8, 10, 12, 15, 20),
-         tiles=(0, 32, 64), ref_k: int = 2, tol: float = 1e-10, chain_precision: int = 0,
+         tiles=(0, 32, 48, 64), ref_k: int = 2, tol: float = 1e-10, chain_precision: int = 0,
          reps: int = 2, cache_file: str | None = None, tag: str = ""):
     """Pick (k, tile) for fields shaped like V (B, M, N).
 
