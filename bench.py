@@ -77,6 +77,8 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--precision", default="fp64", choices=["fp64"] + [f"bf16x{i}" for i in range(3, 9)],
                    help="chain-product precision of the timed steps (QR and inversions stay FP64)")
+    p.add_argument("--no-unshared", action="store_true",
+                   help="skip the extra un-pipelined step that times the dominant kernel alone")
     p.add_argument("--graphs", default="auto", choices=["auto", "on", "off"],
                    help="CUDA-graph mode of the handle (auto: on for the launch-bound workloads)")
     p.add_argument("--mixed-slices", type=int, default=8,
@@ -330,6 +332,31 @@ def run_gpu(args, wl, rank, world):
     value = job_value(batch, world, args.steps, tot_ms)
     fl = flops_per_greens(N, M, k)
 
+    # ---- the dominant kernel once more, not sharing SMs: one extra step with the
+    # sub-batch pipeline off (after the timed region; reported beside the roofline)
+    unshared = None
+    if not args.no_unshared:
+        prev = os.environ.get("DQMC_PIPELINE")
+        os.environ["DQMC_PIPELINE"] = "0"
+        h.set_graph_mode(False)
+        h.profile(True)
+        h.profile_reset()
+        step()
+        torch.cuda.synchronize()
+        c_ms, c_n, c_fl = h.profile_read(h.PROF_QRP if prec else h.PROF_CHAIN)
+        h.profile(False)
+        h.set_graph_mode(graphs)
+        if prev is None:
+            del os.environ["DQMC_PIPELINE"]
+        else:
+            os.environ["DQMC_PIPELINE"] = prev
+        if c_ms > 0:
+            u_ach = c_fl / (c_ms / 1e3) / 1e12
+            unshared = {"achieved": u_ach, "frac": u_ach / FP64_PEAK_TFLOPS, "launches": c_n,
+                        "avg_launch_ms": c_ms / max(c_n, 1),
+                        "note": "same kernel in one extra step with the sub-batch pipeline off "
+                                "(full batch per launch, no concurrent kernels); not timed"}
+
     # ---- the same step with the chain products on the tensor cores -----------
     mixed = None
     if args.mixed_slices and prec == 0:
@@ -445,6 +472,7 @@ def run_gpu(args, wl, rank, world):
                      "kernel": dom_kernel,
                      "launches": dom_n, "avg_launch_ms": dom_ms / max(dom_n, 1),
                      "stream_time_share": dom_ms / tot_ms if tot_ms > 0 else None,
+                     "unshared": unshared,
                      "peak_source": "derived: 152 SM x 4 FP64 flop/clk x 2070 MHz"},
         "roofline_tensor": roof_tensor,
         "gpu_launches": launches_per_step * args.steps,
