@@ -192,6 +192,26 @@ dqmc_status dqmc_greens_ragged(dqmc_handle h, int batch, const dqmc_instance* de
                                double* G_pool, double* logdet, int* sign,
                                int* status);
 
+/* Ragged time-displaced G: instances of different N, M, k, dtau and K in one
+ * call, pools and descriptors as for dqmc_greens_ragged.  Instance b writes
+ * its n_tau(M_b, k_b) x N_b x N_b values of G(tau_j, tau_j) to Gtt_pool and of
+ * G(tau_j, 0) to Gt0_pool, both at desc[b].off_G (either pool may be NULL).
+ * Instances with equal (N, M, k, dtau, off_K) run as one batch of the uniform
+ * path (dqmc_greens_tdisplaced); the groups run one after another, staged in
+ * a second handle-owned device buffer.  status (may be NULL) is indexed by
+ * instance.  Host pointer mode: DQMC_ERR_UNSUPPORTED. */
+dqmc_status dqmc_greens_tdisplaced_ragged(dqmc_handle h, int batch, const dqmc_instance* desc,
+                                          const double* K_pool, const double* V_pool,
+                                          double* Gtt_pool, double* Gt0_pool, int* status);
+
+/* Ragged log-det gradient: as dqmc_logdet_grad per instance, grouped as in
+ * dqmc_greens_tdisplaced_ragged.  Instance b writes its M_b x N_b gradient
+ * (layout of its V) to dV_pool at desc[b].off_G; logdet, sign and status (each
+ * may be NULL) are indexed by instance. */
+dqmc_status dqmc_logdet_grad_ragged(dqmc_handle h, int batch, const dqmc_instance* desc,
+                                    const double* K_pool, const double* V_pool, double* logdet,
+                                    int* sign, double* dV_pool, int* status);
+
 /* Allocation-free variant of dqmc_greens, for callers that cannot allocate
  * device memory (an application or pool that owns the whole device budget, a
  * plugin that must not go around its host's allocator, a process with a fixed

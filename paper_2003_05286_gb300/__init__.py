@@ -19,7 +19,8 @@ import torch
 from . import _abi
 
 __all__ = ["Handle", "greens", "logdet", "greens_tdisplaced", "logdet_grad", "greens_ragged",
-           "selftest_wait_timeout", "LogDet", "n_tau", "lib"]
+           "greens_tdisplaced_ragged", "logdet_grad_ragged", "selftest_wait_timeout", "LogDet",
+           "n_tau", "lib"]
 
 
 def lib():
@@ -233,6 +234,76 @@ def greens_ragged(instances, *, handle: Handle | None = None, device=None):
         N = descs[i].N
         Gs.append(Gp[descs[i].off_G: descs[i].off_G + N * N].view(N, N))
     return Gs, ld, sg, st
+
+
+def _pack_ragged(instances, device, out_len):
+    """Descriptors and device pools of a ragged call; out_len(N, M, k) is the
+    output block length of one instance."""
+    descs = (_abi.DqmcInstance * len(instances))()
+    offK = offV = offO = 0
+    Ks, Vs = [], []
+    seenK = {}
+    for i, (K, dtau, V, k) in enumerate(instances):
+        N = K.shape[0]
+        M = V.shape[0]
+        key = (K.data_ptr(), tuple(K.shape), tuple(K.stride()))
+        if key not in seenK:
+            seenK[key] = offK
+            Ks.append(K.reshape(-1))
+            offK += N * N
+        descs[i] = _abi.DqmcInstance(N, M, int(k), 0, float(dtau), seenK[key], offV, offO)
+        Vs.append(V.reshape(-1))
+        offV += M * N
+        offO += out_len(N, M, int(k))
+    Kp = torch.cat(Ks).to(device=device, dtype=torch.float64).contiguous()
+    Vp = torch.cat(Vs).to(device=device, dtype=torch.float64).contiguous()
+    return descs, Kp, Vp, offO
+
+
+def greens_tdisplaced_ragged(instances, *, handle: Handle | None = None, device=None,
+                             want_tt: bool = True, want_t0: bool = True):
+    """Ragged G(tau_j, tau_j) and G(tau_j, 0): ``instances`` as for greens_ragged.
+
+    Returns (list of Gtt (n_tau, N, N) or None, list of Gt0 or None, status)."""
+    device = device or instances[0][0].device
+    descs, Kp, Vp, total = _pack_ragged(instances, device, lambda N, M, k: n_tau(M, k) * N * N)
+    Gtt = torch.empty(total, dtype=torch.float64, device=device) if want_tt else None
+    Gt0 = torch.empty(total, dtype=torch.float64, device=device) if want_t0 else None
+    B = len(instances)
+    st = torch.empty(B, dtype=torch.int32, device=device)
+    h = _handle(handle)
+    _abi.check(h._lib.dqmc_greens_tdisplaced_ragged(h.h, B, descs, _ptr(Kp), _ptr(Vp), _ptr(Gtt),
+                                                    _ptr(Gt0), _ptr(st)),
+               "dqmc_greens_tdisplaced_ragged")
+    outs = []
+    for pool in (Gtt, Gt0):
+        if pool is None:
+            outs.append(None)
+            continue
+        lst = []
+        for i in range(B):
+            d = descs[i]
+            nt = n_tau(d.M, d.k)
+            lst.append(pool[d.off_G: d.off_G + nt * d.N * d.N].view(nt, d.N, d.N))
+        outs.append(lst)
+    return outs[0], outs[1], st
+
+
+def logdet_grad_ragged(instances, *, handle: Handle | None = None, device=None):
+    """Ragged log det and gradient: returns (logdet, sign, list of dV (M, N), status)."""
+    device = device or instances[0][0].device
+    descs, Kp, Vp, total = _pack_ragged(instances, device, lambda N, M, k: M * N)
+    dV = torch.empty(total, dtype=torch.float64, device=device)
+    B = len(instances)
+    ld = torch.empty(B, dtype=torch.float64, device=device)
+    sg = torch.empty(B, dtype=torch.int32, device=device)
+    st = torch.empty(B, dtype=torch.int32, device=device)
+    h = _handle(handle)
+    _abi.check(h._lib.dqmc_logdet_grad_ragged(h.h, B, descs, _ptr(Kp), _ptr(Vp), _ptr(ld), _ptr(sg),
+                                              _ptr(dV), _ptr(st)), "dqmc_logdet_grad_ragged")
+    dVs = [dV[descs[i].off_G: descs[i].off_G + descs[i].M * descs[i].N].view(descs[i].M, descs[i].N)
+           for i in range(B)]
+    return ld, sg, dVs, st
 
 
 def selftest_wait_timeout(status: torch.Tensor, stream: torch.cuda.Stream | None = None):

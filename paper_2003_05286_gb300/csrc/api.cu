@@ -59,6 +59,10 @@ struct dqmc_handle_s {
   bool gvalid = false;
   unsigned long long gkey[24] = {0};
   long long glaunches = 0;
+  // staging buffer of the grouped ragged calls (kept apart from ws, which the
+  // uniform path they call may grow)
+  char* rws = nullptr;
+  size_t rws_bytes = 0;
 };
 
 namespace {
@@ -637,6 +641,7 @@ dqmc_status dqmc_destroy(dqmc_handle h) {
   for (auto e : h->auxev) cudaEventDestroy(e);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->gstream) cudaStreamDestroy(h->gstream);
+  if (h->rws) cudaFree(h->rws);
   delete h;
   return DQMC_OK;
 }
@@ -1540,6 +1545,168 @@ dqmc_status dqmc_greens_ragged(dqmc_handle h, int batch, const dqmc_instance* de
   cudaEventDestroy(fork);
   h->cur = h->stream;
   return rc;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Ragged time-displaced G and log-det gradient: instances grouped by
+// (N, M, k, dtau, K); each group is gathered into a contiguous batch, run
+// through the uniform path and scattered back, one group after another on
+// the handle's stream.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct UGroup {
+  int N, M, k;
+  double dtau;
+  long long offK;
+  std::vector<int> idx;
+};
+
+dqmc_status group_uniform(int batch, const dqmc_instance* desc, std::vector<UGroup>& groups) {
+  for (int b = 0; b < batch; ++b) {
+    const dqmc_instance& d = desc[b];
+    if (d.N < 1 || d.N > 1024 || d.M < 1 || d.k < 1 || d.k > d.M || !(d.dtau >= 0.0) ||
+        d.off_K < 0 || d.off_V < 0 || d.off_G < 0)
+      return DQMC_ERR_ARG;
+    UGroup* g = nullptr;
+    for (auto& x : groups)
+      if (x.N == d.N && x.M == d.M && x.k == d.k && x.dtau == d.dtau && x.offK == d.off_K) {
+        g = &x;
+        break;
+      }
+    if (!g) {
+      groups.push_back(UGroup{d.N, d.M, d.k, d.dtau, d.off_K, {}});
+      g = &groups.back();
+    }
+    g->idx.push_back(b);
+  }
+  return DQMC_OK;
+}
+
+dqmc_status ensure_rws(dqmc_handle h, size_t bytes) {
+  if (bytes <= h->rws_bytes) return DQMC_OK;
+  if (h->rws) {
+    cudaStreamSynchronize(h->stream);
+    cudaFree(h->rws);
+    h->rws = nullptr;
+    h->rws_bytes = 0;
+  }
+  if (cudaMalloc(&h->rws, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    h->rws = nullptr;
+    return DQMC_ERR_NOMEM;
+  }
+  h->rws_bytes = bytes;
+  return DQMC_OK;
+}
+
+// Staging of one group: V in, `nout` output blocks of `outlen` doubles per
+// instance, per-instance scalars, index tables.
+struct Stage {
+  double *V, *out[2], *ld;
+  int *sg, *st, *gidx;
+  long long *offV, *offO;
+};
+
+dqmc_status stage_group(dqmc_handle h, const UGroup& g, const dqmc_instance* desc,
+                        const double* V_pool, long long outlen, int nout, Stage& S) {
+  const int nb = (int)g.idx.size();
+  const long long vlen = (long long)g.M * g.N;
+  auto lay = [&](Arena& ar) {
+    S.V = ar.take<double>(vlen * nb);
+    for (int o = 0; o < 2; ++o) S.out[o] = o < nout ? ar.take<double>(outlen * nb) : nullptr;
+    S.ld = ar.take<double>(nb);
+    S.sg = ar.take<int>(nb);
+    S.st = ar.take<int>(nb);
+    S.gidx = ar.take<int>(nb);
+    S.offV = ar.take<long long>(nb);
+    S.offO = ar.take<long long>(nb);
+  };
+  Arena m;
+  lay(m);
+  CKS(ensure_rws(h, m.off));
+  Arena ar;
+  ar.base = h->rws;
+  lay(ar);
+  std::vector<int> gidx(nb);
+  std::vector<long long> offV(nb), offO(nb);
+  for (int j = 0; j < nb; ++j) {
+    gidx[j] = g.idx[j];
+    offV[j] = desc[g.idx[j]].off_V;
+    offO[j] = desc[g.idx[j]].off_G;
+  }
+  cudaStream_t st = h->stream;
+  if (cudaMemcpyAsync(S.gidx, gidx.data(), nb * sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(S.offV, offV.data(), nb * sizeof(long long), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(S.offO, offO.data(), nb * sizeof(long long), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)   // the host tables go out of scope
+    return DQMC_ERR_CUDA;
+  CK(move_blocks(V_pool, S.V, S.offV, vlen, nb, 0, st));
+  return DQMC_OK;
+}
+
+dqmc_status check_ragged(dqmc_handle h, int batch, const dqmc_instance* desc,
+                         const double* K_pool, const double* V_pool) {
+  if (!h || batch < 0) return DQMC_ERR_ARG;
+  if (batch == 0) return DQMC_OK;
+  if (!desc || !K_pool || !V_pool) return DQMC_ERR_ARG;
+  if (h->pmode == DQMC_PTR_HOST) return DQMC_ERR_UNSUPPORTED;
+  return DQMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dqmc_status dqmc_greens_tdisplaced_ragged(dqmc_handle h, int batch, const dqmc_instance* desc,
+                                          const double* K_pool, const double* V_pool,
+                                          double* Gtt_pool, double* Gt0_pool, int* status) {
+  CKS(check_ragged(h, batch, desc, K_pool, V_pool));
+  if (batch == 0) return DQMC_OK;
+  std::vector<UGroup> groups;
+  CKS(group_uniform(batch, desc, groups));
+  long long launches = 0;
+  for (const UGroup& g : groups) {
+    const int nb = (int)g.idx.size();
+    const long long outlen = (long long)(n_chunks(g.M, g.k) + 1) * g.N * g.N;
+    Stage S;
+    CKS(stage_group(h, g, desc, V_pool, outlen, 2, S));
+    CKS(tdisplaced_impl(h, nb, g.N, g.M, K_pool + g.offK, g.dtau, S.V, g.k,
+                        Gtt_pool ? S.out[0] : nullptr, Gt0_pool ? S.out[1] : nullptr, S.st));
+    launches += h->launches;
+    cudaStream_t st = h->stream;
+    if (Gtt_pool) CK(move_blocks(S.out[0], Gtt_pool, S.offO, outlen, nb, 1, st));
+    if (Gt0_pool) CK(move_blocks(S.out[1], Gt0_pool, S.offO, outlen, nb, 1, st));
+    if (status) CK(scatter_scalars(S.gidx, nb, nullptr, nullptr, S.st, nullptr, nullptr, status, st));
+  }
+  h->launches = launches;
+  return DQMC_OK;
+}
+
+dqmc_status dqmc_logdet_grad_ragged(dqmc_handle h, int batch, const dqmc_instance* desc,
+                                    const double* K_pool, const double* V_pool, double* logdet,
+                                    int* sign, double* dV_pool, int* status) {
+  CKS(check_ragged(h, batch, desc, K_pool, V_pool));
+  if (batch == 0) return DQMC_OK;
+  if (!dV_pool) return DQMC_ERR_ARG;
+  std::vector<UGroup> groups;
+  CKS(group_uniform(batch, desc, groups));
+  long long launches = 0;
+  for (const UGroup& g : groups) {
+    const int nb = (int)g.idx.size();
+    const long long outlen = (long long)g.M * g.N;
+    Stage S;
+    CKS(stage_group(h, g, desc, V_pool, outlen, 1, S));
+    CKS(grad_impl(h, nb, g.N, g.M, K_pool + g.offK, g.dtau, S.V, g.k, S.ld, S.sg, S.out[0], S.st));
+    launches += h->launches;
+    cudaStream_t st = h->stream;
+    CK(move_blocks(S.out[0], dV_pool, S.offO, outlen, nb, 1, st));
+    CK(scatter_scalars(S.gidx, nb, S.ld, S.sg, S.st, logdet, sign, status, st));
+  }
+  h->launches = launches;
+  return DQMC_OK;
 }
 
 }  // extern "C"

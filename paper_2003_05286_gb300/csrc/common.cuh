@@ -156,6 +156,10 @@ cudaError_t exp_gather(const double* V, const long long* offV, const int* Mb, in
                        int N, double* out, int* status, cudaStream_t st);
 cudaError_t scatter_mats(const double* src, const long long* offG, int N, int batch, double* dst,
                          cudaStream_t st);
+// Blocks of len doubles between a pool (at offs[b]) and a contiguous batch:
+// gather (scatter = 0) pool -> batch, scatter (1) batch -> pool.
+cudaError_t move_blocks(const double* src, double* dst, const long long* offs, long long len,
+                        int batch, int scatter, cudaStream_t st);
 cudaError_t scatter_scalars(const int* gidx, int batch, const double* ld, const int* sg,
                             const int* stt, double* ld_out, int* sg_out, int* st_out,
                             cudaStream_t st);

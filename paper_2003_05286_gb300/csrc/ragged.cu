@@ -78,4 +78,25 @@ cudaError_t scatter_scalars(const int* gidx, int batch, const double* ld, const 
   return cudaGetLastError();
 }
 
+// Contiguous blocks of len doubles: gather dst[b*len + i] = src[offs[b] + i],
+// scatter dst[offs[b] + i] = src[b*len + i].
+__global__ void move_blocks_kernel(const double* src, double* dst, const long long* offs,
+                                   long long len, int batch, int scatter) {
+  const long long total = len * batch;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long b = e / len, i = e % len;
+    if (scatter) dst[offs[b] + i] = src[e];
+    else dst[e] = src[offs[b] + i];
+  }
+}
+
+cudaError_t move_blocks(const double* src, double* dst, const long long* offs, long long len,
+                        int batch, int scatter, cudaStream_t st) {
+  const long long total = len * batch;
+  if (total <= 0) return cudaSuccess;
+  move_blocks_kernel<<<nblocks(total), TPB, 0, st>>>(src, dst, offs, len, batch, scatter);
+  return cudaGetLastError();
+}
+
 }  // namespace dqmc

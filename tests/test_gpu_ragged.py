@@ -86,3 +86,44 @@ def test_ragged_full_size_sampled(dq):
             assert np.abs(Gs[i].cpu().numpy() - Go).max() <= GTOL * max(1.0, np.abs(Go).max()), (N, i)
             assert abs(float(ld[i]) - ldo) <= 1e-9 * abs(ldo)
             assert int(sg[i]) == so
+
+
+def _mixed_sizes(n, seed):
+    rng = np.random.default_rng(seed)
+    insts = []
+    for i in range(n):
+        L = int(rng.choice([2, 3, 4]))
+        beta = float(rng.choice([1.0, 1.5, 2.0]))
+        insts.append(di.hubbard_instance(L, float(rng.uniform(2, 6)), 0.1, beta, int(rng.choice([5, 10])),
+                                         seed * 100 + i))
+    Ks = {L: _dev(di.square_hopping(L)) for L in (2, 3, 4)}
+    items = [(Ks[int(round(x.N ** 0.5))], x.dtau, _dev(x.V), x.k) for x in insts]
+    return insts, items
+
+
+def test_ragged_tdisplaced(dq):
+    """Groups of equal (N, M, k, K): every instance equals its own uniform call bitwise
+    and matches the oracle."""
+    insts, items = _mixed_sizes(18, 31)
+    Gtt, Gt0, st = dq.greens_tdisplaced_ragged(items)
+    assert int((st != 0).sum()) == 0
+    for i, x in enumerate(insts):
+        a, b, s1 = dq.greens_tdisplaced(_dev(x.K), x.dtau, _dev(x.V), x.k)
+        assert torch.equal(Gtt[i], a) and torch.equal(Gt0[i], b), i
+        if i < 6:
+            Ott, Ot0 = od.greens_tdisplaced(x.K, x.dtau, x.V, x.k)
+            sc = max(1.0, np.abs(Ott).max())
+            assert np.abs(Gtt[i].cpu().numpy() - Ott).max() <= GTOL * sc
+            assert np.abs(Gt0[i].cpu().numpy() - Ot0).max() <= GTOL * max(1.0, np.abs(Ot0).max())
+
+
+def test_ragged_grad(dq):
+    insts, items = _mixed_sizes(14, 47)
+    ld, sg, dVs, st = dq.logdet_grad_ragged(items)
+    assert int((st != 0).sum()) == 0
+    for i, x in enumerate(insts):
+        l1, s1, d1, t1 = dq.logdet_grad(_dev(x.K), x.dtau, _dev(x.V), x.k)
+        assert torch.equal(dVs[i], d1) and float(l1) == float(ld[i]) and int(s1) == int(sg[i]), i
+        if i < 4:
+            dVo = od.logdet_grad(x.K, x.dtau, x.V, x.k)
+            assert np.abs(dVs[i].cpu().numpy() - dVo).max() <= 1e-9
