@@ -189,24 +189,24 @@ class ClockSampler:
                 "samples": len(self.rows)}
 
 
-def kernel_source_hash() -> str:
+def kernel_source_hash(src: str = "gemm_f64.cu") -> str:
     h = hashlib.sha256()
-    for f in ("gemm_f64.cu",):
-        with open(os.path.join(ROOT, "paper_2003_05286_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    with open(os.path.join(ROOT, "paper_2003_05286_gb300", "csrc", src), "rb") as fh:
+        h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def measured_traffic(workload: str):
-    """DRAM bytes per launch of the slice-chain GEMM from the committed ncu summary,
-    or None when the kernel source changed since the capture."""
-    path = os.path.join(ROOT, "profiles", "chain_gemm_traffic.json")
+def measured_traffic(workload: str, record: str = "chain_gemm_traffic.json",
+                     src: str = "gemm_f64.cu"):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary
+    (profiles/<record>), or None when the kernel source changed since the capture."""
+    path = os.path.join(ROOT, "profiles", record)
     if not os.path.exists(path):
         return None
     with open(path) as f:
         d = json.load(f)
     e = d.get(workload)
-    if not e or e.get("kernel_source_sha256_16") != kernel_source_hash():
+    if not e or e.get("kernel_source_sha256_16") != kernel_source_hash(src):
         return None
     return e.get("dram_bytes_per_launch")
 
@@ -442,7 +442,8 @@ def run_gpu(args, wl, rank, world):
         # products on the tensor cores: the FP64 pivoted QR dominates the step
         dom_ms, dom_n, dom_flops = qr_ms, qr_n, qr_flops
         dom_kernel = "qrp_fused_kernel (pivoted QR incl. forming Q, 8N^3/3 x batch flops per launch)"
-        traffic = None
+        traffic = measured_traffic(f"{args.workload}_bf16x{prec}", "qrp_fused_traffic.json",
+                                   "qrp_f64.cu")
     achieved = (dom_flops / (dom_ms / 1e3)) / 1e12 if dom_ms > 0 else None
     roof_tensor = None
     if prec > 0 and chain_ms > 0:
