@@ -24,12 +24,13 @@
 // normwise, not elementwise -- entries much smaller than their column's
 // largest keep correspondingly fewer digits.
 //
-// Per CTA: one 128 x 64 output tile of one instance; 4 warps; warp 0 issues the
+// Per CTA: one 128 x 64 output tile of one instance; 8 warps; warp 0 issues the
 // TMA loads of the s A-slice tiles (128 x 32 BF16) and s B-slice tiles
 // (64 x 32 BF16) of a K-block into one of two shared-memory stages (64-byte
 // swizzle), one thread of warp 1 issues the tcgen05.mma (M=128, N=64, K=16,
-// kind::f16 with BF16 inputs, FP32 accumulators in TMEM), and all four warps
-// read the accumulators back (tcgen05.ld 32x32b) for the epilogue.  Every
+// kind::f16 with BF16 inputs, FP32 accumulators in TMEM), and all eight warps
+// read the accumulators back (tcgen05.ld 32x32b) for the epilogue, which
+// stages the FP64 tile in the idle stage buffers and stores whole rows.  Every
 // mbarrier wait is bounded (~2 s by the global timer); a CTA that gives up
 // records DQMC_STATUS_TIMEOUT in its instance's status word, waits (bounded)
 // for its own copies, frees its TMEM and returns.
@@ -49,6 +50,9 @@ constexpr int OZ_STAGES = 2;
 constexpr int OZ_THREADS = 256;   // 8 warps: two per TMEM lane quarter in the epilogue
 constexpr int OZ_A_TILE = OZ_BM * OZ_BK * 2;   // 8 KB
 constexpr int OZ_B_TILE = OZ_BN * OZ_BK * 2;   // 4 KB
+// FP64 result tile staged in shared memory for coalesced row stores (padded rows)
+constexpr int OZ_C_LD = OZ_BN + 1;
+constexpr int OZ_C_TILE = OZ_BM * OZ_C_LD * 8;   // 66.5 KB
 constexpr unsigned long long OZ_WAIT_NS = 2000000000ull;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -91,15 +95,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     if (mbar_try_wait(bar, parity)) return true;
     if (globaltimer() - t0 > OZ_WAIT_NS) return false;
   }
-}
-
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar,
-                                            int c0, int c1, int c2) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
-      : "memory");
 }
 
 __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar,
@@ -159,67 +154,44 @@ __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-      "%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
 // S * 2^e for a signed 128-bit S, rounded to nearest even, by integer
 // operations only (leading-zero count, shift, exponent assembly); results
 // outside the normal range take the library conversion.
-__device__ __forceinline__ double i128_times_pow2(__int128 S, int e) {
-  if (S == 0) return 0.0;
-  const unsigned long long sign = S < 0 ? (1ull << 63) : 0ull;
-  const unsigned __int128 m = S < 0 ? (unsigned __int128)(-S) : (unsigned __int128)S;
-  const unsigned long long hi = (unsigned long long)(m >> 64), lo = (unsigned long long)m;
-  const int nb = hi ? 128 - __clzll((long long)hi) : 64 - __clzll((long long)lo);
+// (T 2^32 + r) 2^e correctly rounded to FP64, for |T| < 2^45 and 0 <= r < 2^32
+// (the exact sum of the weight groups), with 64-bit integer operations only:
+// the magnitude is split into (Ta, ra) the same way, the 53-bit mantissa taken
+// from Ta and the top bits of ra, and the discarded bits of ra decide the
+// round-to-nearest-even step.
+__device__ __forceinline__ double split_times_pow2(long long T, unsigned int r, int e) {
+  if (T == 0 && r == 0) return 0.0;
+  const bool neg = T < 0;
+  unsigned long long Ta;
+  unsigned int ra;
+  if (!neg) { Ta = (unsigned long long)T; ra = r; }
+  else if (r) { Ta = (unsigned long long)(-(T + 1)); ra = (unsigned int)(0x100000000ull - r); }
+  else { Ta = (unsigned long long)(-T); ra = 0u; }
   unsigned long long mant;
-  int ex = nb - 1 + e;
-  if (nb <= 53) {
-    mant = lo << (53 - nb);
-  } else {
+  int ex;
+  if (Ta < (1ull << 21)) {   // below 2^53: exact
+    const unsigned long long A = (Ta << 32) | ra;
+    const int nb = 64 - __clzll((long long)A);
+    mant = A << (53 - nb);
+    ex = nb - 1 + e;
+  } else {                   // 54..77 bits: drop sh = 1..24 bits of ra
+    const int nb = 96 - __clzll((long long)Ta);
     const int sh = nb - 53;
-    const unsigned __int128 rem = m & (((unsigned __int128)1 << sh) - 1);
-    const unsigned __int128 half = (unsigned __int128)1 << (sh - 1);
-    mant = (unsigned long long)(m >> sh);
+    mant = (Ta << (32 - sh)) | (ra >> sh);
+    const unsigned int rem = ra & ((1u << sh) - 1u), half = 1u << (sh - 1);
+    ex = nb - 1 + e;
     if (rem > half || (rem == half && (mant & 1ull))) {
       if (++mant == (1ull << 53)) { mant >>= 1; ++ex; }
     }
   }
   const int be = ex + 1023;
-  if (be <= 0 || be >= 2047) {
-    return ldexp(ldexp((double)(long long)(m >> 64), 64) + (double)lo, e) * (sign ? -1.0 : 1.0);
-  }
-  return __longlong_as_double((long long)(sign | ((unsigned long long)be << 52) |
-                                          (mant & 0xFFFFFFFFFFFFFull)));
-}
-
-__device__ __forceinline__ double i64_times_pow2(long long S, int e) {
-  if (S == 0) return 0.0;
-  const unsigned long long sign = S < 0 ? (1ull << 63) : 0ull;
-  const unsigned long long m = S < 0 ? (unsigned long long)(-S) : (unsigned long long)S;
-  const int nb = 64 - __clzll((long long)m);           // significant bits of |S|
-  unsigned long long mant;
-  int ex = nb - 1 + e;                                  // |S| 2^e = 1.f x 2^ex
-  if (nb <= 53) {
-    mant = m << (53 - nb);
-  } else {
-    const int sh = nb - 53;
-    const unsigned long long rem = m & ((1ull << sh) - 1), half = 1ull << (sh - 1);
-    mant = m >> sh;
-    if (rem > half || (rem == half && (mant & 1ull))) {
-      if (++mant == (1ull << 53)) { mant >>= 1; ++ex; }
-    }
-  }
-  const int be = ex + 1023;
-  if (be <= 0 || be >= 2047) return ldexp((double)S, e);
-  return __longlong_as_double((long long)(sign | ((unsigned long long)be << 52) |
+  if (be <= 0 || be >= 2047)   // result outside the normal range: scale in FP64
+    return ldexp((double)Ta * 4294967296.0 + (double)ra, e) * (neg ? -1.0 : 1.0);
+  return __longlong_as_double((long long)((neg ? (1ull << 63) : 0ull) |
+                                          ((unsigned long long)be << 52) |
                                           (mant & 0xFFFFFFFFFFFFFull)));
 }
 
@@ -246,7 +218,8 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   const int s = pr.s;
   const int stage_bytes = s * (OZ_A_TILE + OZ_B_TILE);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(base + OZ_STAGES * stage_bytes);
+  const int data_bytes = OZ_STAGES * stage_bytes > OZ_C_TILE ? OZ_STAGES * stage_bytes : OZ_C_TILE;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + data_bytes);
   uint64_t* full = bars;                    // [OZ_STAGES]
   uint64_t* empty = bars + OZ_STAGES;       // [OZ_STAGES]
   uint64_t* done = bars + 2 * OZ_STAGES;    // [1]
@@ -306,14 +279,18 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t sa = smem_u32(base + st * stage_bytes);
-      const uint32_t sbB = sa + s * OZ_A_TILE;
+      // descriptors: the stage's base descriptor plus tile offsets in its
+      // start-address field (address >> 4; shared addresses stay below 256 KB,
+      // so the field never carries)
+      const uint64_t dA = smem_desc_sw64(smem_u32(base + st * stage_bytes));
+      const uint64_t dB = dA + (uint64_t)((s * OZ_A_TILE) >> 4);
       for (int kk = 0; kk < OZ_BK / 16; ++kk) {
+        const uint64_t dAk = dA + (uint64_t)(kk * 2), dBk = dB + (uint64_t)(kk * 2);
+        const bool first_k = kb == 0 && kk == 0;
         for (int i = 0; i < pr.n; ++i) {
-          const uint64_t ad = smem_desc_sw64(sa + pr.p[i] * OZ_A_TILE + kk * 32);
-          const uint64_t bd = smem_desc_sw64(sbB + pr.q[i] * OZ_B_TILE + kk * 32);
-          const uint32_t acc = (kb == 0 && kk == 0 && pr.first[i]) ? 0u : 1u;
-          umma(tmem + pr.g[i] * OZ_BN, ad, bd, idesc, acc);
+          const uint64_t ad = dAk + (uint64_t)(pr.p[i] * (OZ_A_TILE >> 4));
+          const uint64_t bd = dBk + (uint64_t)(pr.q[i] * (OZ_B_TILE >> 4));
+          umma(tmem + pr.g[i] * OZ_BN, ad, bd, idesc, (first_k && pr.first[i]) ? 0u : 1u);
         }
       }
       umma_commit(&empty[st]);   // frees the stage once these MMAs have read it
@@ -333,6 +310,7 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
   const int* eBb = eB + (long long)b * seB;
   double* Cb = C + (long long)b * sC;
   const int shift0 = 7 * (s + 1);
+  double* ctile = reinterpret_cast<double*>(base);   // OZ_BM x OZ_C_LD
   if (ok) {
     const uint32_t lane_addr = (uint32_t)((warp & 3) * 32) << 16;
     for (int c0 = cbase; c0 < cbase + 32; c0 += 8) {
@@ -356,16 +334,24 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
           if (sh >= 32) hi[j] += v << (sh - 32); else lo[j] += v << sh;
         }
       }
-      if (row < N) {
+      // S = hi 2^32 + lo = T 2^32 + r with 0 <= r < 2^32; results go to the
+      // padded tile in the (now idle) stage buffers
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int col = n0 + c0 + j;
-          if (col < N) {
-            const __int128 S = ((__int128)hi[j] << 32) + (__int128)lo[j];
-            Cb[(long long)row * N + col] = i128_times_pow2(S, ea + eBb[col] - shift0);
-          }
-        }
+      for (int j = 0; j < 8; ++j) {
+        const int col = n0 + c0 + j;
+        double v = 0.0;
+        if (row < N && col < N)
+          v = split_times_pow2(hi[j] + (lo[j] >> 32), (unsigned int)(lo[j] & 0xFFFFFFFFll),
+                               ea + eBb[col] - shift0);
+        ctile[((warp & 3) * 32 + lane) * OZ_C_LD + c0 + j] = v;
       }
+    }
+  }
+  if (ok) {
+    __syncthreads();
+    for (int e = tid; e < OZ_BM * OZ_BN; e += OZ_THREADS) {   // rows of 64 doubles
+      const int r = e / OZ_BN, c = e % OZ_BN;
+      if (m0 + r < N && n0 + c < N) Cb[(long long)(m0 + r) * N + n0 + c] = ctile[r * OZ_C_LD + c];
     }
   } else if (tid == 0 && status) {
     atomicOr(&status[b], DQMC_STATUS_TIMEOUT);
@@ -513,7 +499,8 @@ OzPairs oz_pairs(int s, int N) {
 int oz_groups(int s, int N) { return oz_pairs(s, N).ngroups; }
 
 size_t oz_gemm_smem(int s) {
-  return (size_t)OZ_STAGES * s * (OZ_A_TILE + OZ_B_TILE) + 1024 + 256;
+  const size_t stages = (size_t)OZ_STAGES * s * (OZ_A_TILE + OZ_B_TILE);
+  return (stages > (size_t)OZ_C_TILE ? stages : (size_t)OZ_C_TILE) + 1024 + 256;
 }
 
 cudaError_t ozaki_split(const double* X, long long ldm, long long ldj, long long sX,
