@@ -261,10 +261,10 @@ inline int pad_to(int n, int m) { return (n + m - 1) / m * m; }
 // into a chain workspace's shared A-operand buffers.
 cudaError_t split_E(const double* E, int N, int transposeE, const ChainWs& w, cudaStream_t st) {
   // row i of the A operand is a "column" of the splitter: element (m, i)
-  return transposeE ? ozaki_split(E, N, 1, 0, nullptr, 0, N, w.oz_P128, w.oz_PK, w.oz_s, w.ozA, 0,
-                                  w.ozeA, 0, 1, st)
-                    : ozaki_split(E, 1, N, 0, nullptr, 0, N, w.oz_P128, w.oz_PK, w.oz_s, w.ozA, 0,
-                                  w.ozeA, 0, 1, st);
+  return transposeE ? ozaki_split(E, N, 1, 0, nullptr, 0, N, w.oz_P128, w.oz_PK, 128, w.oz_s,
+                                  w.ozA, 0, w.ozeA, 0, 1, st)
+                    : ozaki_split(E, 1, N, 0, nullptr, 0, N, w.oz_P128, w.oz_PK, 128, w.oz_s,
+                                  w.ozA, 0, w.ozeA, 0, 1, st);
 }
 
 // Mixed-precision buffers of a chain over `batch` instances with s slices.
@@ -319,7 +319,7 @@ dqmc_status chunk_products(dqmc_handle h, int dir, int batch, int N, int M, int 
       const double* sc = nullptr;
       if (dir > 0) sc = expV + (long long)(l - 1) * N;
       else if (i > 0) sc = expV + (long long)l * N;       // e^{V_{l+1}}
-      CK(ozaki_split(prev, N, 1, sprev, sc, sV, N, PK, PK, sl, w.ozB, (long long)sl * PK * PK,
+      CK(ozaki_split(prev, N, 1, sprev, sc, sV, N, PK, PK, 64, sl, w.ozB, (long long)sl * PK * PK,
                      w.ozeB, PK, batch, st));
       CKP(PC_CHAIN, 2.0 * N * N * (double)N * batch,
           ozaki_gemm(w.ozA, w.ozeA, 0, 0, w.oz_P128, w.ozB, w.ozeB, PK, PK, PK, sl, N, batch,
@@ -387,9 +387,9 @@ dqmc_status chunk_xupdate(dqmc_handle h, int dir, int batch, int N, int k, int c
     // tensor cores: slices of T' (A operand, per instance; row i of T' is a
     // "column" of the splitter) and of the rows of X_src gathered by perm
     const int P1 = w.oz_P128, PK = w.oz_PK, sl = w.oz_s;
-    CK(ozaki_split(w.T, 1, N, NN, nullptr, 0, N, P1, PK, sl, w.ozT, (long long)sl * P1 * PK,
+    CK(ozaki_split(w.T, 1, N, NN, nullptr, 0, N, P1, PK, 128, sl, w.ozT, (long long)sl * P1 * PK,
                    w.ozeT, P1, batch, st));
-    CK(ozaki_split(slotX(s, src), N, 1, s.instX, nullptr, 0, N, PK, PK, sl, w.ozB,
+    CK(ozaki_split(slotX(s, src), N, 1, s.instX, nullptr, 0, N, PK, PK, 64, sl, w.ozB,
                    (long long)sl * PK * PK, w.ozeB, PK, batch, st, w.perm, N));
     CKP(PC_XUPD, (double)N * N * (double)N * batch,
         ozaki_gemm(w.ozT, w.ozeT, (long long)sl * P1 * PK, P1, P1, w.ozB, w.ozeB, PK, PK, PK, sl,

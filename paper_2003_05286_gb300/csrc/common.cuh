@@ -179,7 +179,7 @@ dqmc_status greens_on_workspace(void* stream, void* ws, size_t ws_bytes, int bat
 namespace dqmc {
 // Error-free BF16 slicing and tensor-core slice products (ozaki_tc.cu).
 cudaError_t ozaki_split(const double* X, long long ldm, long long ldj, long long sX,
-                        const double* sc, long long ssc, int N, int PJ, int PM, int s,
+                        const double* sc, long long ssc, int N, int PJ, int PM, int R, int s,
                         __nv_bfloat16* S, long long sS, int* e, long long se, int batch,
                         cudaStream_t st, const int* gm = nullptr, long long sgm = 0);
 cudaError_t ozaki_gemm(const __nv_bfloat16* As, const int* eA, long long sA, long long seA,

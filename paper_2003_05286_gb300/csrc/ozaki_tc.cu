@@ -24,17 +24,20 @@
 // normwise, not elementwise -- entries much smaller than their column's
 // largest keep correspondingly fewer digits.
 //
+// Digit planes are stored as contiguous tiles (128 x 32 BF16 for the A
+// operand, 64 x 32 for B), each already in the 64-byte-swizzled byte order the
+// tensor core reads from shared memory, so that one bulk copy moves a tile:
+// tensor-map loads of 64-byte-wide boxes cost one request per 64-byte row.
+//
 // Per CTA: one 128 x 64 output tile of one instance; 8 warps; warp 0 issues the
-// TMA loads of the s A-slice tiles (128 x 32 BF16) and s B-slice tiles
-// (64 x 32 BF16) of a K-block into one of two shared-memory stages (64-byte
-// swizzle), one thread of warp 1 issues the tcgen05.mma (M=128, N=64, K=16,
+// bulk copies of the s A-slice tiles and s B-slice tiles of a K-block into one
+// of two shared-memory stages, one thread of warp 1 issues the tcgen05.mma (M=128, N=64, K=16,
 // kind::f16 with BF16 inputs, FP32 accumulators in TMEM), and all eight warps
 // read the accumulators back (tcgen05.ld 32x32b) for the epilogue, which
 // stages the FP64 tile in the idle stage buffers and stores whole rows.  Every
 // mbarrier wait is bounded (~2 s by the global timer); a CTA that gives up
 // records DQMC_STATUS_TIMEOUT in its instance's status word, waits (bounded)
 // for its own copies, frees its TMEM and returns.
-#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include "common.cuh"
@@ -97,13 +100,13 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   }
 }
 
-__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar,
-                                            int c0, int c1, int c2, int c3) {
+// One contiguous global -> shared copy, completion counted in bytes on bar.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes,
+                                          uint64_t* bar) {
   asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2),
-      "r"(c3)
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
 
@@ -121,8 +124,10 @@ __device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t saddr) {
 
 // Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both
 // K-major, N = 64, M = 128.
-__host__ __device__ constexpr uint32_t oz_idesc() {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BN >> 3) << 17) |
+// kind::f16 instruction descriptor: BF16 A and B, FP32 accumulator, K-major
+// operands, M = OZ_BM, N = n columns (a multiple of 16, at most 256)
+__host__ __device__ constexpr uint32_t oz_idesc(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
          ((uint32_t)(OZ_BM >> 4) << 24);
 }
 
@@ -208,10 +213,11 @@ struct OzPairs {
 };
 
 __global__ void __launch_bounds__(OZ_THREADS, 1)
-ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                  const OzPairs pr, int N, int nkb, const int* __restrict__ eA, long long seA,
-                  int a_batched, const int* __restrict__ eB, long long seB,
-                  double* __restrict__ C, long long sC, int* status) {
+ozaki_gemm_kernel(const __nv_bfloat16* __restrict__ As, long long sA, int P128,
+                  const __nv_bfloat16* __restrict__ Bs, int PN, const OzPairs pr, int N, int nkb,
+                  const int* __restrict__ eA, long long seA, int a_batched,
+                  const int* __restrict__ eB, long long seB, double* __restrict__ C,
+                  long long sC, int* status) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte aligned stage buffers
   unsigned char* base = reinterpret_cast<unsigned char*>(
@@ -254,7 +260,7 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
   const uint32_t tmem = *tmem_holder;
 
   if (warp == 0 && lane == 0) {
-    // ---- producer: TMA loads of the slice tiles of each K-block -----------
+    // ---- producer: bulk copies of the slice tiles of each K-block ---------
     for (int kb = 0; kb < (pr.stall ? 0 : nkb); ++kb) {
       const int st = kb % OZ_STAGES;
       if (kb >= OZ_STAGES && !mbar_wait(&empty[st], ((kb / OZ_STAGES) - 1) & 1)) {
@@ -264,14 +270,28 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
       if (*(volatile int*)s_fail) break;
       unsigned char* sb = base + st * stage_bytes;
       mbar_arrive_expect_tx(&full[st], (uint32_t)stage_bytes);
+      // tile (row block, K-block kb) of every digit plane: one contiguous copy each
+      const long long PK = (long long)nkb * OZ_BK;
+      const __nv_bfloat16* a0 = As + (long long)bA * sA +
+                                ((long long)(m0 / OZ_BM) * nkb + kb) * (OZ_BM * OZ_BK);
+      const __nv_bfloat16* b0 = Bs + (long long)b * s * PN * PK +
+                                ((long long)(n0 / OZ_BN) * nkb + kb) * (OZ_BN * OZ_BK);
       for (int p = 0; p < s; ++p)
-        tma_load_4d(sb + p * OZ_A_TILE, &tmA, &full[st], kb * OZ_BK, m0, p, bA);
+        bulk_load(sb + p * OZ_A_TILE, a0 + (long long)p * P128 * PK, OZ_A_TILE, &full[st]);
       for (int q = 0; q < s; ++q)
-        tma_load_4d(sb + s * OZ_A_TILE + q * OZ_B_TILE, &tmB, &full[st], kb * OZ_BK, n0, q, b);
+        bulk_load(sb + s * OZ_A_TILE + q * OZ_B_TILE, b0 + (long long)q * PN * PK, OZ_B_TILE,
+                  &full[st]);
     }
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer ---------------------------------------------------------
-    const uint32_t idesc = oz_idesc();
+    // The pairs (p, q) of one A digit p go to the consecutive weight groups
+    // g = p + q (q = 0 .. s-1-p), whose accumulators are adjacent OZ_BN-column
+    // blocks of TMEM, and their B digit tiles are adjacent in the stage: one
+    // MMA with N = n OZ_BN (n <= 4) covers n pairs and reads the A tile once
+    // instead of n times (the operand reads from shared memory, not the
+    // arithmetic, bound the product).
+    const uint32_t idesc1 = oz_idesc(OZ_BN), idesc2 = oz_idesc(2 * OZ_BN),
+                   idesc3 = oz_idesc(3 * OZ_BN), idesc4 = oz_idesc(4 * OZ_BN);
     for (int kb = 0; kb < nkb; ++kb) {
       const int st = kb % OZ_STAGES;
       if (!mbar_wait(&full[st], (kb / OZ_STAGES) & 1)) {
@@ -287,10 +307,16 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
       for (int kk = 0; kk < OZ_BK / 16; ++kk) {
         const uint64_t dAk = dA + (uint64_t)(kk * 2), dBk = dB + (uint64_t)(kk * 2);
         const bool first_k = kb == 0 && kk == 0;
-        for (int i = 0; i < pr.n; ++i) {
-          const uint64_t ad = dAk + (uint64_t)(pr.p[i] * (OZ_A_TILE >> 4));
-          const uint64_t bd = dBk + (uint64_t)(pr.q[i] * (OZ_B_TILE >> 4));
-          umma(tmem + pr.g[i] * OZ_BN, ad, bd, idesc, (first_k && pr.first[i]) ? 0u : 1u);
+        for (int pd = 0; pd < s; ++pd) {
+          const uint64_t ad = dAk + (uint64_t)(pd * (OZ_A_TILE >> 4));
+          // p = 0 reaches every group first: it starts the accumulation
+          const uint32_t acc = (first_k && pd == 0) ? 0u : 1u;
+          for (int q0 = 0; q0 < s - pd; q0 += 4) {
+            const int n = (s - pd - q0) < 4 ? (s - pd - q0) : 4;
+            const uint32_t idesc = n == 4 ? idesc4 : (n == 3 ? idesc3 : (n == 2 ? idesc2 : idesc1));
+            umma(tmem + (uint32_t)(pd + q0) * OZ_BN, ad,
+                 dBk + (uint64_t)(q0 * (OZ_B_TILE >> 4)), idesc, acc);
+          }
         }
       }
       umma_commit(&empty[st]);   // frees the stage once these MMAs have read it
@@ -372,13 +398,16 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
 // ---------------------------------------------------------------------------
 // Splitting kernel: X (FP64, element (m, j) at X[g(m)*ldm + j*ldj], g the
 // optional row gather gm, identity if null) times an optional scale sc[m]
-// -> s BF16 slice planes S[q][j][m] (K-major, PJ x PM per
-// plane, zero padded) and column exponents e[j] with max_m |x_mj| < 2^{e_j}.
+// -> s BF16 slice planes of PJ x PM (zero padded), each stored as tiles of R
+// rows j by 32 consecutive m (tile (j / R, m / 32) at ((j / R)(PM / 32) +
+// m / 32) R 32 elements; inside, row r's 16-byte chunk c at chunk c ^ ((r >> 1)
+// & 3): the 64-byte swizzle), and column exponents e[j] with
+// max_m |x_mj| < 2^{e_j}.
 // One CTA per 32 columns j of one instance; 256 threads.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
 ozaki_split_kernel(const double* __restrict__ X, long long ldm, long long ldj, long long sX,
-                   const double* __restrict__ sc, long long ssc, int N, int PJ, int PM, int s,
+                   const double* __restrict__ sc, long long ssc, int N, int PJ, int PM, int R, int s,
                    __nv_bfloat16* __restrict__ S, long long sS, int* __restrict__ e,
                    long long se, const int* __restrict__ gm, long long sgm) {
   extern __shared__ double tile[];   // [PM][33]
@@ -432,11 +461,17 @@ ozaki_split_kernel(const double* __restrict__ X, long long ldm, long long ldj, l
         F = sh >= 0 ? (m53 << sh) : (sh > -64 ? (m53 >> (-sh)) : 0ull);
       }
       long long S = bits < 0 ? -(long long)F : (long long)F;
+      // element (row jc, k = m) of the R x 32 tile (row block jc / R, K-block
+      // m / 32), rows of 64 bytes whose 16-byte chunks are permuted as the
+      // tensor core's 64-byte swizzle expects them in shared memory
+      const int jr = jc % R, mk = m & 31, ch = mk >> 3;
+      const long long tile_off = ((long long)(jc / R) * (PM / 32) + (m >> 5)) * (R * 32) +
+                                 jr * 32 + ((ch ^ ((jr >> 1) & 3)) << 3) + (mk & 7);
       for (int q = 0; q < s; ++q) {
         const int sh = 56 - 7 * q;                      // digit weight 2^{-7(q+1)}
         const long long d = (S + (1ll << (sh - 1))) >> sh;   // nearest, in [-64, 64]
         S -= d << sh;
-        Sb[q * plane + (long long)jc * PM + m] = __int2bfloat16_rn((int)d);
+        Sb[q * plane + tile_off] = __int2bfloat16_rn((int)d);
       }
     }
   }
@@ -445,26 +480,6 @@ ozaki_split_kernel(const double* __restrict__ X, long long ldm, long long ldj, l
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
-                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
-                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-static EncodeTiledFn encode_fn() {
-  static EncodeTiledFn fn = nullptr;
-  if (!fn) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                         &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess) {
-      cudaGetLastError();
-      return nullptr;
-    }
-    fn = reinterpret_cast<EncodeTiledFn>(p);
-  }
-  return fn;
-}
 
 OzPairs oz_pairs(int s, int N) {
   OzPairs pr{};
@@ -504,63 +519,44 @@ size_t oz_gemm_smem(int s) {
 }
 
 cudaError_t ozaki_split(const double* X, long long ldm, long long ldj, long long sX,
-                        const double* sc, long long ssc, int N, int PJ, int PM, int s,
+                        const double* sc, long long ssc, int N, int PJ, int PM, int R, int s,
                         __nv_bfloat16* S, long long sS, int* e, long long se, int batch,
                         cudaStream_t st, const int* gm, long long sgm) {
+  if (R < 8 || PJ % R || PM % 32) return cudaErrorInvalidValue;
   size_t sm = (size_t)PM * 33 * sizeof(double);
   cudaFuncSetAttribute(ozaki_split_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   dim3 grid((PJ + 31) / 32, batch);
-  ozaki_split_kernel<<<grid, 256, sm, st>>>(X, ldm, ldj, sX, sc, ssc, N, PJ, PM, s, S, sS, e, se,
-                                            gm, sgm);
+  ozaki_split_kernel<<<grid, 256, sm, st>>>(X, ldm, ldj, sX, sc, ssc, N, PJ, PM, R, s, S, sS, e,
+                                            se, gm, sgm);
   return cudaGetLastError();
 }
 
 // C_b = 2^{eA_b} As_b * (2^{eB_b} Bs_b)  for b < batch.  As: s planes of
-// P128 x PK (rows i, K contiguous) per instance (sA elements apart, eA_b =
-// eA + b seA) or shared by all instances (sA = 0); Bs: per instance s planes of
-// PN x PK (columns j, K contiguous); PK, PN multiples of 64, P128 a multiple of 128.
+// P128 x PK (rows i) in 128-row tiles (ozaki_split with R = 128) per instance
+// (sA elements apart, eA_b = eA + b seA) or shared by all instances (sA = 0);
+// Bs: per instance s planes of PN x PK (columns j) in 64-row tiles (R = 64);
+// PK, PN multiples of 64, P128 a multiple of 128.
 static cudaError_t ozaki_gemm_impl(const __nv_bfloat16* As, const int* eA, long long sA,
                                    long long seA, int P128, const __nv_bfloat16* Bs, const int* eB,
                                    long long seB, int PN, int PK, int s, int N, int batch,
                                    double* C, long long sC, int* status, cudaStream_t st,
                                    int stall) {
-  EncodeTiledFn enc = encode_fn();
-  if (!enc) return cudaErrorNotSupported;
   if (sA != 0 && sA < (long long)s * P128 * PK) return cudaErrorInvalidValue;
-  CUtensorMap tA, tB;
-  {
-    const int nA = sA ? batch : 1;
-    const long long strideA = sA ? sA : (long long)s * P128 * PK;
-    cuuint64_t dims[4] = {(cuuint64_t)PK, (cuuint64_t)P128, (cuuint64_t)s, (cuuint64_t)nA};
-    cuuint64_t strides[3] = {(cuuint64_t)PK * 2, (cuuint64_t)PK * P128 * 2,
-                             (cuuint64_t)strideA * 2};
-    cuuint32_t box[4] = {OZ_BK, OZ_BM, 1, 1};
-    cuuint32_t es[4] = {1, 1, 1, 1};
-    if (enc(&tA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)As, dims, strides, box, es,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
-            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-      return cudaErrorInvalidValue;
-  }
-  {
-    cuuint64_t dims[4] = {(cuuint64_t)PK, (cuuint64_t)PN, (cuuint64_t)s, (cuuint64_t)batch};
-    cuuint64_t strides[3] = {(cuuint64_t)PK * 2, (cuuint64_t)PK * PN * 2,
-                             (cuuint64_t)PK * PN * s * 2};
-    cuuint32_t box[4] = {OZ_BK, OZ_BN, 1, 1};
-    cuuint32_t es[4] = {1, 1, 1, 1};
-    if (enc(&tB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)Bs, dims, strides, box, es,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
-            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-      return cudaErrorInvalidValue;
-  }
+  if (P128 % OZ_BM || PN % OZ_BN || PK % OZ_BK || PK < OZ_BK) return cudaErrorInvalidValue;
   if (s < 1 || s > 8) return cudaErrorInvalidValue;
   OzPairs pr = oz_pairs(s, N);
   if (pr.ngroups > 8 || pr.n > 40) return cudaErrorNotSupported;
+  // the kernel issues the pairs of one A digit as one wide MMA: it needs one
+  // group per weight (g = p + q), which holds for N <= 256
+  if (pr.ngroups != s) return cudaErrorNotSupported;
+  for (int i = 0; i < pr.n; ++i)
+    if (pr.g[i] != pr.p[i] + pr.q[i]) return cudaErrorNotSupported;
   pr.stall = stall;
   size_t sm = oz_gemm_smem(s);
   cudaFuncSetAttribute(ozaki_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   dim3 grid((N + OZ_BN - 1) / OZ_BN, (N + OZ_BM - 1) / OZ_BM, batch);
-  ozaki_gemm_kernel<<<grid, OZ_THREADS, sm, st>>>(tA, tB, pr, N, PK / OZ_BK, eA, seA, sA != 0, eB,
-                                                  seB, C, sC, status);
+  ozaki_gemm_kernel<<<grid, OZ_THREADS, sm, st>>>(As, sA, P128, Bs, PN, pr, N, PK / OZ_BK, eA, seA,
+                                                  sA != 0, eB, seB, C, sC, status);
   return cudaGetLastError();
 }
 
