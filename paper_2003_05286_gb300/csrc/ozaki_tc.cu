@@ -26,8 +26,8 @@
 //
 // Digit planes are stored as contiguous tiles (128 x 32 BF16 for the A
 // operand, 64 x 32 for B), each already in the 64-byte-swizzled byte order the
-// tensor core reads from shared memory, so that one bulk copy moves a tile:
-// tensor-map loads of 64-byte-wide boxes cost one request per 64-byte row.
+// tensor core reads from shared memory, so that one plain bulk copy
+// (cp.async.bulk) moves a tile and no tensor map is needed.
 //
 // Per CTA: one 128 x 64 output tile of one instance; 8 warps; warp 0 issues the
 // bulk copies of the s A-slice tiles and s B-slice tiles of a K-block into one
