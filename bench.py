@@ -64,6 +64,16 @@ WORKLOADS = {
 }
 
 
+# metric and unit of each workload, the same in the GPU arm and the oracle arm
+METRICS = {
+    "n256_beta20": ("greens_functions_per_second", "G/s"),
+    "tdisplaced_n64": ("tdisplaced_sets_per_second", "sets/s"),
+    "grad_n144": ("logdet_gradients_per_second", "grads/s"),
+    "ragged_1024": ("greens_functions_per_second", "G/s"),
+    "n16_beta8": ("greens_functions_per_second", "G/s"),
+}
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -212,57 +222,102 @@ def measured_traffic(workload: str, record: str = "chain_gemm_traffic.json",
 
 
 # ---------------------------------------------------------------------------
-def cpu_oracle_rate(insts, seconds: float):
-    """Oracle G/s on the host cores: instances one after another until `seconds` pass."""
-    from oracle import dqmc as od
+def cpu_oracle_rate(run, seconds: float):
+    """Oracle rate on the host cores: samples one after another until `seconds` pass."""
     t0 = time.perf_counter()
-    n = 0
+    n, units = 0, 0.0
     while True:
-        x = insts[n % len(insts)]
-        od.greens(x.K, x.dtau, x.V, x.k)
+        units += run(n)
         n += 1
         if time.perf_counter() - t0 >= seconds:
             break
     dt = time.perf_counter() - t0
-    return n / dt, n, dt
+    return units / dt, n, dt
+
+
+def oracle_sampler(wl: dict, name: str, n_inst: int = 4):
+    """The oracle routine that matches a workload's metric, as one bounded CPU sample.
+
+    Returns (run, what): ``run(i)`` computes sample i on the host
+    cores and returns how many metric units it completed (a fraction for the
+    gradient, whose slices the oracle computes one by one from scratch)."""
+    from oracle import dqmc as od
+    if name == "ragged_1024":
+        insts = [di.ragged_instance(i, 10) for i in range(n_inst)]
+
+        def run(i):
+            x = insts[i % len(insts)]
+            od.greens(x.K, x.dtau, x.V, x.k)
+            return 1.0
+        return run, "equal-time G of the uneven-size instances one after another (k = 10)"
+    if name == "grad_n144":
+        insts = [di.gaussian_instance(wl["L"], wl["g"], wl["dtau"], wl["beta"], wl["k"], sd)
+                 for sd in rank_seeds(wl, 0, n_inst)]
+        M = insts[0].M
+        per = 2                                   # slices l of dV per sample
+
+        def run(i):
+            x = insts[i % len(insts)]
+            first = 1 + (per * i) % M
+            od.logdet_grad(x.K, x.dtau, x.V, x.k,
+                           slices=[(first - 1 + j) % M + 1 for j in range(per)])
+            return per / M
+        return run, f"{per} of the {M} slices of dV per sample, each G_l from scratch; " \
+            f"a gradient counts as {M} slices"
+    insts = [di.hubbard_instance(wl["L"], wl["U"], wl["dtau"], wl["beta"], wl["k"], sd)
+             for sd in rank_seeds(wl, 0, n_inst)]
+    if name == "tdisplaced_n64":
+        def run(i):
+            x = insts[i % len(insts)]
+            od.greens_tdisplaced(x.K, x.dtau, x.V, x.k)
+            return 1.0
+        return run, "G(tau_j, tau_j) and G(tau_j, 0) on the k-grid of one instance per sample"
+
+    def run(i):
+        x = insts[i % len(insts)]
+        od.greens(x.K, x.dtau, x.V, x.k)
+        return 1.0
+    return run, "equal-time G and log det of one instance per sample"
+
+
+def cpu_baseline_line(wl: dict, args) -> dict:
+    """The oracle timed for about ``args.cpu_seconds`` on the host cores (rank 0, N = 1)."""
+    run, what = oracle_sampler(wl, args.workload)
+    unit = METRICS[args.workload][1]
+    rate, n, dt = cpu_oracle_rate(run, args.cpu_seconds)
+    return {"value": rate, "unit": unit, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{n} sample(s) in {dt:.1f} s: {what} "
+                      f"(NumPy/SciPy FP64, BLAS threads = all cores)"}
 
 
 def run_reference(args, wl, rank, world):
+    """The oracle as it stands, on the host cores, on the same workload and metric."""
     if rank != 0:
         return
-    if "U" not in wl:
-        print(json.dumps({"impl": "reference", "unavailable":
-                          f"the CPU oracle arm is timed on the equal-time workloads only ({args.workload})"}))
-        return
-    batch = args.batch or wl["batch"]
-    K, V, insts = make_inputs(wl, 0, min(batch, 8))
-    from oracle import dqmc as od
+    run, what = oracle_sampler(wl, args.workload)
+    metric, unit = METRICS[args.workload]
     for i in range(args.warmup):
-        x = insts[i % len(insts)]
-        od.greens(x.K, x.dtau, x.V, x.k)
-    times = []
+        run(i)
+    times, units = [], 0.0
     for s in range(args.steps):
-        x = insts[s % len(insts)]
         t0 = time.perf_counter()
-        od.greens(x.K, x.dtau, x.V, x.k)
+        units += run(args.warmup + s)
         times.append(time.perf_counter() - t0)
-    per = sum(times) / len(times)
-    value = 1.0 / per
+    tot = sum(times)
+    value = units / tot
     cores = os.cpu_count()
-    N = wl["L"] ** 2
-    M = int(round(wl["beta"] / wl["dtau"]))
+    cfg = {"workload": args.workload, "instances_per_step": units / args.steps, "l2": "n/a (CPU)"}
+    cfg.update({key: wl[key] for key in ("L", "U", "g", "dtau", "beta", "k") if key in wl})
     line = {
-        "metric": "greens_functions_per_second", "value": value, "unit": "G/s",
+        "metric": metric, "value": value, "unit": unit,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "N": N, "M": M, "k": wl["k"], "beta": wl["beta"],
-                   "U": wl["U"], "instances_per_step": 1, "l2": "n/a (CPU)"},
+        "ms_per_step": tot / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
         "impl": "reference",
-        "cpu_baseline": {"value": value, "unit": "G/s", "cores": cores, "kind": "oracle",
-                         "sample": f"1 instance of the {args.workload} workload per step "
+        "cpu_baseline": {"value": value, "unit": unit, "cores": cores, "kind": "oracle",
+                         "sample": f"{what}; {args.steps} timed step(s) "
                                    f"(NumPy/SciPy FP64, BLAS threads = all {cores} cores)"},
-        "e2e": {"value": value, "unit": "G/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
@@ -429,10 +484,7 @@ def run_gpu(args, wl, rank, world):
         return
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        rate, n, dt = cpu_oracle_rate(insts[:4], args.cpu_seconds)
-        cpu = {"value": rate, "unit": "G/s", "cores": os.cpu_count(), "kind": "oracle",
-               "sample": f"{n} instance(s) of the {args.workload} workload run one after "
-                         f"another in {dt:.1f} s (NumPy/SciPy FP64, BLAS threads = all cores)"}
+        cpu = cpu_baseline_line(wl, args)
     if prec == 0:
         # dominant kernel: the FP64 slice product
         dom_ms, dom_n, dom_flops = chain_ms, chain_n, chain_flops
@@ -524,7 +576,6 @@ def run_gpu_other(args, wl, rank, world):
 
         def step():
             return dq.greens_ragged(items, handle=h)
-        metric, unit = "greens_functions_per_second", "G/s"
     else:
         if name == "grad_n144":
             insts = [di.gaussian_instance(wl["L"], wl["g"], wl["dtau"], wl["beta"], wl["k"], sd)
@@ -540,20 +591,18 @@ def run_gpu_other(args, wl, rank, world):
 
             def step():
                 return dq.greens_tdisplaced(K, wl["dtau"], V, k, handle=h)
-            metric, unit = "tdisplaced_sets_per_second", "sets/s"
         elif name == "grad_n144":
             fl = batch * flops_per_grad(N, M, k)
 
             def step():
                 return dq.logdet_grad(K, wl["dtau"], V, k, handle=h)
-            metric, unit = "logdet_gradients_per_second", "grads/s"
         else:
             fl = batch * flops_per_greens(N, M, k)
 
             def step():
                 return dq.greens(K, wl["dtau"], V, k, handle=h)
-            metric, unit = "greens_functions_per_second", "G/s"
         extra.update(N=N, M=M, k=k)
+    metric, unit = METRICS[name]
     for _ in range(args.warmup):
         out = step()
     torch.cuda.synchronize()
@@ -588,7 +637,9 @@ def run_gpu_other(args, wl, rank, world):
                          "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
                          "kernel": "whole step (all kernels), algorithmic FP64 flops"},
             "gpu_launches": launches * args.steps, "clocks": clk,
-            "status_nonzero": int((st != 0).sum().item()), "e2e": None, "cpu_baseline": None}
+            "status_nonzero": int((st != 0).sum().item()), "e2e": None,
+            "cpu_baseline": cpu_baseline_line(wl, args)
+            if world == 1 and not args.no_cpu_baseline else None}
     print(json.dumps(line), flush=True)
 
 
