@@ -239,6 +239,28 @@ def greens_displaced(K, dtau, V, k, l1: int, l2: int = 0):
     return inv_sum_loh(UL, DL, XL, UR, DR, XR)
 
 
+def greens_displaced_back(K, dtau, V, k, l1: int, l2: int):
+    """G(tau_1, tau_2) for tau_2 = l2*dtau > tau_1 = l1*dtau (Sec. 6, second case
+    of Eq. (tdgf_propagate)): -(1 - G_{l1+1}) (B_{l2}...B_{l1+1})^{-1}.
+
+    With C = B_{l2}...B_{l1+1} and Y = B_{l1}...B_1 B_M...B_{l2+1}, so that
+    G_{l1+1} = [1 + Y C]^{-1}, one has 1 - G_{l1+1} = (1 + Y C)^{-1} Y C and
+    hence, as in the paper's derivation of the first case,
+        G(tau_1, tau_2) = -[C + Y^{-1}]^{-1},
+        Y^{-1} = B_{l2+1}^{-1}...B_M^{-1} B_1^{-1}...B_{l1}^{-1}.
+    C grows by B_{l1+1} first, Y^{-1} by B_{l1}^{-1} first; both are
+    stabilised every k slices and combined by inv_sum_loh.  l1 == l2 gives
+    -(1 - G_{l1+1}) (the tau_2 -> tau_1^+ limit); (l1, l2) = (0, M) gives -G_1."""
+    M, N = V.shape
+    assert 0 <= l1 <= l2 <= M
+    EK = hopping_exponential(K, dtau)
+    EKinv = hopping_exponential(K, dtau, sign=+1.0)
+    UL, DL, XL = udx_chain(forward_slices(EK, V, list(range(l1 + 1, l2 + 1))), k, N)
+    right = inverse_slices(EKinv, V, list(range(l1, 0, -1)) + list(range(M, l2, -1)))
+    UR, DR, XR = udx_chain(right, k, N)
+    return -inv_sum_loh(UL, DL, XL, UR, DR, XR)
+
+
 def tau_grid(M: int, k: int):
     """Slice indices l_j = min(j*k, M), j = 0..ceil(M/k), of the k-grid."""
     nc = -(-M // k)
@@ -252,6 +274,13 @@ def greens_tdisplaced(K, dtau, V, k):
     Gtt = np.stack([greens(K, dtau, V, k, l=l + 1)[0] for l in grid])
     Gt0 = np.stack([greens_displaced(K, dtau, V, k, l, 0) for l in grid])
     return Gtt, Gt0
+
+
+def greens_tdisplaced_0t(K, dtau, V, k):
+    """G0t[j] = G(0, tau_j) on the k-grid by the second case of Eq. (tdgf_propagate);
+    G0t[0] is its tau -> 0^+ limit -(1 - G_1), G0t[-1] = G(0, beta) = -G_1."""
+    M, N = V.shape
+    return np.stack([greens_displaced_back(K, dtau, V, k, 0, l) for l in tau_grid(M, k)])
 
 
 # ---------------------------------------------------------------------------

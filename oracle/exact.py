@@ -58,6 +58,18 @@ def closed_form_displaced(K: np.ndarray, beta: float, tau: float,
     return (Q * w[None, :]) @ Q.T
 
 
+def closed_form_displaced_back(K: np.ndarray, beta: float, tau: float,
+                               shift_total: float = 0.0, shift_tau: float = 0.0):
+    """G(0, tau) = -(1 - G_1) B(tau, 0)^{-1}
+    = -Q diag(exp(tau eps - s_tau) / (1 + exp(beta eps - s))) Q^T.
+
+    1 - G_1 has eigenvalues 1 / (1 + exp(beta eps - s)) and B(tau, 0)^{-1} has
+    exp(tau eps - s_tau); each weight is evaluated in the overflow-free form."""
+    eps, Q = np.linalg.eigh(K)
+    w = np.exp(tau * eps - shift_tau - np.logaddexp(0.0, beta * eps - shift_total))
+    return -(Q * w[None, :]) @ Q.T
+
+
 # ---------------------------------------------------------------------------
 # Arbitrary-precision brute force
 # ---------------------------------------------------------------------------
@@ -123,6 +135,13 @@ class BruteForce:
         """G(tau_{l1}, 0) = B_{l1}...B_1 [1 + B_M...B_1]^{-1}."""
         G1, _, _ = self.greens(1)
         return self.chain(range(1, l1 + 1)) * G1
+
+    def displaced_back(self, l1: int, l2: int):
+        """G(tau_{l1}, tau_{l2}), l2 >= l1: -(1 - G_{l1+1}) (B_{l2}...B_{l1+1})^{-1}."""
+        mp = self.mp
+        G, _, _ = self.greens(l1 + 1)
+        C = self.chain(range(l1 + 1, l2 + 1))
+        return -(mp.eye(self.N) - G) * mp.inverse(C)
 
     @staticmethod
     def to_numpy(A) -> np.ndarray:

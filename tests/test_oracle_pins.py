@@ -266,3 +266,59 @@ def test_tau_grid():
     assert od.tau_grid(80, 10) == [0, 10, 20, 30, 40, 50, 60, 70, 80]
     assert od.tau_grid(25, 10) == [0, 10, 20, 25]
     assert od.tau_grid(5, 10) == [0, 5]
+
+
+# ---------------------------------------------------------------------------
+# G(tau_1, tau_2) for tau_2 > tau_1 (second case of Eq. (tdgf_propagate))
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("l2", [0, 1, 10, 200, 390, 400])
+def test_closed_form_displaced_back(l2, rng):
+    """P1 for G(0, tau) at beta = 40: -(1 - G_1) B(tau,0)^{-1} in the eigenbasis of K."""
+    K = di.chain_hopping(8)
+    M = 400
+    c = rng.uniform(-0.3, 0.3, M)
+    V = np.repeat(c[:, None], 8, axis=1)
+    G = od.greens_displaced_back(K, 0.1, V, 10, 0, l2)
+    Gx = ex.closed_form_displaced_back(K, 40.0, 0.1 * l2, shift_total=c.sum(),
+                                       shift_tau=c[:l2].sum())
+    assert np.abs(G - Gx).max() < 1e-12
+
+
+@pytest.mark.parametrize("N,M,k,scale,seed", [(3, 40, 7, 0.7, 2), (4, 35, 8, 1.2, 4)])
+def test_brute_force_displaced_back(N, M, k, scale, seed):
+    """P4 for tau_2 > tau_1: mpmath -(1 - G_{l1+1}) (B_{l2}...B_{l1+1})^{-1}."""
+    K = di.chain_hopping(N, periodic=N > 2)
+    V = scale * di.ising_field(seed, M, N)
+    bf = ex.BruteForce(K, 0.1, V)
+    for l1, l2 in ((0, 0), (0, 1), (0, M // 2), (0, M), (M // 3, 2 * M // 3), (5, 5)):
+        G = od.greens_displaced_back(K, 0.1, V, k, l1, l2)
+        assert np.abs(G - bf.to_numpy(bf.displaced_back(l1, l2))).max() < 1e-12
+
+
+def test_displaced_back_propagation_and_ends():
+    """P6: G(0, tau + dtau) = G(0, tau) B_{l+1}^{-1}; G(0, 0^+) = -(1 - G_1); G(0, beta) = -G_1."""
+    K, V = _hubbard(4, 4.0, 6.0, seed=11)
+    M = V.shape[0]
+    EKinv = od.hopping_exponential(K, 0.1, +1.0)
+    G1 = od.greens(K, 0.1, V, 10)[0]
+    assert np.abs(od.greens_displaced_back(K, 0.1, V, 10, 0, 0) + (np.eye(16) - G1)).max() < 1e-12
+    assert np.abs(od.greens_displaced_back(K, 0.1, V, 10, 0, M) + G1).max() < 1e-12
+    for l in (0, 23, 44):
+        Ga = od.greens_displaced_back(K, 0.1, V, 10, 0, l)
+        Gb = od.greens_displaced_back(K, 0.1, V, 10, 0, l + 1)
+        assert np.abs(Gb - Ga @ od.inverse_slice_matrix(EKinv, V[l])).max() < 1e-10
+
+
+@pytest.mark.parametrize("beta", [4.0, 20.0])
+def test_particle_hole_displaced(beta):
+    """P7 links the two cases: B_{-V}(tau,0) = Lambda B_V(tau,0)^{-T} Lambda gives
+    G_{-V}(tau, 0) = -Lambda G_V(0, tau)^T Lambda at every tau."""
+    L = 4
+    K, V = _hubbard(L, 4.0, beta, seed=5)
+    M = V.shape[0]
+    lam = np.array([(-1.0) ** (x + y) for y in range(L) for x in range(L)])
+    for l in (0, 7, M // 2, M):
+        Gm = od.greens_displaced(K, 0.1, -V, 10, l, 0)
+        Gp = od.greens_displaced_back(K, 0.1, V, 10, 0, l)
+        assert np.abs(Gm + lam[:, None] * Gp.T * lam[None, :]).max() < 1e-10
