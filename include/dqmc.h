@@ -165,6 +165,22 @@ dqmc_status dqmc_greens_tdisplaced(dqmc_handle h, int batch, int N, int M,
                                    const double* K, double dtau, const double* V,
                                    int k, double* Gtt, double* Gt0, int* status);
 
+/* As dqmc_greens_tdisplaced, plus the other time order on the same k-grid
+ * (second case of Eq. (tdgf_propagate), Sec. 6):
+ *   G0t [batch*n_tau*N*N]  G(0, tau_j) = -(1 - G_1) (B_{l_j}...B_1)^{-1}, may be NULL,
+ * same layout as Gtt.  j = 0 holds the limit tau -> 0^+, -(1 - G_1), and
+ * j = n_tau - 1 holds G(0, beta) = -G_1.  With B(tau,0) = U_F a X_F and
+ * B(beta,tau)^T = U_b b T_b from the two stacks,
+ *   G(0,tau) = -[B(tau,0) + B(beta,tau)^{-1}]^{-1} = -T_b^T b_m mid^{-1} a_p^{-1} U_F^T,
+ * where mid is the D+/D- split middle matrix that G(tau,0) inverts and the
+ * solve mid^{-1} a_p^{-1} U_F^T is the one G(tau,tau) uses: G0t costs one
+ * N x N product per tau_j on top of Gtt.  Arguments, errors and status as in
+ * dqmc_greens_tdisplaced. */
+dqmc_status dqmc_greens_tdisplaced_ex(dqmc_handle h, int batch, int N, int M,
+                                      const double* K, double dtau, const double* V,
+                                      int k, double* Gtt, double* Gt0, double* G0t,
+                                      int* status);
+
 /* Gradient dV[(b*M + (l-1))*N + i] = d log|det(1 + B_M...B_1)| / dV_l(i)
  * = 1 - G_l(i,i) for every slice l (derived from Eqs. (etgf), (etgf_tau)):
  * G_l at the k-grid from the two stacks, then G_{l+1} = B_l G_l B_l^{-1}
@@ -203,6 +219,13 @@ dqmc_status dqmc_greens_ragged(dqmc_handle h, int batch, const dqmc_instance* de
 dqmc_status dqmc_greens_tdisplaced_ragged(dqmc_handle h, int batch, const dqmc_instance* desc,
                                           const double* K_pool, const double* V_pool,
                                           double* Gtt_pool, double* Gt0_pool, int* status);
+
+/* As dqmc_greens_tdisplaced_ragged, plus G(0, tau_j) of each instance in
+ * G0t_pool at desc[b].off_G (see dqmc_greens_tdisplaced_ex; may be NULL). */
+dqmc_status dqmc_greens_tdisplaced_ragged_ex(dqmc_handle h, int batch, const dqmc_instance* desc,
+                                             const double* K_pool, const double* V_pool,
+                                             double* Gtt_pool, double* Gt0_pool,
+                                             double* G0t_pool, int* status);
 
 /* Ragged log-det gradient: as dqmc_logdet_grad per instance, grouped as in
  * dqmc_greens_tdisplaced_ragged.  Instance b writes its M_b x N_b gradient

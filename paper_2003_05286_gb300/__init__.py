@@ -163,21 +163,33 @@ def logdet(K, dtau: float, V, k: int, *, handle: Handle | None = None):
 
 
 def greens_tdisplaced(K, dtau: float, V, k: int, *, handle: Handle | None = None,
-                      want_tt: bool = True, want_t0: bool = True):
-    """G(tau_j, tau_j) and G(tau_j, 0) on the k-grid: tensors (B, n_tau, N, N) and status."""
+                      want_tt: bool = True, want_t0: bool = True, want_0t: bool = False):
+    """G(tau_j, tau_j) and G(tau_j, 0) on the k-grid: tensors (B, n_tau, N, N) and status.
+
+    With ``want_0t`` also G(0, tau_j) (dqmc_greens_tdisplaced_ex), returned
+    after Gt0: (Gtt, Gt0, G0t, status)."""
     K, V, sq = _prep(K, V)
     B, M, N = V.shape
     nt = n_tau(M, k)
     h = _handle(handle)
-    Gtt = torch.empty((B, nt, N, N), dtype=torch.float64, device=V.device) if want_tt else None
-    Gt0 = torch.empty((B, nt, N, N), dtype=torch.float64, device=V.device) if want_t0 else None
+
+    def out(want):
+        return torch.empty((B, nt, N, N), dtype=torch.float64, device=V.device) if want else None
+    Gtt, Gt0, G0t = out(want_tt), out(want_t0), out(want_0t)
     st = torch.empty(B, dtype=torch.int32, device=V.device)
-    _abi.check(h._lib.dqmc_greens_tdisplaced(h.h, B, N, M, _ptr(K), float(dtau), _ptr(V), int(k),
-                                             _ptr(Gtt), _ptr(Gt0), _ptr(st)),
-               "dqmc_greens_tdisplaced")
+    if want_0t:
+        _abi.check(h._lib.dqmc_greens_tdisplaced_ex(h.h, B, N, M, _ptr(K), float(dtau), _ptr(V),
+                                                    int(k), _ptr(Gtt), _ptr(Gt0), _ptr(G0t),
+                                                    _ptr(st)), "dqmc_greens_tdisplaced_ex")
+        res = (Gtt, Gt0, G0t)
+    else:
+        _abi.check(h._lib.dqmc_greens_tdisplaced(h.h, B, N, M, _ptr(K), float(dtau), _ptr(V),
+                                                 int(k), _ptr(Gtt), _ptr(Gt0), _ptr(st)),
+                   "dqmc_greens_tdisplaced")
+        res = (Gtt, Gt0)
     if sq:
-        return (Gtt[0] if Gtt is not None else None), (Gt0[0] if Gt0 is not None else None), st[0]
-    return Gtt, Gt0, st
+        return tuple(x[0] if x is not None else None for x in res) + (st[0],)
+    return res + (st,)
 
 
 def logdet_grad(K, dtau: float, V, k: int, *, handle: Handle | None = None):
@@ -261,22 +273,31 @@ def _pack_ragged(instances, device, out_len):
 
 
 def greens_tdisplaced_ragged(instances, *, handle: Handle | None = None, device=None,
-                             want_tt: bool = True, want_t0: bool = True):
+                             want_tt: bool = True, want_t0: bool = True, want_0t: bool = False):
     """Ragged G(tau_j, tau_j) and G(tau_j, 0): ``instances`` as for greens_ragged.
 
-    Returns (list of Gtt (n_tau, N, N) or None, list of Gt0 or None, status)."""
+    Returns (list of Gtt (n_tau, N, N) or None, list of Gt0 or None, status);
+    with ``want_0t`` also the list of G(0, tau_j) after Gt0."""
     device = device or instances[0][0].device
     descs, Kp, Vp, total = _pack_ragged(instances, device, lambda N, M, k: n_tau(M, k) * N * N)
-    Gtt = torch.empty(total, dtype=torch.float64, device=device) if want_tt else None
-    Gt0 = torch.empty(total, dtype=torch.float64, device=device) if want_t0 else None
+
+    def pool(want):
+        return torch.empty(total, dtype=torch.float64, device=device) if want else None
+    Gtt, Gt0, G0t = pool(want_tt), pool(want_t0), pool(want_0t)
     B = len(instances)
     st = torch.empty(B, dtype=torch.int32, device=device)
     h = _handle(handle)
-    _abi.check(h._lib.dqmc_greens_tdisplaced_ragged(h.h, B, descs, _ptr(Kp), _ptr(Vp), _ptr(Gtt),
-                                                    _ptr(Gt0), _ptr(st)),
-               "dqmc_greens_tdisplaced_ragged")
+    if want_0t:
+        _abi.check(h._lib.dqmc_greens_tdisplaced_ragged_ex(h.h, B, descs, _ptr(Kp), _ptr(Vp),
+                                                           _ptr(Gtt), _ptr(Gt0), _ptr(G0t),
+                                                           _ptr(st)),
+                   "dqmc_greens_tdisplaced_ragged_ex")
+    else:
+        _abi.check(h._lib.dqmc_greens_tdisplaced_ragged(h.h, B, descs, _ptr(Kp), _ptr(Vp),
+                                                        _ptr(Gtt), _ptr(Gt0), _ptr(st)),
+                   "dqmc_greens_tdisplaced_ragged")
     outs = []
-    for pool in (Gtt, Gt0):
+    for pool in ((Gtt, Gt0, G0t) if want_0t else (Gtt, Gt0)):
         if pool is None:
             outs.append(None)
             continue
@@ -286,7 +307,7 @@ def greens_tdisplaced_ragged(instances, *, handle: Handle | None = None, device=
             nt = n_tau(d.M, d.k)
             lst.append(pool[d.off_G: d.off_G + nt * d.N * d.N].view(nt, d.N, d.N))
         outs.append(lst)
-    return outs[0], outs[1], st
+    return tuple(outs) + (st,)
 
 
 def logdet_grad_ragged(instances, *, handle: Handle | None = None, device=None):

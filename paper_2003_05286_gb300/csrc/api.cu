@@ -1053,14 +1053,18 @@ dqmc_status dqmc_logdet(dqmc_handle h, int batch, int N, int M, const double* K,
 //   mid = a_p^{-1} (U_F^T U_b) b_p^{-1} + a_m (X_F T_b^T) b_m        (all factors <= 1)
 //   1 + B(tau,0) B(beta,tau)       = U_F a_p mid b_p U_b^T
 //   B(tau,0)^{-1} + B(beta,tau)    = X_F^{-1} a_m^{-1} mid b_p U_b^T
+//   B(tau,0) + B(beta,tau)^{-1}    = U_F a_p mid b_m^{-1} T_b^{-T}
 // so that
 //   G(tau,tau) = U_b b_p^{-1} mid^{-1} a_p^{-1} U_F^T
 //   G(tau,0)   = U_b b_p^{-1} mid^{-1} a_m X_F
+//   G(0,tau)   = -T_b^T b_m mid^{-1} a_p^{-1} U_F^T
 // The second line is Eq. (inversion_tdgf_loh) with the left chain
 // B_1^{-1}...B_l^{-1} = X_F^{-1} a^{-1} U_F^T taken from the forward stack
 // (its scales a^{-1} split as D_Lp = a_m^{-1}, D_Lm = a_p^{-1}); the first is
-// the same split applied to the equal-time bracket of App. A.  One LU of mid
-// serves both right-hand sides.
+// the same split applied to the equal-time bracket of App. A; the third is
+// the second case of Eq. (tdgf_propagate), -(1 - G_1) B(tau,0)^{-1}
+// = -[B(tau,0) + B(beta,tau)^{-1}]^{-1}.  One LU of mid serves all three:
+// G(tau,tau) and G(0,tau) share the solve Z = mid^{-1} a_p^{-1} U_F^T.
 // ---------------------------------------------------------------------------
 namespace {
 
@@ -1133,13 +1137,15 @@ void take_mid(Arena& ar, long long Q, int N, int ncols, MidWs& w) {
   w.bpinv = ar.take<double>(Q * N);
 }
 
-// Problems q = b*nt + j over all stack slots; writes G(tau,tau) to Gtt and
-// G(tau,0) to Gt0 (either may be null), each Q x N x N.
+// Problems q = b*nt + j over all stack slots; writes G(tau,tau) to Gtt,
+// G(tau,0) to Gt0 and G(0,tau) to G0t (each may be null), each Q x N x N.
 dqmc_status run_two_stack_inversion(dqmc_handle h, int Q, int N, int nt, const StackWs& w,
-                                    const MidWs& m, double* Gtt, double* Gt0, int* status) {
+                                    const MidWs& m, double* Gtt, double* Gt0, double* G0t,
+                                    int* status) {
   cudaStream_t st = h->cur;
   const long long NN = (long long)N * N;
-  const int ncols = (Gtt ? N : 0) + (Gt0 ? N : 0);
+  const bool want_z = Gtt || G0t;                      // Z = mid^{-1} a_p^{-1} U_F^T
+  const int ncols = (want_z ? N : 0) + (Gt0 ? N : 0);
   if (ncols == 0) return DQMC_OK;
   const double gflops = 2.0 * N * (double)N * N * Q;
   GemmArgs g1;                                         // C1 = U_F^T U_b
@@ -1164,7 +1170,7 @@ dqmc_status run_two_stack_inversion(dqmc_handle h, int Q, int N, int nt, const S
   ax.cb = w.Db; ax.cb_mode = 2; ax.scb = N;
   ax.C = m.mid; ax.sC = NN;
   CK(axpby2(ax, st));
-  CK(build_rhs(N, Q, w.UF, w.XF, w.DF, m.R, ncols, Gtt != nullptr, Gt0 != nullptr, st));
+  CK(build_rhs(N, Q, w.UF, w.XF, w.DF, m.R, ncols, want_z, Gt0 != nullptr, st));
   LuArgs lu;
   lu.N = N; lu.nrhs = ncols; lu.batch = Q;
   lu.A = m.mid; lu.sA = NN;
@@ -1180,9 +1186,21 @@ dqmc_status run_two_stack_inversion(dqmc_handle h, int Q, int N, int nt, const S
     GemmArgs g;                                        // G = U_b b_p^{-1} Z
     g.M = g.N = g.K = N; g.batch = Q;
     g.A = w.Ub; g.lda = N; g.sA = NN;
-    g.B = m.Z + ((part == 1 && Gtt) ? N : 0); g.ldb = ncols; g.sB = (long long)N * ncols;
+    g.B = m.Z + ((part == 1 && want_z) ? N : 0); g.ldb = ncols; g.sB = (long long)N * ncols;
     g.ms = m.bpinv; g.sms = N;
     g.C = out; g.ldc = N; g.sC = NN;
+    CKP(PC_OTHER, gflops, gemm_f64(g, st));
+  }
+  if (G0t) {
+    // b_m overwrites b_p^{-1}: the products above are ahead of it on the stream
+    CK(dsplit_vec(w.Db, N, N, Q, m.bpinv, 2, st));
+    GemmArgs g;                                        // G(0,tau) = -T_b^T b_m Z
+    g.M = g.N = g.K = N; g.batch = Q;
+    g.A = w.Tb; g.lda = N; g.sA = NN; g.transA = 1;
+    g.B = m.Z; g.ldb = ncols; g.sB = (long long)N * ncols;
+    g.ms = m.bpinv; g.sms = N;
+    g.alpha = -1.0;
+    g.C = G0t; g.ldc = N; g.sC = NN;
     CKP(PC_OTHER, gflops, gemm_f64(g, st));
   }
   return DQMC_OK;
@@ -1194,22 +1212,28 @@ extern "C" {
 
 static dqmc_status tdisplaced_impl(dqmc_handle h, int batch, int N, int M, const double* K,
                                    double dtau, const double* V, int k, double* Gtt, double* Gt0,
-                                   int* status);
+                                   double* G0t, int* status);
+
+dqmc_status dqmc_greens_tdisplaced_ex(dqmc_handle h, int batch, int N, int M, const double* K,
+                                      double dtau, const double* V, int k, double* Gtt,
+                                      double* Gt0, double* G0t, int* status) {
+  if (!h) return DQMC_ERR_ARG;
+  GraphKey key = key_of(3, batch, N, M, K, dtau, V, k);
+  key.addp(Gtt); key.addp(Gt0); key.addp(G0t); key.addp(status);
+  return graph_call(h, key, [&] {
+    return tdisplaced_impl(h, batch, N, M, K, dtau, V, k, Gtt, Gt0, G0t, status);
+  });
+}
 
 dqmc_status dqmc_greens_tdisplaced(dqmc_handle h, int batch, int N, int M, const double* K,
                                    double dtau, const double* V, int k, double* Gtt, double* Gt0,
                                    int* status) {
-  if (!h) return DQMC_ERR_ARG;
-  GraphKey key = key_of(3, batch, N, M, K, dtau, V, k);
-  key.addp(Gtt); key.addp(Gt0); key.addp(status);
-  return graph_call(h, key, [&] {
-    return tdisplaced_impl(h, batch, N, M, K, dtau, V, k, Gtt, Gt0, status);
-  });
+  return dqmc_greens_tdisplaced_ex(h, batch, N, M, K, dtau, V, k, Gtt, Gt0, nullptr, status);
 }
 
 static dqmc_status tdisplaced_impl(dqmc_handle h, int batch, int N, int M, const double* K,
                                    double dtau, const double* V, int k, double* Gtt, double* Gt0,
-                                   int* status) {
+                                   double* G0t, int* status) {
   CKS(check_common(h, batch, N, M, K, dtau, V, k));
   if (h->prec != DQMC_CHAIN_FP64 && N > 256) return DQMC_ERR_UNSUPPORTED;
   h->launches = 0;
@@ -1221,10 +1245,10 @@ static dqmc_status tdisplaced_impl(dqmc_handle h, int batch, int N, int M, const
   const long long Mp = (long long)(nc + 1) * k;
   const long long Q = (long long)batch * nt;
   if (Q > (1LL << 30)) return DQMC_ERR_ARG;
-  const int ncols = (Gtt ? N : 0) + (Gt0 ? N : 0);
+  const int ncols = (Gtt || G0t ? N : 0) + (Gt0 ? N : 0);
 
   ExpmWs ew; ChainWs cw, cw2; StackWs sw; MidWs mw; HostIO io;
-  double *expV, *Gttd = nullptr, *Gt0d = nullptr;
+  double *expV, *Gttd = nullptr, *Gt0d = nullptr, *G0td = nullptr;
   int* stat;
   auto layout = [&](Arena& ar) {
     take_expm(ar, N, ew);
@@ -1243,6 +1267,7 @@ static dqmc_status tdisplaced_impl(dqmc_handle h, int batch, int N, int M, const
       io.V = ar.take<double>((long long)M * N * batch);
       Gttd = Gtt ? ar.take<double>(Q * NN) : nullptr;
       Gt0d = Gt0 ? ar.take<double>(Q * NN) : nullptr;
+      G0td = G0t ? ar.take<double>(Q * NN) : nullptr;
     }
   };
   Arena measure;
@@ -1256,23 +1281,25 @@ static dqmc_status tdisplaced_impl(dqmc_handle h, int batch, int N, int M, const
   const double* Vd = V;
   double* Gtto = Gtt;
   double* Gt0o = Gt0;
+  double* G0to = G0t;
   int* stout = status ? status : stat;
   if (host) {
     if (cudaMemcpyAsync(io.K, K, NN * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaMemcpyAsync(io.V, V, (size_t)M * N * batch * sizeof(double), cudaMemcpyHostToDevice,
                         st) != cudaSuccess)
       return DQMC_ERR_CUDA;
-    Kd = io.K; Vd = io.V; Gtto = Gttd; Gt0o = Gt0d; stout = stat;
+    Kd = io.K; Vd = io.V; Gtto = Gttd; Gt0o = Gt0d; G0to = G0td; stout = stat;
   }
   if (cudaMemsetAsync(stout, 0, sizeof(int) * batch, st) != cudaSuccess) return DQMC_ERR_CUDA;
   CKS(run_expm(h, Kd, N, dtau, -1.0, ew, stout, batch));
   CK(exp_pad(Vd, expV, batch, M, (int)Mp, N, 1.0, stout, st));
   CKS(run_stacks(h, batch, N, M, k, ew.t0, expV, Mp * N, sw, cw, cw2, stout));
-  CKS(run_two_stack_inversion(h, (int)Q, N, nt, sw, mw, Gtto, Gt0o, stout));
+  CKS(run_two_stack_inversion(h, (int)Q, N, nt, sw, mw, Gtto, Gt0o, G0to, stout));
   if (host) {
     bool ok = true;
     if (Gtt) ok &= cudaMemcpyAsync(Gtt, Gttd, Q * NN * sizeof(double), cudaMemcpyDeviceToHost, st) == cudaSuccess;
     if (Gt0) ok &= cudaMemcpyAsync(Gt0, Gt0d, Q * NN * sizeof(double), cudaMemcpyDeviceToHost, st) == cudaSuccess;
+    if (G0t) ok &= cudaMemcpyAsync(G0t, G0td, Q * NN * sizeof(double), cudaMemcpyDeviceToHost, st) == cudaSuccess;
     if (status) ok &= cudaMemcpyAsync(status, stat, batch * sizeof(int), cudaMemcpyDeviceToHost, st) == cudaSuccess;
     ok &= cudaStreamSynchronize(st) == cudaSuccess;
     if (!ok) return DQMC_ERR_CUDA;
@@ -1372,7 +1399,7 @@ static dqmc_status grad_impl(dqmc_handle h, int batch, int N, int M, const doubl
   CKS(run_loh(h, batch, N, sw.UF + nc * NN, nt * NN, sw.DF + (long long)nc * N, (long long)nt * N,
               sw.XF + nc * NN, nt * NN, nullptr, ldo, sgo, stout, lw));
   // checkpoints G_{jk+1}
-  CKS(run_two_stack_inversion(h, (int)Q, N, nt, sw, mw, Gw, nullptr, stout));
+  CKS(run_two_stack_inversion(h, (int)Q, N, nt, sw, mw, Gw, nullptr, nullptr, stout));
   const double wflops = 2.0 * N * (double)N * N * Q;
   for (int s = 0; s < k; ++s) {
     CK(grad_readout(Gw, N, (int)Q, nt, k, M, s, dVo, st));
@@ -1605,7 +1632,7 @@ dqmc_status ensure_rws(dqmc_handle h, size_t bytes) {
 // Staging of one group: V in, `nout` output blocks of `outlen` doubles per
 // instance, per-instance scalars, index tables.
 struct Stage {
-  double *V, *out[2], *ld;
+  double *V, *out[3], *ld;
   int *sg, *st, *gidx;
   long long *offV, *offO;
 };
@@ -1616,7 +1643,7 @@ dqmc_status stage_group(dqmc_handle h, const UGroup& g, const dqmc_instance* des
   const long long vlen = (long long)g.M * g.N;
   auto lay = [&](Arena& ar) {
     S.V = ar.take<double>(vlen * nb);
-    for (int o = 0; o < 2; ++o) S.out[o] = o < nout ? ar.take<double>(outlen * nb) : nullptr;
+    for (int o = 0; o < 3; ++o) S.out[o] = o < nout ? ar.take<double>(outlen * nb) : nullptr;
     S.ld = ar.take<double>(nb);
     S.sg = ar.take<int>(nb);
     S.st = ar.take<int>(nb);
@@ -1663,6 +1690,14 @@ extern "C" {
 dqmc_status dqmc_greens_tdisplaced_ragged(dqmc_handle h, int batch, const dqmc_instance* desc,
                                           const double* K_pool, const double* V_pool,
                                           double* Gtt_pool, double* Gt0_pool, int* status) {
+  return dqmc_greens_tdisplaced_ragged_ex(h, batch, desc, K_pool, V_pool, Gtt_pool, Gt0_pool,
+                                          nullptr, status);
+}
+
+dqmc_status dqmc_greens_tdisplaced_ragged_ex(dqmc_handle h, int batch, const dqmc_instance* desc,
+                                             const double* K_pool, const double* V_pool,
+                                             double* Gtt_pool, double* Gt0_pool,
+                                             double* G0t_pool, int* status) {
   CKS(check_ragged(h, batch, desc, K_pool, V_pool));
   if (batch == 0) return DQMC_OK;
   std::vector<UGroup> groups;
@@ -1672,13 +1707,15 @@ dqmc_status dqmc_greens_tdisplaced_ragged(dqmc_handle h, int batch, const dqmc_i
     const int nb = (int)g.idx.size();
     const long long outlen = (long long)(n_chunks(g.M, g.k) + 1) * g.N * g.N;
     Stage S;
-    CKS(stage_group(h, g, desc, V_pool, outlen, 2, S));
+    CKS(stage_group(h, g, desc, V_pool, outlen, G0t_pool ? 3 : 2, S));
     CKS(tdisplaced_impl(h, nb, g.N, g.M, K_pool + g.offK, g.dtau, S.V, g.k,
-                        Gtt_pool ? S.out[0] : nullptr, Gt0_pool ? S.out[1] : nullptr, S.st));
+                        Gtt_pool ? S.out[0] : nullptr, Gt0_pool ? S.out[1] : nullptr,
+                        G0t_pool ? S.out[2] : nullptr, S.st));
     launches += h->launches;
     cudaStream_t st = h->stream;
     if (Gtt_pool) CK(move_blocks(S.out[0], Gtt_pool, S.offO, outlen, nb, 1, st));
     if (Gt0_pool) CK(move_blocks(S.out[1], Gt0_pool, S.offO, outlen, nb, 1, st));
+    if (G0t_pool) CK(move_blocks(S.out[2], G0t_pool, S.offO, outlen, nb, 1, st));
     if (status) CK(scatter_scalars(S.gidx, nb, nullptr, nullptr, S.st, nullptr, nullptr, status, st));
   }
   h->launches = launches;

@@ -117,6 +117,20 @@ def test_ragged_tdisplaced(dq):
             assert np.abs(Gt0[i].cpu().numpy() - Ot0).max() <= GTOL * max(1.0, np.abs(Ot0).max())
 
 
+def test_ragged_tdisplaced_g0t(dq):
+    """dqmc_greens_tdisplaced_ragged_ex: G(0, tau_j) per instance equals the uniform call."""
+    insts, items = _mixed_sizes(9, 33)
+    Gtt, Gt0, G0t, st = dq.greens_tdisplaced_ragged(items, want_t0=False, want_0t=True)
+    assert Gt0 is None and int((st != 0).sum()) == 0
+    for i, x in enumerate(insts):
+        a, _, c, _ = dq.greens_tdisplaced(_dev(x.K), x.dtau, _dev(x.V), x.k, want_t0=False,
+                                          want_0t=True)
+        assert torch.equal(Gtt[i], a) and torch.equal(G0t[i], c), i
+        if i < 3:
+            O = od.greens_tdisplaced_0t(x.K, x.dtau, x.V, x.k)
+            assert np.abs(G0t[i].cpu().numpy() - O).max() <= GTOL * max(1.0, np.abs(O).max())
+
+
 def test_ragged_grad(dq):
     insts, items = _mixed_sizes(14, 47)
     ld, sg, dVs, st = dq.logdet_grad_ragged(items)

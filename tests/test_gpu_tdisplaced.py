@@ -114,3 +114,90 @@ def test_tdisplaced_full_size_sampled(dq):
             Ott = od.greens(x.K, 0.1, x.V, 10, l=l + 1)[0]
             assert _cmp(Gt0[b, j].cpu().numpy(), Ot0) <= GTOL, (b, j)
             assert _cmp(Gtt[b, j].cpu().numpy(), Ott) <= GTOL, (b, j)
+
+
+# ---------------------------------------------------------------------------
+# G(0, tau_j): the second case of Eq. (tdgf_propagate) (dqmc_greens_tdisplaced_ex)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("L,beta,k,seed", [(2, 3.0, 10, 1), (3, 2.5, 10, 2), (4, 4.0, 7, 4),
+                                            (6, 6.3, 10, 5)])
+def test_g0t_vs_oracle(dq, L, beta, k, seed):
+    """G(0, tau_j) on every grid point, incl. a short last chunk (M = 63, k = 10 or 7)."""
+    inst = di.hubbard_instance(L, 4.0, 0.1, beta, k, seed)
+    K, V = _dev(inst.K), _dev(inst.V)
+    Gtt, Gt0, G0t, st = dq.greens_tdisplaced(K, 0.1, V, k, want_0t=True)
+    assert int(st) == 0
+    # the two existing outputs are the same numbers as without G0t
+    a, b, _ = dq.greens_tdisplaced(K, 0.1, V, k)
+    assert torch.equal(a, Gtt) and torch.equal(b, Gt0)
+    O0t = od.greens_tdisplaced_0t(inst.K, 0.1, inst.V, k)
+    G0t = G0t.cpu().numpy()
+    assert G0t.shape == O0t.shape
+    for j in range(O0t.shape[0]):
+        assert _cmp(G0t[j], O0t[j]) <= GTOL, j
+
+
+def test_g0t_alone_and_ends(dq):
+    """G0t without the other outputs (one right-hand side block); G(0,0^+) = -(1 - G_1),
+    G(0, beta) = -G_1."""
+    inst = di.hubbard_instance(4, 4.0, 0.1, 6.0, 10, 8)
+    K, V = _dev(inst.K), _dev(inst.V)
+    _, _, G0t, st = dq.greens_tdisplaced(K, 0.1, V, 10, want_tt=False, want_t0=False,
+                                         want_0t=True)
+    _, _, full, _ = dq.greens_tdisplaced(K, 0.1, V, 10, want_0t=True)
+    assert int(st) == 0
+    assert (G0t - full).abs().max() <= 1e-12
+    G1 = dq.greens(K, 0.1, V, 10)[0]
+    I = torch.eye(16, dtype=torch.float64, device="cuda")
+    assert (G0t[0] + (I - G1)).abs().max() <= GTOL
+    assert (G0t[-1] + G1).abs().max() <= GTOL
+
+
+def test_g0t_closed_form_beta40(dq):
+    """U = 0, site-independent field, beta = 40: -(1 - G_1) B(tau,0)^{-1} at every tau."""
+    K = di.chain_hopping(8)
+    M = 400
+    c = np.random.default_rng(41).uniform(-0.3, 0.3, M)
+    V = np.repeat(c[:, None], 8, axis=1)
+    _, _, G0t, st = dq.greens_tdisplaced(_dev(K), 0.1, _dev(V), 10, want_tt=False,
+                                         want_t0=False, want_0t=True)
+    G0t = G0t.cpu().numpy()
+    for j, l in enumerate(od.tau_grid(M, 10)):
+        Gx = ex.closed_form_displaced_back(K, 40.0, 0.1 * l, c.sum(), c[:l].sum())
+        assert np.abs(G0t[j] - Gx).max() <= GTOL, (j, np.abs(G0t[j] - Gx).max())
+
+
+def test_g0t_brute_force(dq):
+    K = di.chain_hopping(4)
+    V = 0.8 * di.ising_field(6, 60, 4)
+    bf = ex.BruteForce(K, 0.1, V)
+    _, _, G0t, _ = dq.greens_tdisplaced(_dev(K), 0.1, _dev(V), 10, want_0t=True)
+    G0t = G0t.cpu().numpy()
+    for j, l in enumerate(od.tau_grid(60, 10)):
+        assert np.abs(G0t[j] - bf.to_numpy(bf.displaced_back(0, l))).max() <= GTOL
+
+
+def test_g0t_full_size(dq):
+    """8x8 lattice, U=4, beta=40, k=10, 256 instances in one call.  Every tau_j of
+    every instance: the particle-hole link G_{-V}(tau,0) = -Lambda G_V(0,tau)^T Lambda
+    between two calls; instances 0 and 255 against the oracle at five tau_j."""
+    insts = [di.batch_n64_tdisplaced(i) for i in range(256)]
+    K = _dev(insts[0].K)
+    V = _dev(np.stack([x.V for x in insts]))
+    _, _, G0t, st = dq.greens_tdisplaced(K, 0.1, V, 10, want_tt=False, want_t0=False,
+                                         want_0t=True)
+    assert int((st != 0).sum()) == 0 and G0t.shape == (256, 41, 64, 64)
+    _, Gt0m, st2 = dq.greens_tdisplaced(K, 0.1, -V, 10, want_tt=False)
+    assert int((st2 != 0).sum()) == 0
+    lam = torch.tensor([(-1.0) ** (x + y) for y in range(8) for x in range(8)],
+                       dtype=torch.float64, device="cuda")
+    link = Gt0m + lam[:, None] * G0t.transpose(-1, -2) * lam[None, :]
+    scale = torch.clamp(Gt0m.abs().amax(dim=(-1, -2)), min=1.0)
+    assert float((link.abs().amax(dim=(-1, -2)) / scale).max()) <= GTOL
+    for b in (0, 255):
+        x = insts[b]
+        for j in (0, 13, 20, 40):
+            l = min(10 * j, 400)
+            O = od.greens_displaced_back(x.K, 0.1, x.V, 10, 0, l)
+            assert _cmp(G0t[b, j].cpu().numpy(), O) <= GTOL, (b, j)
