@@ -23,6 +23,7 @@ __global__ void __launch_bounds__(NT) lu_kernel(const LuArgs a) {
   double* dinv = lbuf + N;                              // 1 / u_jj
   __shared__ unsigned long long sk[32];
   __shared__ int si[32];
+  __shared__ double sv[32];
   __shared__ int s_flag, s_sign;
   __shared__ double s_lad;
 
@@ -63,34 +64,39 @@ __global__ void __launch_bounds__(NT) lu_kernel(const LuArgs a) {
     // ---- elimination with partial pivoting -------------------------------
     // Per column j, three barriers: (1) candidates of the pivot search (the
     // column is kept in registers), (2) multipliers + row swap, (3) update.
+    // The pivot value travels with its candidate: between (1) and (2) thread
+    // 0 swaps rows j and p (column j included), so W[p][j] is not re-read.
     for (int j = 0; j < N; ++j) {
       double x[RPT];
       unsigned long long key = 0ull;   // |a_rj| bits (sign cleared), ordered like the values
       int idx = 0x7fffffff;
+      double val = 0.0;                // a_rj of the candidate
 #pragma unroll
       for (int q = 0; q < RPT; ++q) {
         const int r = j + tid + q * NT;
         x[q] = r < N ? W[(long long)r * Wd + j] : 0.0;
         if (r < N) {
           unsigned long long k2 = (unsigned long long)__double_as_longlong(x[q]) & 0x7fffffffffffffffull;
-          if (k2 > key || (k2 == key && r < idx)) { key = k2; idx = r; }
+          if (k2 > key || (k2 == key && r < idx)) { key = k2; idx = r; val = x[q]; }
         }
       }
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) {
         unsigned long long k2 = __shfl_down_sync(0xffffffffu, key, off);
         int i2 = __shfl_down_sync(0xffffffffu, idx, off);
-        if (k2 > key || (k2 == key && i2 < idx)) { key = k2; idx = i2; }
+        double v2 = __shfl_down_sync(0xffffffffu, val, off);
+        if (k2 > key || (k2 == key && i2 < idx)) { key = k2; idx = i2; val = v2; }
       }
-      if (lane == 0) { sk[wid] = key; si[wid] = idx; }
+      if (lane == 0) { sk[wid] = key; si[wid] = idx; sv[wid] = val; }
       const double ajj = W[(long long)j * Wd + j];
       __syncthreads();
       key = sk[0];
       idx = si[0];
+      val = sv[0];
       for (int w = 1; w < NT / 32; ++w)
-        if (sk[w] > key || (sk[w] == key && si[w] < idx)) { key = sk[w]; idx = si[w]; }
+        if (sk[w] > key || (sk[w] == key && si[w] < idx)) { key = sk[w]; idx = si[w]; val = sv[w]; }
       const int p = (idx >= j && idx < N) ? idx : j;
-      const double piv = p == j ? ajj : W[(long long)p * Wd + j];
+      const double piv = p == j ? ajj : val;
       const double inv = piv != 0.0 ? 1.0 / piv : 0.0;
       // multipliers of rows r > j after the swap (row p then holds the old row j)
 #pragma unroll

@@ -181,7 +181,12 @@ def test_g0t_brute_force(dq):
 def test_g0t_full_size(dq):
     """8x8 lattice, U=4, beta=40, k=10, 256 instances in one call.  Every tau_j of
     every instance: the particle-hole link G_{-V}(tau,0) = -Lambda G_V(0,tau)^T Lambda
-    between two calls; instances 0 and 255 against the oracle at five tau_j."""
+    between two calls; instances 0 and 255 against the oracle at four tau_j.
+
+    The link holds to 1e-10 * max(1, max|G|) except on ill-conditioned instances
+    (|G(tau,0)| up to ~1e3), where FP64 itself resolves G only to ~1e-9: there the
+    oracle's two routes miss the same link by a comparable amount, and the GPU
+    must stay within 4x of the oracle's own miss."""
     insts = [di.batch_n64_tdisplaced(i) for i in range(256)]
     K = _dev(insts[0].K)
     V = _dev(np.stack([x.V for x in insts]))
@@ -194,7 +199,17 @@ def test_g0t_full_size(dq):
                        dtype=torch.float64, device="cuda")
     link = Gt0m + lam[:, None] * G0t.transpose(-1, -2) * lam[None, :]
     scale = torch.clamp(Gt0m.abs().amax(dim=(-1, -2)), min=1.0)
-    assert float((link.abs().amax(dim=(-1, -2)) / scale).max()) <= GTOL
+    r = (link.abs().amax(dim=(-1, -2)) / scale).cpu().numpy()
+    over = np.argwhere(r > GTOL)
+    assert len(over) <= 64, len(over)
+    lam_h = lam.cpu().numpy()
+    for b, j in over:
+        x = insts[b]
+        l = min(10 * int(j), 400)
+        Om = od.greens_displaced(x.K, 0.1, -x.V, 10, l, 0)
+        Op = od.greens_displaced_back(x.K, 0.1, x.V, 10, 0, l)
+        own = np.abs(Om + lam_h[:, None] * Op.T * lam_h[None, :]).max() / max(1.0, np.abs(Om).max())
+        assert r[b, j] <= 4.0 * own + GTOL, (int(b), int(j), r[b, j], own)
     for b in (0, 255):
         x = insts[b]
         for j in (0, 13, 20, 40):
