@@ -198,6 +198,17 @@ def logdet(K, dtau, V, k):
 # Time-displaced Green's function (Sec. 6, Eqs. (tdgf_propagate), (inversion_tdgf_loh))
 # ---------------------------------------------------------------------------
 
+def _loh_mid(UL, DL, XL, UR, DR, XR):
+    """The middle matrix of Eq. (inversion_tdgf_loh) (see inv_sum_loh)."""
+    N = DL.shape[0]
+    DLp, DLm = np.maximum(DL, 1.0), np.minimum(DL, 1.0)
+    DRp, DRm = np.maximum(DR, 1.0), np.minimum(DR, 1.0)
+    XRinv = sla.solve(XR, np.eye(N))
+    mid = (DLm[:, None] * (XL @ XRinv)) / DRp[None, :] \
+        + ((UL.T @ UR) / DLp[:, None]) * DRm[None, :]
+    return mid, XRinv, DLp, DRp
+
+
 def inv_sum_loh(UL, DL, XL, UR, DR, XR):
     """[U_L D_L X_L + U_R D_R X_R]^{-1} by the split of Eq. (inversion_tdgf_loh).
 
@@ -209,16 +220,34 @@ def inv_sum_loh(UL, DL, XL, UR, DR, XR):
     D_Rp^{-1} (u d x)^{-1} D_Lp^{-1} is decomposed again (u' d' x'), and the
     result is (X_R^{-1} u') d' (x' U_L^T)."""
     N = DL.shape[0]
-    DLp, DLm = np.maximum(DL, 1.0), np.minimum(DL, 1.0)
-    DRp, DRm = np.maximum(DR, 1.0), np.minimum(DR, 1.0)
-    XRinv = sla.solve(XR, np.eye(N))
-    mid = (DLm[:, None] * (XL @ XRinv)) / DRp[None, :] \
-        + ((UL.T @ UR) / DLp[:, None]) * DRm[None, :]
+    mid, XRinv, DLp, DRp = _loh_mid(UL, DL, XL, UR, DR, XR)
     u, d, x = udt(mid)
     inner = (sla.solve(x, np.eye(N)) / d[None, :]) @ u.T
     inner = inner / DRp[:, None] / DLp[None, :]
     u2, d2, x2 = udt(inner)
     return ((XRinv @ u2) * d2[None, :]) @ (x2 @ UL.T)
+
+
+def _displaced_chains(K, dtau, V, k, l1: int, l2: int):
+    """U_L D_L X_L of B_{l2+1}^{-1}...B_{l1}^{-1} and U_R D_R X_R of
+    B_{l2}...B_1 B_M...B_{l1+1} (Sec. 6), tau_1 = l1*dtau >= tau_2 = l2*dtau."""
+    M, N = V.shape
+    assert 0 <= l2 <= l1 <= M
+    EK = hopping_exponential(K, dtau)
+    EKinv = hopping_exponential(K, dtau, sign=+1.0)
+    left = inverse_slices(EKinv, V, list(range(l1, l2, -1)))
+    right = forward_slices(EK, V, list(range(l1 + 1, M + 1)) + list(range(1, l2 + 1)))
+    return udx_chain(left, k, N) + udx_chain(right, k, N)
+
+
+def displaced_condition(K, dtau, V, k, l1: int, l2: int = 0) -> float:
+    """2-norm condition number of the middle matrix that inv_sum_loh inverts for
+    G(tau_1, tau_2) (Eq. (inversion_tdgf_loh)).  A backward-stable FP64 inversion
+    resolves G(tau_1, tau_2) to about eps * this number relative to max|G|; it is
+    the accuracy bound of an ill-conditioned field, for the oracle and any other
+    FP64 route alike."""
+    mid = _loh_mid(*_displaced_chains(K, dtau, V, k, l1, l2))[0]
+    return float(np.linalg.cond(mid))
 
 
 def greens_displaced(K, dtau, V, k, l1: int, l2: int = 0):
@@ -228,15 +257,7 @@ def greens_displaced(K, dtau, V, k, l1: int, l2: int = 0):
     the left chain grows by B_{l1}^{-1} first, the right chain by B_{l1+1}
     first; both are stabilised every k slices and combined by inv_sum_loh.
     l1 == l2 gives G_{l1+1} (the tau_1 -> tau_2^+ limit)."""
-    M, N = V.shape
-    assert 0 <= l2 <= l1 <= M
-    EK = hopping_exponential(K, dtau)
-    EKinv = hopping_exponential(K, dtau, sign=+1.0)
-    left = inverse_slices(EKinv, V, list(range(l1, l2, -1)))
-    UL, DL, XL = udx_chain(left, k, N)
-    right = forward_slices(EK, V, list(range(l1 + 1, M + 1)) + list(range(1, l2 + 1)))
-    UR, DR, XR = udx_chain(right, k, N)
-    return inv_sum_loh(UL, DL, XL, UR, DR, XR)
+    return inv_sum_loh(*_displaced_chains(K, dtau, V, k, l1, l2))
 
 
 def greens_displaced_back(K, dtau, V, k, l1: int, l2: int):

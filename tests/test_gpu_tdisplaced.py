@@ -183,10 +183,11 @@ def test_g0t_full_size(dq):
     every instance: the particle-hole link G_{-V}(tau,0) = -Lambda G_V(0,tau)^T Lambda
     between two calls; instances 0 and 255 against the oracle at four tau_j.
 
-    The link holds to 1e-10 * max(1, max|G|) except on ill-conditioned instances
-    (|G(tau,0)| up to ~1e3), where FP64 itself resolves G only to ~1e-9: there the
-    oracle's two routes miss the same link by a comparable amount, and the GPU
-    must stay within 4x of the oracle's own miss."""
+    The link holds to 1e-10 * max(1, max|G|) except on ill-conditioned fields
+    (|G(tau,0)| up to ~1e4), where any FP64 route, the oracle's included, resolves
+    G only to about eps * cond(mid) (mid: the middle matrix of Eq.
+    (inversion_tdgf_loh), cond ~ 1e6 there).  At those points the link, a sum of
+    two such errors, must stay below 16 * eps * cond(mid)."""
     insts = [di.batch_n64_tdisplaced(i) for i in range(256)]
     K = _dev(insts[0].K)
     V = _dev(np.stack([x.V for x in insts]))
@@ -202,14 +203,12 @@ def test_g0t_full_size(dq):
     r = (link.abs().amax(dim=(-1, -2)) / scale).cpu().numpy()
     over = np.argwhere(r > GTOL)
     assert len(over) <= 64, len(over)
-    lam_h = lam.cpu().numpy()
+    eps = np.finfo(np.float64).eps
     for b, j in over:
         x = insts[b]
         l = min(10 * int(j), 400)
-        Om = od.greens_displaced(x.K, 0.1, -x.V, 10, l, 0)
-        Op = od.greens_displaced_back(x.K, 0.1, x.V, 10, 0, l)
-        own = np.abs(Om + lam_h[:, None] * Op.T * lam_h[None, :]).max() / max(1.0, np.abs(Om).max())
-        assert r[b, j] <= 4.0 * own + GTOL, (int(b), int(j), r[b, j], own)
+        kappa = od.displaced_condition(x.K, 0.1, -x.V, 10, l, 0)
+        assert r[b, j] <= 16.0 * eps * kappa, (int(b), int(j), r[b, j], kappa)
     for b in (0, 255):
         x = insts[b]
         for j in (0, 13, 20, 40):
