@@ -181,9 +181,26 @@ static void launch_gemm(const GemmArgs& a, int zb, cudaStream_t st) {
   gemm_f64_kernel<BM, BN, BK, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, st>>>(a);
 }
 
+// Small products.  One SM sub-partition issues an FP64 warp instruction every
+// 64 cycles, so a CTA whose outputs sit in one or two warps is bound by that
+// issue rate, not by the launch: a 16 x 16 x 16 product on the 64-thread
+// 32-tile (3/4 of it padding) takes ~15 us.  Outputs of at most 16 x 16 take a
+// 16-tile with one output per thread (8 warps, two per sub-partition); outputs
+// of at most 32 x 32 take a 256-thread 32-tile with 2 x 2 per thread while the
+// batch leaves most SMs idle.  The K order per output is unchanged.
+constexpr int kSmallTileCtas = 2 * 152;
+
 cudaError_t gemm_f64(const GemmArgs& a, cudaStream_t st) {
   if (a.batch <= 0 || a.M <= 0 || a.N <= 0) return cudaSuccess;
   const int zb = a.batch < 65535 ? a.batch : 65535;   // grid z limit; the kernel loops
+  if (!a.tile && a.M <= 16 && a.N <= 16) {
+    launch_gemm<16, 16, 1, 1>(a, zb, st);                      // 256 threads, 1 output each
+    return cudaGetLastError();
+  }
+  if (!a.tile && a.M <= 32 && a.N <= 32 && a.batch < kSmallTileCtas) {
+    launch_gemm<32, 32, 2, 2>(a, zb, st);                      // 256 threads, 2x2 each
+    return cudaGetLastError();
+  }
   const int tile = a.tile ? a.tile : pick_tile(a.M, a.N);
   if (tile == 64) launch_gemm<64, 64, 4, 4>(a, zb, st);        // 256 threads, 4x4 each
   else if (tile == 48) launch_gemm<48, 48, 3, 3>(a, zb, st);   // 256 threads, 3x3 each

@@ -729,7 +729,11 @@ static size_t qrp_smem(int N) { return (size_t)N * (6 * sizeof(double) + sizeof(
 
 cudaError_t qrp_f64(const QrpArgs& a, cudaStream_t st) {
   if (a.batch <= 0 || a.N <= 0) return cudaSuccess;
-  if (a.N <= 32) return launch_qrp_fused<64, 2, 1>(a, st);
+  // N <= 32: four warps, so that the per-step FP64 work of every column
+  // spreads over all four sub-partitions (two threads per column would put
+  // all columns of N <= 16 in one warp)
+  if (a.N <= 16) return launch_qrp_fused<128, 8, 1>(a, st);
+  if (a.N <= 32) return launch_qrp_fused<128, 4, 1>(a, st);
   if (a.N <= 64) return launch_qrp_fused<128, 2, 2>(a, st);
   if (a.N <= 128) return launch_qrp_fused<256, 2, 4>(a, st);
   if (a.N <= 256) return launch_qrp_fused<512, 2, 8>(a, st);
