@@ -74,6 +74,9 @@ METRICS = {
 }
 
 
+FOLDS = {"sequential": 0, "tree": 1, "auto": 2}
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -91,6 +94,8 @@ def parse():
                    help="skip the extra un-pipelined step that times the dominant kernel alone")
     p.add_argument("--graphs", default="auto", choices=["auto", "on", "off"],
                    help="CUDA-graph mode of the handle (auto: on for the launch-bound workloads)")
+    p.add_argument("--fold", default="auto", choices=["auto", "tree", "sequential"],
+                   help="equal-time chain fold of the handle (auto: tree for small batches)")
     p.add_argument("--mixed-slices", type=int, default=8,
                    help="also time the mixed chain with this many BF16 slices (0: skip)")
     return p.parse_args()
@@ -344,7 +349,7 @@ def run_gpu(args, wl, rank, world):
     V = torch.tensor(V_np, device=dev)
     prec = 0 if args.precision == "fp64" else int(args.precision[-1])
     graphs = use_graphs(args, wl)
-    h = dq.Handle(chain_precision=prec, graphs=graphs)
+    h = dq.Handle(chain_precision=prec, graphs=graphs, fold=FOLDS[args.fold])
     h.bind_stream()
 
     def step():
@@ -445,7 +450,7 @@ def run_gpu(args, wl, rank, world):
     e2e = None
     if not args.no_e2e:
         import ctypes as C
-        he = dq.Handle(chain_precision=prec)
+        he = dq.Handle(chain_precision=prec, fold=FOLDS[args.fold])
         he.bind_stream()
         he.set_pointer_mode(True)
         Kh = torch.tensor(K_np).pin_memory()
@@ -515,7 +520,7 @@ def run_gpu(args, wl, rank, world):
         "vs_baseline": None, "dtype": "f64" if prec == 0 else f"bf16x{prec}+f64", "data": "synthetic",
         "config": {"workload": args.workload, "N": N, "M": M, "k": k, "beta": wl["beta"],
                    "U": wl["U"], "dtau": wl["dtau"], "instances_per_gpu": batch,
-                   "chain_precision": args.precision, "cuda_graphs": graphs,
+                   "chain_precision": args.precision, "cuda_graphs": graphs, "fold": args.fold,
                    "l2": "flushed between timed steps (256 MB write)"},
         "fp64_tflops": fl * batch * world * args.steps / (tot_ms / 1e3) / 1e12,
         "fp64_frac_of_peak": fl * batch * args.steps / (tot_ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
@@ -549,7 +554,7 @@ def run_gpu_other(args, wl, rank, world):
     name = args.workload
     prec = 0 if args.precision == "fp64" or name == "ragged_1024" else int(args.precision[-1])
     graphs = use_graphs(args, wl)
-    h = dq.Handle(chain_precision=prec, graphs=graphs)
+    h = dq.Handle(chain_precision=prec, graphs=graphs, fold=FOLDS[args.fold])
     h.bind_stream()
     extra = {}
     if name == "ragged_1024":
@@ -631,7 +636,7 @@ def run_gpu_other(args, wl, rank, world):
             "vs_baseline": None, "dtype": "f64" if prec == 0 else f"bf16x{prec}+f64",
             "data": "synthetic",
             "config": dict(workload=name, instances_per_gpu=batch, chain_precision=prec,
-                           cuda_graphs=graphs,
+                           cuda_graphs=graphs, fold=args.fold,
                            l2="flushed between timed steps (256 MB write)", **extra),
             "roofline": {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
                          "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,

@@ -118,6 +118,23 @@ dqmc_status dqmc_set_graph_mode(dqmc_handle h, int enable);
  * pads N least), 32, 48 or 64.  A tuning knob for the autotuner
  * (paper_2003_05286_gb300/tune.py); results do not depend on it. */
 dqmc_status dqmc_set_gemm_tile(dqmc_handle h, int tile);
+
+/* How the equal-time chain of dqmc_greens / dqmc_logdet is folded (FP64
+ * chain precision only; the other calls and the mixed precisions always run
+ * the sequential chain):
+ *   DQMC_FOLD_SEQUENTIAL  chunk after chunk, Eq. (stabmult) with the running
+ *                         U D X (one pivoted QR per chunk, in order);
+ *   DQMC_FOLD_TREE        all chunk products at once, each decomposed, then
+ *                         neighbours combined pairwise by Eq. (stabmult)
+ *                         (U_2 D_2 X_2)(U_1 D_1 X_1) = (U_2 u) d (x X_1),
+ *                         u d x = udt(D_2 (X_2 U_1) D_1), in ceil(log2(ceil(M/k)))
+ *                         levels: fewer dependent steps, more arithmetic;
+ *   DQMC_FOLD_AUTO        (default) tree when batch * ceil(M/k) <= 152 and
+ *                         ceil(M/k) >= 4, else sequential.
+ * Both give G and log det of the same definition; they differ by rounding.
+ * Invalid mode: DQMC_ERR_ARG. */
+typedef enum { DQMC_FOLD_SEQUENTIAL = 0, DQMC_FOLD_TREE = 1, DQMC_FOLD_AUTO = 2 } dqmc_fold_mode;
+dqmc_status dqmc_set_chain_fold(dqmc_handle h, int mode);
 /* Number of kernel launches issued by the most recent compute call. */
 long long dqmc_last_launch_count(dqmc_handle h);
 /* Bytes of device workspace the handle currently holds. */

@@ -35,7 +35,8 @@ def n_tau(M: int, k: int) -> int:
 class Handle:
     """Owns a dqmc_handle (workspace + settings) bound to the current device."""
 
-    def __init__(self, chain_precision: int = _abi.CHAIN_FP64, graphs: bool = False):
+    def __init__(self, chain_precision: int = _abi.CHAIN_FP64, graphs: bool = False,
+                 fold: int = _abi.FOLD_AUTO):
         self._lib = lib()
         h = C.c_void_p()
         _abi.check(self._lib.dqmc_create(C.byref(h)), "dqmc_create")
@@ -45,6 +46,12 @@ class Handle:
                        "dqmc_set_chain_precision")
         if graphs:
             self.set_graph_mode(True)
+        if fold != _abi.FOLD_AUTO:
+            self.set_chain_fold(fold)
+
+    def set_chain_fold(self, mode: int):
+        """Equal-time chain: FOLD_SEQUENTIAL, FOLD_TREE (pairwise Eq. (stabmult)) or FOLD_AUTO."""
+        _abi.check(self._lib.dqmc_set_chain_fold(self.h, int(mode)), "dqmc_set_chain_fold")
 
     def set_graph_mode(self, enable: bool):
         """Record calls as CUDA graphs and replay them for identical arguments."""

@@ -21,6 +21,7 @@ CHAIN_FP64 = 0
 CHAIN_BF16X3 = 3
 PTR_DEVICE = 0
 PTR_HOST = 1
+FOLD_SEQUENTIAL, FOLD_TREE, FOLD_AUTO = 0, 1, 2
 
 
 class DqmcInstance(C.Structure):
@@ -41,6 +42,7 @@ SIGNATURES = {
     "dqmc_set_pointer_mode": (_I, [_P, _I]),
     "dqmc_set_chain_precision": (_I, [_P, _I]),
     "dqmc_set_gemm_tile": (_I, [_P, _I]),
+    "dqmc_set_chain_fold": (_I, [_P, _I]),
     "dqmc_last_launch_count": (C.c_longlong, [_P]),
     "dqmc_workspace_bytes": (C.c_longlong, [_P]),
     "dqmc_status_string": (C.c_char_p, [_I]),

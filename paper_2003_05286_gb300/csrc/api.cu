@@ -37,6 +37,7 @@ struct dqmc_handle_s {
   dqmc_pointer_mode pmode = DQMC_PTR_DEVICE;
   dqmc_chain_prec prec = DQMC_CHAIN_FP64;
   int gemm_tile = 0;
+  int fold = DQMC_FOLD_AUTO;               // equal-time chain: sequential or tree
   char* ws = nullptr;
   size_t ws_bytes = 0;
   long long launches = 0;
@@ -520,6 +521,165 @@ dqmc_status run_chain_pair(dqmc_handle h, const ChainJob job[2], int N, int M, i
 }
 
 // ---------------------------------------------------------------------------
+// Tree-parallel fold of the forward chain.  The pairwise product of Eq.
+// (stabmult),
+//   (U_2 D_2 X_2)(U_1 D_1 X_1) = (U_2 u) d (x X_1),   u d x = udt(D_2 (X_2 U_1) D_1),
+// is associative, so the chunk products C_c = B_{ck+k}...B_{ck+1} can all be
+// formed at once, decomposed, and folded pairwise in ceil(log2(ceil(M/k)))
+// levels.  For a batch that leaves most SMs idle this replaces ceil(M/k)
+// dependent pivoted QRs (one CTA per instance each) by one QR per level, each
+// over batch x (chunks at that level) CTAs.
+//
+// The chunk count is padded to a power of two P0 with identity factors
+// (copied through the products, skipped by the level-0 QR), so that the pair
+// (2i, 2i+1) of instance b at a level of P factors per instance sits at
+// 2 (b P/2 + i): every operand of a level is a plain strided batch.  D_2
+// enters as a row scale of the product X_2 U_1 and D_1 as the QR's column
+// scale.  Its largest entry is that of the left half's scales, which is no
+// larger than those of the whole chain's D.
+// ---------------------------------------------------------------------------
+struct TreeWs {
+  double *Iden, *C0, *C1, *U[2], *D[2], *X[2], *W, *T;
+  int *perm, *len;
+  int P0 = 1;
+};
+
+int tree_width(int nc) {
+  int p = 1;
+  while (p < nc) p <<= 1;
+  return p;
+}
+
+void take_tree(Arena& ar, int batch, int N, int nc, TreeWs& w) {
+  const long long NN = (long long)N * N;
+  w.P0 = tree_width(nc);
+  const long long Q = (long long)batch * w.P0, H = Q / 2 > 0 ? Q / 2 : 1;
+  w.Iden = ar.take<double>(NN);
+  w.C0 = ar.take<double>(Q * NN);
+  w.C1 = ar.take<double>(Q * NN);
+  w.U[0] = ar.take<double>(Q * NN);
+  w.D[0] = ar.take<double>(Q * N);
+  w.X[0] = ar.take<double>(Q * NN);
+  w.U[1] = ar.take<double>(H * NN);
+  w.D[1] = ar.take<double>(H * N);
+  w.X[1] = ar.take<double>(H * NN);
+  w.W = ar.take<double>(Q * NN);
+  w.T = ar.take<double>(Q * NN);
+  w.perm = ar.take<int>(Q * N);
+  w.len = ar.take<int>(Q);
+}
+
+// Leaves B_M...B_1 = U D X of instance b at *U + b N^2, *D + b N, *X + b N^2.
+dqmc_status run_chain_tree(dqmc_handle h, int batch, int N, int M, int k, const double* E,
+                           const double* expV, long long sV, const TreeWs& w, int* status,
+                           const double** Uo, const double** Do, const double** Xo) {
+  cudaStream_t st = h->cur;
+  const long long NN = (long long)N * N;
+  const int nc = n_chunks(M, k), P0 = w.P0;
+  const int Q = batch * P0;
+  const double f2 = 2.0 * N * (double)N * N;
+  CK(set_identity(w.Iden, 0, N, 1, st));
+  CK(chunk_len(w.len, batch, P0, nc, k, M, st));
+  // a1: C_c for every chunk of every instance (identity for the padding)
+  double* bufs[2] = {w.C0, w.C1};
+  const double* prev = w.Iden;
+  long long sprev = 0;
+  for (int i = 0; i < k; ++i) {
+    GemmArgs g;
+    g.M = g.N = g.K = N;
+    g.batch = Q;
+    g.A = E; g.lda = N; g.sA = 0;
+    g.B = prev; g.ldb = N; g.sB = sprev;
+    g.C = bufs[i & 1]; g.ldc = N; g.sC = NN;
+    g.ms = expV + (long long)i * N; g.sms = sV; g.divS = P0; g.sms_inner = (long long)k * N;
+    g.lim = w.len; g.lim_at = i + 1;
+    g.tile = h->gemm_tile;
+    CKP(PC_CHAIN, f2 * Q, gemm_f64(g, st));
+    prev = bufs[i & 1];
+    sprev = NN;
+  }
+  // a3 on every chunk: C_c = U_c D_c X_c; the padding keeps U = X = 1, D = 1
+  CK(set_identity(w.U[0], NN, N, Q, st));
+  CK(set_const(w.D[0], (long long)Q * N, 1.0, st));
+  {
+    QrpArgs q;
+    q.N = N; q.batch = Q;
+    q.A = prev; q.sA = NN;
+    q.W = w.W; q.sW = NN;
+    q.U = w.U[0]; q.sU = NN;
+    q.D = w.D[0]; q.sD = N;
+    q.T = w.T; q.sT = NN;
+    q.perm = w.perm; q.sperm = N;
+    q.status = status; q.status_div = P0;
+    q.lim = w.len; q.lim_at = 1;
+    CKP(PC_QRP, 8.0 / 3.0 * N * N * (double)N * Q, qrp_f64(q, st));
+    GemmArgs g;                                       // X_c = T' P^T (identity for the padding)
+    g.M = g.N = g.K = N; g.batch = Q;
+    g.A = w.T; g.lda = N; g.sA = NN; g.upperA = 1;
+    g.B = w.Iden; g.ldb = N; g.sB = 0;
+    g.permB = w.perm; g.sperm = N;
+    g.C = w.X[0]; g.ldc = N; g.sC = NN;
+    g.lim = w.len; g.lim_at = 1;
+    CKP(PC_XUPD, (double)N * N * (double)N * Q, gemm_f64(g, st));
+  }
+  // levels: pair i of instance b = (left 2i+1, right 2i) -> i
+  int cur = 0;
+  for (int P = P0; P > 1; P >>= 1) {
+    const int np = P / 2, B2 = batch * np, nxt = cur ^ 1;
+    double* Y = w.C0;       // the chunk buffers are free after level 0
+    double* Uq = w.C1;
+    GemmArgs gy;                                      // Y = D_2 (X_2 U_1)
+    gy.M = gy.N = gy.K = N; gy.batch = B2;
+    gy.A = w.X[cur] + NN; gy.lda = N; gy.sA = 2 * NN;
+    gy.B = w.U[cur]; gy.ldb = N; gy.sB = 2 * NN;
+    gy.rs = w.D[cur] + N; gy.srs = 2LL * N;
+    gy.C = Y; gy.ldc = N; gy.sC = NN;
+    gy.tile = h->gemm_tile;
+    CKP(PC_OTHER, f2 * B2, gemm_f64(gy, st));
+    QrpArgs q;                                        // Y D_1 = u d x
+    q.N = N; q.batch = B2;
+    q.A = Y; q.sA = NN;
+    q.Din = w.D[cur]; q.sDin = 2LL * N;
+    q.W = w.W; q.sW = NN;
+    q.U = Uq; q.sU = NN;
+    q.D = w.D[nxt]; q.sD = N;
+    q.T = w.T; q.sT = NN;
+    q.perm = w.perm; q.sperm = N;
+    q.status = status; q.status_div = np;
+    CKP(PC_QRP, 8.0 / 3.0 * N * N * (double)N * B2, qrp_f64(q, st));
+    GemmArgs gu;                                      // U = U_2 u
+    gu.M = gu.N = gu.K = N; gu.batch = B2;
+    gu.A = w.U[cur] + NN; gu.lda = N; gu.sA = 2 * NN;
+    gu.B = Uq; gu.ldb = N; gu.sB = NN;
+    gu.C = w.U[nxt]; gu.ldc = N; gu.sC = NN;
+    gu.tile = h->gemm_tile;
+    CKP(PC_OTHER, f2 * B2, gemm_f64(gu, st));
+    GemmArgs gx;                                      // X = x X_1
+    gx.M = gx.N = gx.K = N; gx.batch = B2;
+    gx.A = w.T; gx.lda = N; gx.sA = NN; gx.upperA = 1;
+    gx.B = w.X[cur]; gx.ldb = N; gx.sB = 2 * NN;
+    gx.permB = w.perm; gx.sperm = N;
+    gx.C = w.X[nxt]; gx.ldc = N; gx.sC = NN;
+    CKP(PC_XUPD, (double)N * N * (double)N * B2, gemm_f64(gx, st));
+    cur = nxt;
+  }
+  *Uo = w.U[cur];
+  *Do = w.D[cur];
+  *Xo = w.X[cur];
+  return DQMC_OK;
+}
+
+// Tree fold for the equal-time chain: by setting, or (auto) when the level-0
+// QRs of all chunks of the batch fit in one wave of CTAs and the chain has at
+// least four chunks.
+bool use_tree(dqmc_handle h, int batch, int nc) {
+  if (h->prec != DQMC_CHAIN_FP64) return false;
+  if (h->fold == DQMC_FOLD_TREE) return nc > 1;
+  if (h->fold == DQMC_FOLD_SEQUENTIAL) return false;
+  return nc >= 4 && (long long)batch * nc <= 152;
+}
+
+// ---------------------------------------------------------------------------
 // a6-a7: G = [1 + U D X]^{-1} by Eq. (inversion_loh) and log|det(1 + U D X)|.
 //   Y = X^{-1} D_p^{-1}           (LU solve with diagonal right-hand side)
 //   Mx = Y + U D_m
@@ -697,6 +857,13 @@ dqmc_status dqmc_set_chain_precision(dqmc_handle h, dqmc_chain_prec prec) {
   return DQMC_OK;
 }
 
+dqmc_status dqmc_set_chain_fold(dqmc_handle h, int mode) {
+  if (!h || (mode != DQMC_FOLD_SEQUENTIAL && mode != DQMC_FOLD_TREE && mode != DQMC_FOLD_AUTO))
+    return DQMC_ERR_ARG;
+  h->fold = mode;
+  return DQMC_OK;
+}
+
 dqmc_status dqmc_set_gemm_tile(dqmc_handle h, int tile) {
   if (!h || (tile != 0 && tile != 32 && tile != 48 && tile != 64)) return DQMC_ERR_ARG;
   h->gemm_tile = tile;
@@ -745,6 +912,7 @@ static dqmc_status graph_call(dqmc_handle h, GraphKey key, F&& body) {
   if (!h->graphs || h->pmode == DQMC_PTR_HOST || h->prof) return body();
   key.add((unsigned long long)h->prec);
   key.add((unsigned long long)h->gemm_tile);
+  key.add((unsigned long long)h->fold);
   key.add((unsigned long long)pipeline_enabled() * 16 + (unsigned long long)pipeline_jobs(h->prec != DQMC_CHAIN_FP64));
   key.addp(h->ws);
   key.addp(h->stream);
@@ -827,7 +995,12 @@ static dqmc_status greens_impl(dqmc_handle h, int batch, int N, int M, const dou
   const bool host = h->pmode == DQMC_PTR_HOST;
   const long long NN = (long long)N * N;
   const int nc = n_chunks(M, k);
-  const long long Mp = (long long)(nc + 1) * k;   // padded slice stride of exp(V)
+  const bool tree = use_tree(h, batch, nc);
+  // padded slice stride of exp(V): one spare chunk, and for the tree every
+  // padding chunk of its power-of-two width
+  const int mp_chunks = tree && tree_width(nc) > nc + 1 ? tree_width(nc) : nc + 1;
+  const long long Mp = (long long)mp_chunks * k;
+  TreeWs tw;
 
   auto layout = [&](Arena& ar, ExpmWs& ew, ChainWs& cw, LohWs& lw, double*& E, double*& expV,
                     double*& U, double*& D, double*& X0, double*& X1, int*& st, HostIO& io,
@@ -835,11 +1008,16 @@ static dqmc_status greens_impl(dqmc_handle h, int batch, int N, int M, const dou
     take_expm(ar, N, ew);
     E = ew.t0;
     expV = ar.take<double>(Mp * N * batch);
-    U = ar.take<double>(NN * batch);
-    D = ar.take<double>((long long)N * batch);
-    X0 = ar.take<double>(NN * batch);
-    X1 = ar.take<double>(NN * batch);
-    take_chain(ar, batch, N, cw);
+    if (tree) {
+      take_tree(ar, batch, N, nc, tw);
+      U = D = X0 = X1 = nullptr;
+    } else {
+      U = ar.take<double>(NN * batch);
+      D = ar.take<double>((long long)N * batch);
+      X0 = ar.take<double>(NN * batch);
+      X1 = ar.take<double>(NN * batch);
+      take_chain(ar, batch, N, cw);
+    }
     if (h->prec != DQMC_CHAIN_FP64) take_ozaki(ar, batch, N, (int)h->prec, cw);
     take_loh(ar, batch, N, lw);
     st = ar.take<int>(batch);
@@ -886,47 +1064,53 @@ static dqmc_status greens_impl(dqmc_handle h, int batch, int N, int M, const dou
   // exp(V_l) for every slice, padded to Mp slices per instance
   CK(exp_pad(Vd, expV, batch, M, (int)Mp, N, 1.0, stout, st));
 
-  if (cw.oz_s > 0) CK(split_E(E, N, 0, cw, st));   // E slices, shared by all instances
-  CK(set_identity(U, NN, N, batch, st));
-  CK(set_const(D, (long long)N * batch, 1.0, st));
-  CK(set_identity(X0, NN, N, batch, st));
-  Slots s;
-  s.U = U; s.slotU = 0; s.instU = NN;
-  s.D = D; s.slotD = 0; s.instD = N;
-  s.X = X0; s.slotX = 0; s.instX = NN;
-  s.X2 = X1;
-  const int nj = pipeline_jobs(cw.oz_s > 0);
-  if (batch >= 4 * nj && pipeline_enabled()) {
-    // nj sub-batches on nj streams, product phases staggered so that the QRs
-    // of some sub-batches run while the others multiply
-    ChainJob J[4];
-    long long o = 0;
-    for (int q = 0; q < nj; ++q) {
-      const int nb = batch / nj + (q < batch % nj ? 1 : 0);
-      J[q].dir = +1;
-      J[q].batch = nb;
-      J[q].expV = expV + o * Mp * N;
-      J[q].sV = Mp * N;
-      J[q].s = s;
-      J[q].s.U += o * NN; J[q].s.D += o * N; J[q].s.X += o * NN; J[q].s.X2 += o * NN;
-      J[q].w = cw;
-      J[q].w.C0 += o * NN; J[q].w.C1 += o * NN; J[q].w.W += o * NN; J[q].w.T += o * NN;
-      J[q].w.perm += o * N;
-      if (cw.oz_s > 0) {
-        J[q].w.ozB += o * cw.oz_s * (long long)cw.oz_PK * cw.oz_PK;
-        J[q].w.ozeB += o * cw.oz_PK;
-        J[q].w.ozT += o * cw.oz_s * (long long)cw.oz_P128 * cw.oz_PK;
-        J[q].w.ozeT += o * cw.oz_P128;
-      }
-      J[q].status = stout + o;
-      o += nb;
-    }
-    CKS(run_chain_multi(h, J, nj, N, M, k, E));
+  if (tree) {
+    const double *Ut, *Dt, *Xt;
+    CKS(run_chain_tree(h, batch, N, M, k, E, expV, Mp * N, tw, stout, &Ut, &Dt, &Xt));
+    CKS(run_loh(h, batch, N, Ut, NN, Dt, N, Xt, NN, Gout, ldout, sgout, stout, lw));
   } else {
-    CKS(run_chain(h, +1, batch, N, M, k, E, expV, Mp * N, s, cw, stout));
+    if (cw.oz_s > 0) CK(split_E(E, N, 0, cw, st));   // E slices, shared by all instances
+    CK(set_identity(U, NN, N, batch, st));
+    CK(set_const(D, (long long)N * batch, 1.0, st));
+    CK(set_identity(X0, NN, N, batch, st));
+    Slots s;
+    s.U = U; s.slotU = 0; s.instU = NN;
+    s.D = D; s.slotD = 0; s.instD = N;
+    s.X = X0; s.slotX = 0; s.instX = NN;
+    s.X2 = X1;
+    const int nj = pipeline_jobs(cw.oz_s > 0);
+    if (batch >= 4 * nj && pipeline_enabled()) {
+      // nj sub-batches on nj streams, product phases staggered so that the QRs
+      // of some sub-batches run while the others multiply
+      ChainJob J[4];
+      long long o = 0;
+      for (int q = 0; q < nj; ++q) {
+        const int nb = batch / nj + (q < batch % nj ? 1 : 0);
+        J[q].dir = +1;
+        J[q].batch = nb;
+        J[q].expV = expV + o * Mp * N;
+        J[q].sV = Mp * N;
+        J[q].s = s;
+        J[q].s.U += o * NN; J[q].s.D += o * N; J[q].s.X += o * NN; J[q].s.X2 += o * NN;
+        J[q].w = cw;
+        J[q].w.C0 += o * NN; J[q].w.C1 += o * NN; J[q].w.W += o * NN; J[q].w.T += o * NN;
+        J[q].w.perm += o * N;
+        if (cw.oz_s > 0) {
+          J[q].w.ozB += o * cw.oz_s * (long long)cw.oz_PK * cw.oz_PK;
+          J[q].w.ozeB += o * cw.oz_PK;
+          J[q].w.ozT += o * cw.oz_s * (long long)cw.oz_P128 * cw.oz_PK;
+          J[q].w.ozeT += o * cw.oz_P128;
+        }
+        J[q].status = stout + o;
+        o += nb;
+      }
+      CKS(run_chain_multi(h, J, nj, N, M, k, E));
+    } else {
+      CKS(run_chain(h, +1, batch, N, M, k, E, expV, Mp * N, s, cw, stout));
+    }
+    const double* Xf = (nc & 1) ? X1 : X0;
+    CKS(run_loh(h, batch, N, U, NN, D, N, Xf, NN, Gout, ldout, sgout, stout, lw));
   }
-  const double* Xf = (nc & 1) ? X1 : X0;
-  CKS(run_loh(h, batch, N, U, NN, D, N, Xf, NN, Gout, ldout, sgout, stout, lw));
 
   if (host) {
     bool ok = true;

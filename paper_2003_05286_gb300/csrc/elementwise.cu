@@ -86,6 +86,23 @@ __global__ void dsplit_kernel(const double* D, long long sD, int n, int batch, d
   }
 }
 
+// len[b*P0 + c] = number of slices in chunk c of a chain of M slices cut
+// every k (0 for the padding chunks c >= ceil(M/k))
+__global__ void chunk_len_kernel(int* len, long long total, int P0, int nc, int k, int M) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(e % P0);
+    len[e] = c < nc - 1 ? k : (c == nc - 1 ? M - (nc - 1) * k : 0);
+  }
+}
+
+cudaError_t chunk_len(int* len, int batch, int P0, int nc, int k, int M, cudaStream_t st) {
+  const long long total = (long long)batch * P0;
+  if (total <= 0) return cudaSuccess;
+  chunk_len_kernel<<<nblocks(total), TPB, 0, st>>>(len, total, P0, nc, k, M);
+  return cudaGetLastError();
+}
+
 cudaError_t dsplit_vec(const double* D, long long sD, int n, int batch, double* out, int mode,
                        cudaStream_t st) {
   long long total = (long long)n * batch;

@@ -36,12 +36,13 @@ def test_ragged_small_mixed(dq):
                                          1000 + i))
     Gs, ld, sg, st = dq.greens_ragged([(_dev(x.K), x.dtau, _dev(x.V), x.k) for x in insts])
     assert int((st != 0).sum()) == 0
+    seq = dq.Handle(fold=0)     # the ragged chains fold sequentially
     for i, x in enumerate(insts):
         Go, ldo, so = od.greens(x.K, x.dtau, x.V, x.k)
         assert np.abs(Gs[i].cpu().numpy() - Go).max() <= GTOL * max(1.0, np.abs(Go).max()), i
         assert abs(float(ld[i]) - ldo) <= 1e-9 * max(1.0, abs(ldo))
         assert int(sg[i]) == so
-        G1, ld1, _, _ = dq.greens(_dev(x.K), x.dtau, _dev(x.V), x.k)
+        G1, ld1, _, _ = dq.greens(_dev(x.K), x.dtau, _dev(x.V), x.k, handle=seq)
         assert torch.equal(G1, Gs[i]) and float(ld1) == float(ld[i])
 
 
@@ -57,10 +58,11 @@ def test_ragged_shared_K_batches(dq):
     items = [(Ks[int(round(x.N ** 0.5))], x.dtau, _dev(x.V), x.k) for x in insts]
     Gs, ld, sg, st = dq.greens_ragged(items)
     assert int((st != 0).sum()) == 0
+    seq = dq.Handle(fold=0)     # the ragged chains fold sequentially
     for i, x in enumerate(insts):
         Go, ldo, so = od.greens(x.K, x.dtau, x.V, x.k)
         assert np.abs(Gs[i].cpu().numpy() - Go).max() <= GTOL * max(1.0, np.abs(Go).max()), i
-        G1, ld1, _, _ = dq.greens(_dev(x.K), x.dtau, _dev(x.V), x.k)
+        G1, ld1, _, _ = dq.greens(_dev(x.K), x.dtau, _dev(x.V), x.k, handle=seq)
         assert torch.equal(G1, Gs[i]) and float(ld1) == float(ld[i]), i
 
 
