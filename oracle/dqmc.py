@@ -228,6 +228,20 @@ def inv_sum_loh(UL, DL, XL, UR, DR, XR):
     return ((XRinv @ u2) * d2[None, :]) @ (x2 @ UL.T)
 
 
+def inv_sum(UL, DL, XL, UR, DR, XR):
+    """[U_L D_L X_L + U_R D_R X_R]^{-1} by Eq. (inversion_tdgf), without the D+/D- split.
+
+    U_L D_L X_L + U_R D_R X_R = U_L (D_L X_L X_R^{-1} + U_L^T U_R D_R) X_R; the
+    bracket is decomposed (u d x) and the result is (x X_R)^{-1} d^{-1} (U_L u)^T
+    (the printed d^{-1} inside the inverse read as d, as in Eq. (inversion)).
+    The bracket adds the scales of D_L and D_R, which Sec. 6.2.1 shows to lose
+    accuracy at tau ~ beta/2."""
+    N = DL.shape[0]
+    inner = DL[:, None] * (XL @ sla.solve(XR, np.eye(N))) + (UL.T @ UR) * DR[None, :]
+    u, d, x = udt(inner)
+    return sla.solve(x @ XR, (1.0 / d)[:, None] * (UL @ u).T)
+
+
 def _displaced_chains(K, dtau, V, k, l1: int, l2: int):
     """U_L D_L X_L of B_{l2+1}^{-1}...B_{l1}^{-1} and U_R D_R X_R of
     B_{l2}...B_1 B_M...B_{l1+1} (Sec. 6), tau_1 = l1*dtau >= tau_2 = l2*dtau."""
@@ -250,14 +264,16 @@ def displaced_condition(K, dtau, V, k, l1: int, l2: int = 0) -> float:
     return float(np.linalg.cond(mid))
 
 
-def greens_displaced(K, dtau, V, k, l1: int, l2: int = 0):
+def greens_displaced(K, dtau, V, k, l1: int, l2: int = 0, scheme: str = "loh"):
     """G(tau_1, tau_2) for tau_1 = l1*dtau > tau_2 = l2*dtau (Sec. 6).
 
     G(tau_1,tau_2) = [B_{l2+1}^{-1}...B_{l1}^{-1} + B_{l2}...B_1 B_M...B_{l1+1}]^{-1};
     the left chain grows by B_{l1}^{-1} first, the right chain by B_{l1+1}
-    first; both are stabilised every k slices and combined by inv_sum_loh.
-    l1 == l2 gives G_{l1+1} (the tau_1 -> tau_2^+ limit)."""
-    return inv_sum_loh(*_displaced_chains(K, dtau, V, k, l1, l2))
+    first; both are stabilised every k slices and combined by inv_sum_loh
+    (scheme "loh", Eq. (inversion_tdgf_loh)) or inv_sum (scheme "sum",
+    Eq. (inversion_tdgf)).  l1 == l2 gives G_{l1+1} (the tau_1 -> tau_2^+ limit)."""
+    chains = _displaced_chains(K, dtau, V, k, l1, l2)
+    return inv_sum(*chains) if scheme == "sum" else inv_sum_loh(*chains)
 
 
 def greens_displaced_back(K, dtau, V, k, l1: int, l2: int):

@@ -322,3 +322,41 @@ def test_particle_hole_displaced(beta):
         Gm = od.greens_displaced(K, 0.1, -V, 10, l, 0)
         Gp = od.greens_displaced_back(K, 0.1, V, 10, 0, l)
         assert np.abs(Gm + lam[:, None] * Gp.T * lam[None, :]).max() < 1e-10
+
+
+# ---------------------------------------------------------------------------
+# inv_sum (Eq. (inversion_tdgf)): right where the chain is well conditioned,
+# inaccurate at tau ~ beta/2 (the paper's Fig. 6 finding for QR)
+# ---------------------------------------------------------------------------
+
+def test_inv_sum_naive_small_beta():
+    K, V = _hubbard(4, 4.0, 1.0, seed=17)
+    M = V.shape[0]
+    EK = od.hopping_exponential(K, 0.1)
+    Bs = [od.slice_matrix(EK, V[l]) for l in range(M)]
+    P = np.eye(16)
+    for B in Bs:
+        P = B @ P
+    G1 = np.linalg.inv(np.eye(16) + P)
+    for l in (0, 3, 5, 9, 10):
+        Bt = np.eye(16)
+        for B in Bs[:l]:
+            Bt = B @ Bt
+        for scheme in ("sum", "loh"):
+            G = od.greens_displaced(K, 0.1, V, 3, l, 0, scheme=scheme)
+            assert np.abs(G - Bt @ G1).max() < 1e-12, (l, scheme)
+
+
+@pytest.mark.parametrize("l1,sum_ok", [(0, True), (120, False), (400, True)])
+def test_inv_sum_degrades_mid_tau(l1, sum_ok):
+    """beta = 40, U = 0: Loh's split stays at rounding level for every tau; the
+    plain sum loses many digits in between (1e-6 at tau = 12)."""
+    K = di.chain_hopping(8)
+    M = 400
+    c = np.random.default_rng(1).uniform(-0.3, 0.3, M)
+    V = np.repeat(c[:, None], 8, axis=1)
+    Gx = ex.closed_form_displaced(K, 40.0, 0.1 * l1, c.sum(), c[:l1].sum())
+    e_loh = np.abs(od.greens_displaced(K, 0.1, V, 10, l1, 0) - Gx).max()
+    e_sum = np.abs(od.greens_displaced(K, 0.1, V, 10, l1, 0, scheme="sum") - Gx).max()
+    assert e_loh < 1e-12
+    assert (e_sum < 1e-12) if sum_ok else (e_sum > 1e-9)
