@@ -135,6 +135,21 @@ dqmc_status dqmc_set_gemm_tile(dqmc_handle h, int tile);
  * Invalid mode: DQMC_ERR_ARG. */
 typedef enum { DQMC_FOLD_SEQUENTIAL = 0, DQMC_FOLD_TREE = 1, DQMC_FOLD_AUTO = 2 } dqmc_fold_mode;
 dqmc_status dqmc_set_chain_fold(dqmc_handle h, int mode);
+
+/* Inversion scheme (Sec. 5.1 and Sec. 6.1):
+ *   DQMC_INV_LOH    (default) the D+/D- split of Loh et al.: Eq. (inversion_loh)
+ *                   for G and log det, Eq. (inversion_tdgf_loh) for G(tau,0);
+ *   DQMC_INV_PLAIN  the schemes without the split: Eq. (inversion) for G and
+ *                   log det of dqmc_greens, dqmc_logdet and dqmc_greens_ragged,
+ *                   and Eq. (inversion_tdgf) for G(tau,0) of the time-displaced
+ *                   calls, its two terms first brought to U D X form with an
+ *                   orthogonal left factor (one pivoted QR each).  G(tau,tau),
+ *                   G(0,tau), the gradient and dqmc_greens_noalloc keep Loh.
+ * PLAIN exists to reproduce the paper's comparison: for G(tau,0) it loses
+ * accuracy at tau ~ beta/2 (Sec. 6.2.1), while both equal-time schemes agree
+ * (Sec. 5.2).  Invalid scheme: DQMC_ERR_ARG. */
+typedef enum { DQMC_INV_LOH = 0, DQMC_INV_PLAIN = 1 } dqmc_inversion_scheme;
+dqmc_status dqmc_set_inversion_scheme(dqmc_handle h, int scheme);
 /* Number of kernel launches issued by the most recent compute call. */
 long long dqmc_last_launch_count(dqmc_handle h);
 /* Bytes of device workspace the handle currently holds. */

@@ -36,7 +36,7 @@ class Handle:
     """Owns a dqmc_handle (workspace + settings) bound to the current device."""
 
     def __init__(self, chain_precision: int = _abi.CHAIN_FP64, graphs: bool = False,
-                 fold: int = _abi.FOLD_AUTO):
+                 fold: int = _abi.FOLD_AUTO, inversion: int = _abi.INV_LOH):
         self._lib = lib()
         h = C.c_void_p()
         _abi.check(self._lib.dqmc_create(C.byref(h)), "dqmc_create")
@@ -48,6 +48,13 @@ class Handle:
             self.set_graph_mode(True)
         if fold != _abi.FOLD_AUTO:
             self.set_chain_fold(fold)
+        if inversion != _abi.INV_LOH:
+            self.set_inversion_scheme(inversion)
+
+    def set_inversion_scheme(self, scheme: int):
+        """INV_LOH (D+/D- split, default) or INV_PLAIN (Eq. (inversion) / Eq. (inversion_tdgf))."""
+        _abi.check(self._lib.dqmc_set_inversion_scheme(self.h, int(scheme)),
+                   "dqmc_set_inversion_scheme")
 
     def set_chain_fold(self, mode: int):
         """Equal-time chain: FOLD_SEQUENTIAL, FOLD_TREE (pairwise Eq. (stabmult)) or FOLD_AUTO."""

@@ -22,6 +22,7 @@ CHAIN_BF16X3 = 3
 PTR_DEVICE = 0
 PTR_HOST = 1
 FOLD_SEQUENTIAL, FOLD_TREE, FOLD_AUTO = 0, 1, 2
+INV_LOH, INV_PLAIN = 0, 1
 
 
 class DqmcInstance(C.Structure):
@@ -43,6 +44,7 @@ SIGNATURES = {
     "dqmc_set_chain_precision": (_I, [_P, _I]),
     "dqmc_set_gemm_tile": (_I, [_P, _I]),
     "dqmc_set_chain_fold": (_I, [_P, _I]),
+    "dqmc_set_inversion_scheme": (_I, [_P, _I]),
     "dqmc_last_launch_count": (C.c_longlong, [_P]),
     "dqmc_workspace_bytes": (C.c_longlong, [_P]),
     "dqmc_status_string": (C.c_char_p, [_I]),

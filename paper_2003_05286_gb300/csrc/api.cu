@@ -38,6 +38,7 @@ struct dqmc_handle_s {
   dqmc_chain_prec prec = DQMC_CHAIN_FP64;
   int gemm_tile = 0;
   int fold = DQMC_FOLD_AUTO;               // equal-time chain: sequential or tree
+  int inv = DQMC_INV_LOH;                  // inversion scheme of G and G(tau,0)
   char* ws = nullptr;
   size_t ws_bytes = 0;
   long long launches = 0;
@@ -745,6 +746,123 @@ dqmc_status run_loh(dqmc_handle h, int batch, int N, const double* U, long long 
 }
 
 // ---------------------------------------------------------------------------
+// a6-a7 by Eq. (inversion) instead (DQMC_INV_PLAIN):
+//   1 + U D X = U (U^T X^{-1} + D) X,   U^T X^{-1} + D = u d x   (pivoted QR),
+//   G = (x X)^{-1} d^{-1} (U u)^T,
+//   log|det(1 + U D X)| = sum log d (|det U| = |det u| = |det x X| = 1),
+//   sign = sign det(U u) * sign det(x X).
+// ---------------------------------------------------------------------------
+struct PlainWs {
+  double *Iden, *C, *u, *d, *dinv, *W, *T, *xX, *P, *Y, *Wlu;
+  int *perm, *s1, *s2;
+};
+
+void take_plain(Arena& ar, int batch, int N, PlainWs& w) {
+  const long long NN = (long long)N * N;
+  w.Iden = ar.take<double>(NN);
+  w.C = ar.take<double>(NN * batch);
+  w.u = ar.take<double>(NN * batch);
+  w.d = ar.take<double>((long long)N * batch);
+  w.dinv = ar.take<double>((long long)N * batch);
+  w.W = ar.take<double>(NN * batch);
+  w.T = ar.take<double>(NN * batch);
+  w.xX = ar.take<double>(NN * batch);
+  w.P = ar.take<double>(NN * batch);
+  w.Y = ar.take<double>(NN * batch);
+  w.Wlu = ar.take<double>(2 * NN * batch);
+  w.perm = ar.take<int>((long long)N * batch);
+  w.s1 = ar.take<int>(batch);
+  w.s2 = ar.take<int>(batch);
+}
+
+dqmc_status run_one_plus(dqmc_handle h, int batch, int N, const double* U, long long sU,
+                         const double* D, long long sD, const double* X, long long sX, double* G,
+                         double* logdet, int* sign, int* status, const PlainWs& w) {
+  cudaStream_t st = h->cur;
+  const long long NN = (long long)N * N;
+  const double f2 = 2.0 * N * (double)N * N * batch;
+  CK(set_identity(w.Iden, 0, N, 1, st));
+  LuArgs l1;                                          // C = U^T X^{-1}  (X^T C^T = U)
+  l1.N = N; l1.nrhs = N; l1.batch = batch;
+  l1.A = X; l1.sA = sX; l1.transA = 1;
+  l1.R = U; l1.sR = sU; l1.ldr = N;
+  l1.Z = w.C; l1.sZ = NN; l1.ldz = N; l1.transZ = 1;
+  l1.W = w.Wlu; l1.sW = 2 * NN;
+  l1.status = status;
+  CKP(PC_LU, lu_flops(N, N) * batch, lu_solve_f64(l1, st));
+  Axpby2Args ax;                                      // C + D on the diagonal
+  ax.N = N; ax.batch = batch;
+  ax.A = w.C; ax.sA = NN;
+  ax.B = w.Iden; ax.sB = 0;
+  ax.cb = D; ax.cb_mode = 5; ax.scb = sD;
+  ax.C = w.C; ax.sC = NN;
+  CK(axpby2(ax, st));
+  QrpArgs q;                                          // = u d x
+  q.N = N; q.batch = batch;
+  q.A = w.C; q.sA = NN;
+  q.W = w.W; q.sW = NN;
+  q.U = w.u; q.sU = NN;
+  q.D = w.d; q.sD = N;
+  q.T = w.T; q.sT = NN;
+  q.perm = w.perm; q.sperm = N;
+  q.status = status;
+  CKP(PC_QRP, 8.0 / 3.0 * N * N * (double)N * batch, qrp_f64(q, st));
+  GemmArgs gx;                                        // x X
+  gx.M = gx.N = gx.K = N; gx.batch = batch;
+  gx.A = w.T; gx.lda = N; gx.sA = NN; gx.upperA = 1;
+  gx.B = X; gx.ldb = N; gx.sB = sX;
+  gx.permB = w.perm; gx.sperm = N;
+  gx.C = w.xX; gx.ldc = N; gx.sC = NN;
+  CKP(PC_OTHER, f2 / 2, gemm_f64(gx, st));
+  GemmArgs gp;                                        // P = U u
+  gp.M = gp.N = gp.K = N; gp.batch = batch;
+  gp.A = U; gp.lda = N; gp.sA = sU;
+  gp.B = w.u; gp.ldb = N; gp.sB = NN;
+  gp.C = w.P; gp.ldc = N; gp.sC = NN;
+  CKP(PC_OTHER, f2, gemm_f64(gp, st));
+  CK(dsplit_vec(w.d, N, N, batch, w.dinv, 4, st));
+  GemmArgs gy = gp;                                   // Y = U u d^{-1}
+  gy.C = w.Y;
+  gy.cs = w.dinv; gy.scs = N;
+  CKP(PC_OTHER, f2, gemm_f64(gy, st));
+  LuArgs l2;                                          // (x X) G = Y^T
+  l2.N = N; l2.batch = batch;
+  l2.A = w.xX; l2.sA = NN;
+  if (G) {
+    l2.nrhs = N;
+    l2.R = w.Y; l2.sR = NN; l2.ldr = N; l2.transR = 1;
+    l2.Z = G; l2.sZ = NN; l2.ldz = N;
+  } else {
+    l2.nrhs = 0;
+    l2.Z = w.C; l2.sZ = NN; l2.ldz = N;
+  }
+  l2.W = w.Wlu; l2.sW = 2 * NN;
+  l2.sign = w.s1;
+  l2.status = status;
+  CKP(PC_LU, lu_flops(N, l2.nrhs) * batch, lu_solve_f64(l2, st));
+  LuArgs l3;                                          // sign det(U u)
+  l3.N = N; l3.nrhs = 0; l3.batch = batch;
+  l3.A = w.P; l3.sA = NN;
+  l3.Z = w.C; l3.sZ = NN; l3.ldz = N;
+  l3.W = w.Wlu; l3.sW = 2 * NN;
+  l3.sign = w.s2;
+  l3.status = status;
+  CKP(PC_LU, lu_flops(N, 0) * batch, lu_solve_f64(l3, st));
+  CK(finish_logdet(w.d, N, N, batch, nullptr, w.s1, w.s2, logdet, sign, status, st, 1));
+  return DQMC_OK;
+}
+
+// The equal-time inversion the handle's scheme selects.
+dqmc_status run_inversion(dqmc_handle h, int batch, int N, const double* U, long long sU,
+                          const double* D, long long sD, const double* X, long long sX, double* G,
+                          double* logdet, int* sign, int* status, const LohWs& lw,
+                          const PlainWs& pw) {
+  if (h->inv == DQMC_INV_PLAIN)
+    return run_one_plus(h, batch, N, U, sU, D, sD, X, sX, G, logdet, sign, status, pw);
+  return run_loh(h, batch, N, U, sU, D, sD, X, sX, G, logdet, sign, status, lw);
+}
+
+// ---------------------------------------------------------------------------
 // Argument checks and pointer-mode staging
 // ---------------------------------------------------------------------------
 dqmc_status check_common(dqmc_handle h, int batch, int N, int M, const double* K, double dtau,
@@ -857,6 +975,12 @@ dqmc_status dqmc_set_chain_precision(dqmc_handle h, dqmc_chain_prec prec) {
   return DQMC_OK;
 }
 
+dqmc_status dqmc_set_inversion_scheme(dqmc_handle h, int scheme) {
+  if (!h || (scheme != DQMC_INV_LOH && scheme != DQMC_INV_PLAIN)) return DQMC_ERR_ARG;
+  h->inv = scheme;
+  return DQMC_OK;
+}
+
 dqmc_status dqmc_set_chain_fold(dqmc_handle h, int mode) {
   if (!h || (mode != DQMC_FOLD_SEQUENTIAL && mode != DQMC_FOLD_TREE && mode != DQMC_FOLD_AUTO))
     return DQMC_ERR_ARG;
@@ -913,6 +1037,7 @@ static dqmc_status graph_call(dqmc_handle h, GraphKey key, F&& body) {
   key.add((unsigned long long)h->prec);
   key.add((unsigned long long)h->gemm_tile);
   key.add((unsigned long long)h->fold);
+  key.add((unsigned long long)h->inv);
   key.add((unsigned long long)pipeline_enabled() * 16 + (unsigned long long)pipeline_jobs(h->prec != DQMC_CHAIN_FP64));
   key.addp(h->ws);
   key.addp(h->stream);
@@ -1001,6 +1126,7 @@ static dqmc_status greens_impl(dqmc_handle h, int batch, int N, int M, const dou
   const int mp_chunks = tree && tree_width(nc) > nc + 1 ? tree_width(nc) : nc + 1;
   const long long Mp = (long long)mp_chunks * k;
   TreeWs tw;
+  PlainWs pw;
 
   auto layout = [&](Arena& ar, ExpmWs& ew, ChainWs& cw, LohWs& lw, double*& E, double*& expV,
                     double*& U, double*& D, double*& X0, double*& X1, int*& st, HostIO& io,
@@ -1020,6 +1146,7 @@ static dqmc_status greens_impl(dqmc_handle h, int batch, int N, int M, const dou
     }
     if (h->prec != DQMC_CHAIN_FP64) take_ozaki(ar, batch, N, (int)h->prec, cw);
     take_loh(ar, batch, N, lw);
+    if (h->inv == DQMC_INV_PLAIN) take_plain(ar, batch, N, pw);
     st = ar.take<int>(batch);
     if (host) {
       io.K = ar.take<double>(NN);
@@ -1067,7 +1194,7 @@ static dqmc_status greens_impl(dqmc_handle h, int batch, int N, int M, const dou
   if (tree) {
     const double *Ut, *Dt, *Xt;
     CKS(run_chain_tree(h, batch, N, M, k, E, expV, Mp * N, tw, stout, &Ut, &Dt, &Xt));
-    CKS(run_loh(h, batch, N, Ut, NN, Dt, N, Xt, NN, Gout, ldout, sgout, stout, lw));
+    CKS(run_inversion(h, batch, N, Ut, NN, Dt, N, Xt, NN, Gout, ldout, sgout, stout, lw, pw));
   } else {
     if (cw.oz_s > 0) CK(split_E(E, N, 0, cw, st));   // E slices, shared by all instances
     CK(set_identity(U, NN, N, batch, st));
@@ -1109,7 +1236,7 @@ static dqmc_status greens_impl(dqmc_handle h, int batch, int N, int M, const dou
       CKS(run_chain(h, +1, batch, N, M, k, E, expV, Mp * N, s, cw, stout));
     }
     const double* Xf = (nc & 1) ? X1 : X0;
-    CKS(run_loh(h, batch, N, U, NN, D, N, Xf, NN, Gout, ldout, sgout, stout, lw));
+    CKS(run_inversion(h, batch, N, U, NN, D, N, Xf, NN, Gout, ldout, sgout, stout, lw, pw));
   }
 
   if (host) {
@@ -1390,6 +1517,124 @@ dqmc_status run_two_stack_inversion(dqmc_handle h, int Q, int N, int nt, const S
   return DQMC_OK;
 }
 
+// G(tau,0) by Eq. (inversion_tdgf) (DQMC_INV_PLAIN), the scheme Sec. 6.2.1
+// shows to lose accuracy at tau ~ beta/2.  Both terms of
+//   G(tau,0) = [B(tau,0)^{-1} + B(beta,tau)]^{-1} = [U_L D_L X_L + U_R D_R X_R]^{-1}
+// are first brought to U D X form with an orthogonal left factor from the
+// stacks, by one pivoted QR each:
+//   B(tau,0)^{-1} = X_F^{-1} a^{-1} U_F^T,   udt(X_F^{-1} a^{-1}) = u_L d_L x_L,
+//                   U_L = u_L, D_L = d_L, X_L = x_L U_F^T;
+//   B(beta,tau)   = T_b^T b U_b^T,           udt(T_b^T b) = u_R d_R x_R,
+//                   U_R = u_R, D_R = d_R, X_R = x_R U_b^T;
+// then, without splitting the scales,
+//   D_L X_L X_R^{-1} + U_L^T U_R D_R = u d x,   G(tau,0) = (x X_R)^{-1} d^{-1} (U_L u)^T.
+struct SumWs {
+  double *ones, *Xi, *ainv, *uL, *dL, *XL, *TbT, *uR, *dR, *XR, *C1, *C2, *u, *d, *dinv, *xXR,
+      *Y, *W, *T, *Wlu;
+  int* perm;
+};
+
+void take_sum(Arena& ar, long long Q, int N, SumWs& w) {
+  const long long NN = (long long)N * N;
+  w.ones = ar.take<double>(N);
+  for (double** m : {&w.Xi, &w.uL, &w.XL, &w.TbT, &w.uR, &w.XR, &w.C1, &w.C2, &w.u, &w.xXR,
+                     &w.Y, &w.W, &w.T})
+    *m = ar.take<double>(Q * NN);
+  for (double** v : {&w.ainv, &w.dL, &w.dR, &w.d, &w.dinv}) *v = ar.take<double>(Q * N);
+  w.Wlu = ar.take<double>(Q * 2 * NN);
+  w.perm = ar.take<int>(Q * N);
+}
+
+dqmc_status run_inv_sum_t0(dqmc_handle h, int Q, int N, int nt, const StackWs& s,
+                           const SumWs& w, double* Gt0, int* status) {
+  cudaStream_t st = h->cur;
+  const long long NN = (long long)N * N;
+  const double f2 = 2.0 * N * (double)N * N * Q;
+  auto qr = [&](const double* A, const double* Din, double* U, double* D) {
+    QrpArgs q;
+    q.N = N; q.batch = Q;
+    q.A = A; q.sA = NN;
+    q.Din = Din; q.sDin = N;
+    q.W = w.W; q.sW = NN;
+    q.U = U; q.sU = NN;
+    q.D = D; q.sD = N;
+    q.T = w.T; q.sT = NN;
+    q.perm = w.perm; q.sperm = N;
+    q.status = status; q.status_div = nt;
+    return qrp_f64(q, st);
+  };
+  // x P^T V^T for the last QR's T' and perm: rows of V^T gathered by perm
+  auto x_times_Vt = [&](const double* Vm, double* out) {
+    GemmArgs g;
+    g.M = g.N = g.K = N; g.batch = Q;
+    g.A = w.T; g.lda = N; g.sA = NN; g.upperA = 1;
+    g.B = Vm; g.ldb = N; g.sB = NN; g.transB = 1;
+    g.permB = w.perm; g.sperm = N;
+    g.C = out; g.ldc = N; g.sC = NN;
+    return gemm_f64(g, st);
+  };
+  CK(set_const(w.ones, N, 1.0, st));
+  LuArgs li;                                          // X_F^{-1}
+  li.N = N; li.nrhs = N; li.batch = Q;
+  li.A = s.XF; li.sA = NN;
+  li.Rdiag = w.ones; li.sRdiag = 0;
+  li.Z = w.Xi; li.sZ = NN; li.ldz = N;
+  li.W = w.Wlu; li.sW = 2 * NN;
+  li.status = status; li.status_div = nt;
+  CKP(PC_LU, lu_flops(N, N) * Q, lu_solve_f64(li, st));
+  CK(dsplit_vec(s.DF, N, N, Q, w.ainv, 4, st));
+  CKP(PC_QRP, 8.0 / 3.0 * N * N * (double)N * Q, qr(w.Xi, w.ainv, w.uL, w.dL));
+  CKP(PC_OTHER, f2 / 2, x_times_Vt(s.UF, w.XL));      // X_L = x_L U_F^T
+  CK(copy_mats(s.Tb, NN, w.TbT, NN, N, Q, 1, 1, 1, st));
+  CKP(PC_QRP, 8.0 / 3.0 * N * N * (double)N * Q, qr(w.TbT, s.Db, w.uR, w.dR));
+  CKP(PC_OTHER, f2 / 2, x_times_Vt(s.Ub, w.XR));      // X_R = x_R U_b^T
+  LuArgs lr;                                          // C2 = X_L X_R^{-1}
+  lr.N = N; lr.nrhs = N; lr.batch = Q;
+  lr.A = w.XR; lr.sA = NN; lr.transA = 1;
+  lr.R = w.XL; lr.sR = NN; lr.ldr = N; lr.transR = 1;
+  lr.Z = w.C2; lr.sZ = NN; lr.ldz = N; lr.transZ = 1;
+  lr.W = w.Wlu; lr.sW = 2 * NN;
+  lr.status = status; lr.status_div = nt;
+  CKP(PC_LU, lu_flops(N, N) * Q, lu_solve_f64(lr, st));
+  GemmArgs g1;                                        // C1 = U_L^T U_R
+  g1.M = g1.N = g1.K = N; g1.batch = Q;
+  g1.A = w.uL; g1.lda = N; g1.sA = NN; g1.transA = 1;
+  g1.B = w.uR; g1.ldb = N; g1.sB = NN;
+  g1.C = w.C1; g1.ldc = N; g1.sC = NN;
+  CKP(PC_OTHER, f2, gemm_f64(g1, st));
+  Axpby2Args ax;                                      // D_L C2 + C1 D_R
+  ax.N = N; ax.batch = Q;
+  ax.A = w.C2; ax.sA = NN; ax.ra = w.dL; ax.ra_mode = 5; ax.sra = N;
+  ax.B = w.C1; ax.sB = NN; ax.cb = w.dR; ax.cb_mode = 5; ax.scb = N;
+  ax.C = w.C2; ax.sC = NN;
+  CK(axpby2(ax, st));
+  CKP(PC_QRP, 8.0 / 3.0 * N * N * (double)N * Q, qr(w.C2, nullptr, w.u, w.d));
+  GemmArgs gx;                                        // x X_R
+  gx.M = gx.N = gx.K = N; gx.batch = Q;
+  gx.A = w.T; gx.lda = N; gx.sA = NN; gx.upperA = 1;
+  gx.B = w.XR; gx.ldb = N; gx.sB = NN;
+  gx.permB = w.perm; gx.sperm = N;
+  gx.C = w.xXR; gx.ldc = N; gx.sC = NN;
+  CKP(PC_OTHER, f2 / 2, gemm_f64(gx, st));
+  CK(dsplit_vec(w.d, N, N, Q, w.dinv, 4, st));
+  GemmArgs gy;                                        // Y = U_L u d^{-1}
+  gy.M = gy.N = gy.K = N; gy.batch = Q;
+  gy.A = w.uL; gy.lda = N; gy.sA = NN;
+  gy.B = w.u; gy.ldb = N; gy.sB = NN;
+  gy.cs = w.dinv; gy.scs = N;
+  gy.C = w.Y; gy.ldc = N; gy.sC = NN;
+  CKP(PC_OTHER, f2, gemm_f64(gy, st));
+  LuArgs lg;                                          // (x X_R) G = Y^T
+  lg.N = N; lg.nrhs = N; lg.batch = Q;
+  lg.A = w.xXR; lg.sA = NN;
+  lg.R = w.Y; lg.sR = NN; lg.ldr = N; lg.transR = 1;
+  lg.Z = Gt0; lg.sZ = NN; lg.ldz = N;
+  lg.W = w.Wlu; lg.sW = 2 * NN;
+  lg.status = status; lg.status_div = nt;
+  CKP(PC_LU, lu_flops(N, N) * Q, lu_solve_f64(lg, st));
+  return DQMC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1429,9 +1674,10 @@ static dqmc_status tdisplaced_impl(dqmc_handle h, int batch, int N, int M, const
   const long long Mp = (long long)(nc + 1) * k;
   const long long Q = (long long)batch * nt;
   if (Q > (1LL << 30)) return DQMC_ERR_ARG;
-  const int ncols = (Gtt || G0t ? N : 0) + (Gt0 ? N : 0);
+  const bool plain_t0 = h->inv == DQMC_INV_PLAIN && Gt0 != nullptr;
+  const int ncols = (Gtt || G0t ? N : 0) + (Gt0 && !plain_t0 ? N : 0);
 
-  ExpmWs ew; ChainWs cw, cw2; StackWs sw; MidWs mw; HostIO io;
+  ExpmWs ew; ChainWs cw, cw2; StackWs sw; MidWs mw; HostIO io; SumWs sumw;
   double *expV, *Gttd = nullptr, *Gt0d = nullptr, *G0td = nullptr;
   int* stat;
   auto layout = [&](Arena& ar) {
@@ -1445,6 +1691,7 @@ static dqmc_status tdisplaced_impl(dqmc_handle h, int batch, int N, int M, const
     }
     take_stacks(ar, batch, N, nt, sw);
     take_mid(ar, Q, N, ncols > 0 ? ncols : N, mw);
+    if (plain_t0) take_sum(ar, Q, N, sumw);
     stat = ar.take<int>(batch);
     if (host) {
       io.K = ar.take<double>(NN);
@@ -1478,7 +1725,9 @@ static dqmc_status tdisplaced_impl(dqmc_handle h, int batch, int N, int M, const
   CKS(run_expm(h, Kd, N, dtau, -1.0, ew, stout, batch));
   CK(exp_pad(Vd, expV, batch, M, (int)Mp, N, 1.0, stout, st));
   CKS(run_stacks(h, batch, N, M, k, ew.t0, expV, Mp * N, sw, cw, cw2, stout));
-  CKS(run_two_stack_inversion(h, (int)Q, N, nt, sw, mw, Gtto, Gt0o, G0to, stout));
+  CKS(run_two_stack_inversion(h, (int)Q, N, nt, sw, mw, Gtto, plain_t0 ? nullptr : Gt0o, G0to,
+                              stout));
+  if (plain_t0) CKS(run_inv_sum_t0(h, (int)Q, N, nt, sw, sumw, Gt0o, stout));
   if (host) {
     bool ok = true;
     if (Gtt) ok &= cudaMemcpyAsync(Gtt, Gttd, Q * NN * sizeof(double), cudaMemcpyDeviceToHost, st) == cudaSuccess;
@@ -1658,7 +1907,7 @@ dqmc_status dqmc_greens_ragged(dqmc_handle h, int batch, const dqmc_instance* de
   }
   // ---- workspace: one region per group ----------------------------------------
   struct GroupWs {
-    ExpmWs ew; ChainWs cw; LohWs lw;
+    ExpmWs ew; ChainWs cw; LohWs lw; PlainWs pw;
     double *expV, *U, *D, *X0, *X1, *G, *ld;
     int *sg, *st, *Mb, *gidx;
     long long *offV, *offG;
@@ -1679,6 +1928,7 @@ dqmc_status dqmc_greens_ragged(dqmc_handle h, int batch, const dqmc_instance* de
       w.X1 = ar.take<double>(NN * nb);
       take_chain(ar, nb, N, w.cw);
       take_loh(ar, nb, N, w.lw);
+      if (h->inv == DQMC_INV_PLAIN) take_plain(ar, nb, N, w.pw);
       w.G = ar.take<double>(NN * nb);
       w.ld = ar.take<double>(nb);
       w.sg = ar.take<int>(nb);
@@ -1743,7 +1993,8 @@ dqmc_status dqmc_greens_ragged(dqmc_handle h, int batch, const dqmc_instance* de
       sl.X2 = w.X1;
       CKS(run_chain(h, +1, nb, N, g.Mmax, k, w.ew.t0, w.expV, Mp * N, sl, w.cw, w.st, w.Mb));
       const double* Xf = (ncmax & 1) ? w.X1 : w.X0;
-      CKS(run_loh(h, nb, N, w.U, NN, w.D, N, Xf, NN, G_pool ? w.G : nullptr, w.ld, w.sg, w.st, w.lw));
+      CKS(run_inversion(h, nb, N, w.U, NN, w.D, N, Xf, NN, G_pool ? w.G : nullptr, w.ld, w.sg,
+                        w.st, w.lw, w.pw));
       if (G_pool) CK(scatter_mats(w.G, w.offG, N, nb, G_pool, st));
       CK(scatter_scalars(w.gidx, nb, w.ld, w.sg, w.st, logdet, sign, status, st));
       return DQMC_OK;

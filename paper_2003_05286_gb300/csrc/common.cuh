@@ -106,7 +106,7 @@ struct Axpby2Args {
   const double* B = nullptr; long long sB = 0;
   double* C = nullptr; long long sC = 0;
   // each scale: pointer to a D vector + mode (0: none, 1: 1/max(D,1),
-  // 2: min(D,1), 3: max(D,1))
+  // 2: min(D,1), 3: max(D,1), 4: 1/D, 5: D)
   const double* ra = nullptr; int ra_mode = 0; long long sra = 0;
   const double* ca = nullptr; int ca_mode = 0; long long sca = 0;
   const double* rb = nullptr; int rb_mode = 0; long long srb = 0;
@@ -124,11 +124,11 @@ cudaError_t exp_pad(const double* V, double* out, int batch, int M, int Mp, int 
 cudaError_t one_minus_diag(const double* G, long long sG, int N, int batch,
                            double* y, long long sy, int ydiv, long long sy_outer,
                            cudaStream_t st);
-// logdet_b = sum_i log max(D_bi, 1) + logabsdet_b ; sign_b = s1_b * s2_b;
-// flags non-finite results.
+// logdet_b = sum_i log max(D_bi, 1) + logabsdet_b (plain: sum_i log D_bi + ...);
+// sign_b = s1_b * s2_b; flags non-finite results.
 cudaError_t finish_logdet(const double* D, long long sD, int N, int batch, const double* lad,
                           const int* s1, const int* s2, double* logdet, int* sign,
-                          int* status, cudaStream_t st);
+                          int* status, cudaStream_t st, int plain = 0);
 // Copy of strided N x N matrices (out_b = in_b), optional transpose.
 cudaError_t copy_mats(const double* in, long long sin, double* out, long long sout,
                       int N, int batch, int transpose, int divin, int divout,

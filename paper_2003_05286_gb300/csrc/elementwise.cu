@@ -22,6 +22,7 @@ __device__ __forceinline__ double dmode(double d, int mode) {
     case 2: return fmin(d, 1.0);         // D_m
     case 3: return fmax(d, 1.0);         // D_p
     case 4: return 1.0 / d;              // D^{-1}
+    case 5: return d;                    // D
     default: return 1.0;
   }
 }
@@ -161,13 +162,16 @@ cudaError_t one_minus_diag(const double* G, long long sG, int N, int batch, doub
 // one warp per instance: logdet = sum_i log max(D_i, 1) + lad
 __global__ void finish_logdet_kernel(const double* D, long long sD, int N, int batch, const double* lad,
                                      const int* s1, const int* s2, double* logdet, int* sign,
-                                     int* status) {
+                                     int* status, int plain) {
   const int lane = threadIdx.x & 31;
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   for (int b = w; b < batch; b += nw) {
     double s = 0.0;
-    for (int i = lane; i < N; i += 32) s += log(fmax(D[(long long)b * sD + i], 1.0));
+    for (int i = lane; i < N; i += 32) {
+      const double d = D[(long long)b * sD + i];
+      s += log(plain ? d : fmax(d, 1.0));
+    }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
     if (lane == 0) {
@@ -182,11 +186,12 @@ __global__ void finish_logdet_kernel(const double* D, long long sD, int N, int b
 
 cudaError_t finish_logdet(const double* D, long long sD, int N, int batch, const double* lad, const int* s1,
                           const int* s2, double* logdet, int* sign, int* status,
-                          cudaStream_t st) {
+                          cudaStream_t st, int plain) {
   if (batch <= 0) return cudaSuccess;
   int blocks = (batch * 32 + TPB - 1) / TPB;
   if (blocks > 4096) blocks = 4096;
-  finish_logdet_kernel<<<blocks, TPB, 0, st>>>(D, sD, N, batch, lad, s1, s2, logdet, sign, status);
+  finish_logdet_kernel<<<blocks, TPB, 0, st>>>(D, sD, N, batch, lad, s1, s2, logdet, sign, status,
+                                               plain);
   return cudaGetLastError();
 }
 
