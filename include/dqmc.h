@@ -213,6 +213,20 @@ dqmc_status dqmc_greens_tdisplaced_ex(dqmc_handle h, int batch, int N, int M,
                                       int k, double* Gtt, double* Gt0, double* G0t,
                                       int* status);
 
+/* The same three functions at every tau_l = l dtau, l = 0..M (not only on the
+ * k-grid):  Gtt, Gt0, G0t [batch*(M+1)*N*N], entry (b, l, i, m) at
+ * ((b*(M+1) + l)*N + i)*N + m, each may be NULL.  Between grid points the
+ * values are propagated from the stable grid values by at most k-1 one-slice
+ * products (the mixture of stabilised and naive products of Sec. 4.1):
+ *   G(tau_l, 0) = B_l G(tau_{l-1}, 0),   G(0, tau_l) = G(0, tau_{l-1}) B_l^{-1},
+ *   G_{l+1} = B_l G_l B_l^{-1}            (Eqs. (tdgf_propagate), (etgf_tau)).
+ * Values on the grid equal those of dqmc_greens_tdisplaced_ex bitwise.
+ * Arguments, errors and status as in dqmc_greens_tdisplaced. */
+dqmc_status dqmc_greens_tdisplaced_all(dqmc_handle h, int batch, int N, int M,
+                                       const double* K, double dtau, const double* V,
+                                       int k, double* Gtt, double* Gt0, double* G0t,
+                                       int* status);
+
 /* Gradient dV[(b*M + (l-1))*N + i] = d log|det(1 + B_M...B_1)| / dV_l(i)
  * = 1 - G_l(i,i) for every slice l (derived from Eqs. (etgf), (etgf_tau)):
  * G_l at the k-grid from the two stacks, then G_{l+1} = B_l G_l B_l^{-1}

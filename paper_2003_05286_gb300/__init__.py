@@ -18,7 +18,8 @@ import torch
 
 from . import _abi
 
-__all__ = ["Handle", "greens", "logdet", "greens_tdisplaced", "logdet_grad", "greens_ragged",
+__all__ = ["Handle", "greens", "logdet", "greens_tdisplaced", "greens_tdisplaced_all",
+           "logdet_grad", "greens_ragged",
            "greens_tdisplaced_ragged", "logdet_grad_ragged", "selftest_wait_timeout", "LogDet",
            "n_tau", "lib"]
 
@@ -201,6 +202,27 @@ def greens_tdisplaced(K, dtau: float, V, k: int, *, handle: Handle | None = None
                                                  int(k), _ptr(Gtt), _ptr(Gt0), _ptr(st)),
                    "dqmc_greens_tdisplaced")
         res = (Gtt, Gt0)
+    if sq:
+        return tuple(x[0] if x is not None else None for x in res) + (st[0],)
+    return res + (st,)
+
+
+def greens_tdisplaced_all(K, dtau: float, V, k: int, *, handle: Handle | None = None,
+                          want_tt: bool = True, want_t0: bool = True, want_0t: bool = True):
+    """G(tau_l, tau_l), G(tau_l, 0), G(0, tau_l) for every l = 0..M (dqmc_greens_tdisplaced_all):
+    tensors (B, M+1, N, N) (None where not wanted) and status."""
+    K, V, sq = _prep(K, V)
+    B, M, N = V.shape
+    h = _handle(handle)
+
+    def out(want):
+        return torch.empty((B, M + 1, N, N), dtype=torch.float64, device=V.device) if want else None
+    Gtt, Gt0, G0t = out(want_tt), out(want_t0), out(want_0t)
+    st = torch.empty(B, dtype=torch.int32, device=V.device)
+    _abi.check(h._lib.dqmc_greens_tdisplaced_all(h.h, B, N, M, _ptr(K), float(dtau), _ptr(V),
+                                                 int(k), _ptr(Gtt), _ptr(Gt0), _ptr(G0t),
+                                                 _ptr(st)), "dqmc_greens_tdisplaced_all")
+    res = (Gtt, Gt0, G0t)
     if sq:
         return tuple(x[0] if x is not None else None for x in res) + (st[0],)
     return res + (st,)

@@ -16,6 +16,7 @@
 //   a11 gradient 1 - G_l(i,i): checkpoints from the stacks, wrapping in between.
 #include <cstdlib>
 #include <cstring>
+#include <utility>
 #include <vector>
 
 #include "common.cuh"
@@ -1641,7 +1642,18 @@ extern "C" {
 
 static dqmc_status tdisplaced_impl(dqmc_handle h, int batch, int N, int M, const double* K,
                                    double dtau, const double* V, int k, double* Gtt, double* Gt0,
-                                   double* G0t, int* status);
+                                   double* G0t, int* status, bool all_tau = false);
+
+dqmc_status dqmc_greens_tdisplaced_all(dqmc_handle h, int batch, int N, int M, const double* K,
+                                       double dtau, const double* V, int k, double* Gtt,
+                                       double* Gt0, double* G0t, int* status) {
+  if (!h) return DQMC_ERR_ARG;
+  GraphKey key = key_of(5, batch, N, M, K, dtau, V, k);
+  key.addp(Gtt); key.addp(Gt0); key.addp(G0t); key.addp(status);
+  return graph_call(h, key, [&] {
+    return tdisplaced_impl(h, batch, N, M, K, dtau, V, k, Gtt, Gt0, G0t, status, true);
+  });
+}
 
 dqmc_status dqmc_greens_tdisplaced_ex(dqmc_handle h, int batch, int N, int M, const double* K,
                                       double dtau, const double* V, int k, double* Gtt,
@@ -1662,7 +1674,7 @@ dqmc_status dqmc_greens_tdisplaced(dqmc_handle h, int batch, int N, int M, const
 
 static dqmc_status tdisplaced_impl(dqmc_handle h, int batch, int N, int M, const double* K,
                                    double dtau, const double* V, int k, double* Gtt, double* Gt0,
-                                   double* G0t, int* status) {
+                                   double* G0t, int* status, bool all_tau) {
   CKS(check_common(h, batch, N, M, K, dtau, V, k));
   if (h->prec != DQMC_CHAIN_FP64 && N > 256) return DQMC_ERR_UNSUPPORTED;
   h->launches = 0;
@@ -1676,13 +1688,24 @@ static dqmc_status tdisplaced_impl(dqmc_handle h, int batch, int N, int M, const
   if (Q > (1LL << 30)) return DQMC_ERR_ARG;
   const bool plain_t0 = h->inv == DQMC_INV_PLAIN && Gt0 != nullptr;
   const int ncols = (Gtt || G0t ? N : 0) + (Gt0 && !plain_t0 ? N : 0);
+  // outputs per instance: the k-grid, or (all_tau) every tau_l = l dtau, l = 0..M
+  const long long outlen = all_tau ? (long long)(M + 1) * NN : (long long)nt * NN;
 
-  ExpmWs ew; ChainWs cw, cw2; StackWs sw; MidWs mw; HostIO io; SumWs sumw;
-  double *expV, *Gttd = nullptr, *Gt0d = nullptr, *G0td = nullptr;
+  ExpmWs ew, ewi; ChainWs cw, cw2; StackWs sw; MidWs mw; HostIO io; SumWs sumw;
+  double *expV, *expmV = nullptr, *Gttd = nullptr, *Gt0d = nullptr, *G0td = nullptr;
+  double *gq[3] = {nullptr, nullptr, nullptr}, *gtmp = nullptr;   // grid values (all_tau)
   int* stat;
   auto layout = [&](Arena& ar) {
     take_expm(ar, N, ew);
     expV = ar.take<double>(Mp * N * batch);
+    if (all_tau) {
+      take_expm(ar, N, ewi);
+      if (Gtt || G0t) expmV = ar.take<double>(Mp * N * batch);
+      if (Gtt) gq[0] = ar.take<double>(Q * NN);
+      if (Gt0) gq[1] = ar.take<double>(Q * NN);
+      if (G0t) gq[2] = ar.take<double>(Q * NN);
+      gtmp = ar.take<double>(Q * NN);
+    }
     take_chain(ar, batch, N, cw);
     take_chain(ar, batch, N, cw2);
     if (h->prec != DQMC_CHAIN_FP64) {
@@ -1696,9 +1719,9 @@ static dqmc_status tdisplaced_impl(dqmc_handle h, int batch, int N, int M, const
     if (host) {
       io.K = ar.take<double>(NN);
       io.V = ar.take<double>((long long)M * N * batch);
-      Gttd = Gtt ? ar.take<double>(Q * NN) : nullptr;
-      Gt0d = Gt0 ? ar.take<double>(Q * NN) : nullptr;
-      G0td = G0t ? ar.take<double>(Q * NN) : nullptr;
+      Gttd = Gtt ? ar.take<double>(batch * outlen) : nullptr;
+      Gt0d = Gt0 ? ar.take<double>(batch * outlen) : nullptr;
+      G0td = G0t ? ar.take<double>(batch * outlen) : nullptr;
     }
   };
   Arena measure;
@@ -1725,14 +1748,63 @@ static dqmc_status tdisplaced_impl(dqmc_handle h, int batch, int N, int M, const
   CKS(run_expm(h, Kd, N, dtau, -1.0, ew, stout, batch));
   CK(exp_pad(Vd, expV, batch, M, (int)Mp, N, 1.0, stout, st));
   CKS(run_stacks(h, batch, N, M, k, ew.t0, expV, Mp * N, sw, cw, cw2, stout));
-  CKS(run_two_stack_inversion(h, (int)Q, N, nt, sw, mw, Gtto, plain_t0 ? nullptr : Gt0o, G0to,
-                              stout));
-  if (plain_t0) CKS(run_inv_sum_t0(h, (int)Q, N, nt, sw, sumw, Gt0o, stout));
+  double* out[3] = {Gtto, Gt0o, G0to};
+  if (all_tau)
+    for (int i = 0; i < 3; ++i) out[i] = gq[i];
+  CKS(run_two_stack_inversion(h, (int)Q, N, nt, sw, mw, out[0], plain_t0 ? nullptr : out[1],
+                              out[2], stout));
+  if (plain_t0) CKS(run_inv_sum_t0(h, (int)Q, N, nt, sw, sumw, out[1], stout));
+  if (all_tau) {
+    // tau between grid points: k - 1 one-slice steps from every grid value,
+    //   G(tau_l, 0) = B_l G(tau_{l-1}, 0),  G(0, tau_l) = G(0, tau_{l-1}) B_l^{-1},
+    //   G_{l+1} = B_l G_l B_l^{-1}   (Eqs. (tdgf_propagate), (etgf_tau)),
+    // with B_l = E e^{V_l} and B_l^{-1} = e^{-V_l} E^{-1}.
+    CKS(run_expm(h, Kd, N, dtau, +1.0, ewi, nullptr, batch));
+    if (expmV) CK(exp_pad(Vd, expmV, batch, M, (int)Mp, N, -1.0, nullptr, st));
+    double* dst[3] = {Gtto, Gt0o, G0to};
+    const double f2 = 2.0 * N * (double)N * N * Q;
+    for (int s = 0; s < k; ++s) {
+      for (int i = 0; i < 3; ++i)
+        if (out[i]) CK(scatter_tau(out[i], Q, nt, N, k, M, s, dst[i], st));
+      if (s == k - 1) break;
+      GemmArgs left;                                   // E diag(e^{V_l}) G
+      left.M = left.N = left.K = N; left.batch = (int)Q;
+      left.A = ew.t0; left.lda = N; left.sA = 0;
+      left.ldb = N; left.sB = NN;
+      left.ms = expV + (long long)s * N; left.sms = Mp * N;
+      left.sms_inner = (long long)k * N; left.divS = nt;
+      left.ldc = N; left.sC = NN;
+      GemmArgs right;                                  // G diag(e^{-V_l}) E^{-1}
+      right.M = right.N = right.K = N; right.batch = (int)Q;
+      right.lda = N; right.sA = NN;
+      right.B = ewi.t0; right.ldb = N; right.sB = 0;
+      right.ms = expmV + (long long)s * N; right.sms = Mp * N;
+      right.sms_inner = (long long)k * N; right.divS = nt;
+      right.ldc = N; right.sC = NN;
+      if (out[1]) {
+        left.B = out[1]; left.C = gtmp;
+        CKP(PC_OTHER, f2, gemm_f64(left, st));
+        std::swap(out[1], gtmp);
+      }
+      if (out[2]) {
+        right.A = out[2]; right.C = gtmp;
+        CKP(PC_OTHER, f2, gemm_f64(right, st));
+        std::swap(out[2], gtmp);
+      }
+      if (out[0]) {
+        left.B = out[0]; left.C = gtmp;
+        CKP(PC_OTHER, f2, gemm_f64(left, st));
+        right.A = gtmp; right.C = out[0];
+        CKP(PC_OTHER, f2, gemm_f64(right, st));
+      }
+    }
+  }
   if (host) {
     bool ok = true;
-    if (Gtt) ok &= cudaMemcpyAsync(Gtt, Gttd, Q * NN * sizeof(double), cudaMemcpyDeviceToHost, st) == cudaSuccess;
-    if (Gt0) ok &= cudaMemcpyAsync(Gt0, Gt0d, Q * NN * sizeof(double), cudaMemcpyDeviceToHost, st) == cudaSuccess;
-    if (G0t) ok &= cudaMemcpyAsync(G0t, G0td, Q * NN * sizeof(double), cudaMemcpyDeviceToHost, st) == cudaSuccess;
+    const size_t ob = (size_t)batch * outlen * sizeof(double);
+    if (Gtt) ok &= cudaMemcpyAsync(Gtt, Gttd, ob, cudaMemcpyDeviceToHost, st) == cudaSuccess;
+    if (Gt0) ok &= cudaMemcpyAsync(Gt0, Gt0d, ob, cudaMemcpyDeviceToHost, st) == cudaSuccess;
+    if (G0t) ok &= cudaMemcpyAsync(G0t, G0td, ob, cudaMemcpyDeviceToHost, st) == cudaSuccess;
     if (status) ok &= cudaMemcpyAsync(status, stat, batch * sizeof(int), cudaMemcpyDeviceToHost, st) == cudaSuccess;
     ok &= cudaStreamSynchronize(st) == cudaSuccess;
     if (!ok) return DQMC_ERR_CUDA;

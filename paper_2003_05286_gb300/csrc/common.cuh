@@ -140,6 +140,8 @@ cudaError_t scale_rows(double* A, long long sA, const double* v, long long sv, i
 cudaError_t set_identity(double* A, long long sA, int N, int batch, cudaStream_t st);
 cudaError_t set_const(double* x, long long n, double v, cudaStream_t st);
 cudaError_t chunk_len(int* len, int batch, int P0, int nc, int k, int M, cudaStream_t st);
+cudaError_t scatter_tau(const double* cur, long long Q, int nt, int N, int k, int M, int s,
+                        double* out, cudaStream_t st);
 // 1-norm based scaling for the matrix exponential: s = max(0, ceil(log2(||dtau K||_1 / 0.5))),
 // scale = sgn * dtau / 2^s; writes s (int) and scale (double) to device memory;
 // also writes the symmetry defect flag into *asym (1 if K != K^T).

@@ -104,6 +104,39 @@ cudaError_t chunk_len(int* len, int batch, int P0, int nc, int k, int M, cudaStr
   return cudaGetLastError();
 }
 
+// Slot j of instance b (q = b*nt + j) after s one-slice steps from the grid
+// point tau_j = jk holds the value at l = jk + s: copied to out[b][l] while
+// l stays below the next grid point and l < M; slot nt-1 (tau = M dtau) is
+// copied at s = 0 only.
+__global__ void scatter_tau_kernel(const double* cur, long long Q, int nt, int N, int k, int M,
+                                   int s, double* out) {
+  const long long NN = (long long)N * N, total = Q * NN;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long q = e / NN, ij = e % NN;
+    const int j = (int)(q % nt);
+    const long long b = q / nt;
+    int l;
+    if (j == nt - 1) {
+      if (s != 0) continue;
+      l = M;
+    } else {
+      l = j * k + s;
+      const int end = (j + 1) * k < M ? (j + 1) * k : M;
+      if (l >= end) continue;
+    }
+    out[(b * (M + 1) + l) * NN + ij] = cur[e];
+  }
+}
+
+cudaError_t scatter_tau(const double* cur, long long Q, int nt, int N, int k, int M, int s,
+                        double* out, cudaStream_t st) {
+  const long long total = Q * N * (long long)N;
+  if (total <= 0) return cudaSuccess;
+  scatter_tau_kernel<<<nblocks(total), TPB, 0, st>>>(cur, Q, nt, N, k, M, s, out);
+  return cudaGetLastError();
+}
+
 cudaError_t dsplit_vec(const double* D, long long sD, int n, int batch, double* out, int mode,
                        cudaStream_t st) {
   long long total = (long long)n * batch;

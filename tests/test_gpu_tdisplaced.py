@@ -215,3 +215,43 @@ def test_g0t_full_size(dq):
             l = min(10 * j, 400)
             O = od.greens_displaced_back(x.K, 0.1, x.V, 10, 0, l)
             assert _cmp(G0t[b, j].cpu().numpy(), O) <= GTOL, (b, j)
+
+
+# ---------------------------------------------------------------------------
+# every tau_l = l dtau (dqmc_greens_tdisplaced_all)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("L,beta,k,seed", [(3, 2.3, 5, 1), (4, 4.0, 10, 2), (2, 3.7, 7, 3)])
+def test_all_tau_vs_oracle(dq, L, beta, k, seed):
+    """All three functions at every l (short last chunks included); grid values
+    bitwise equal to the k-grid call."""
+    inst = di.hubbard_instance(L, 4.0, 0.1, beta, k, seed)
+    K, V = _dev(inst.K), _dev(inst.V)
+    Att, At0, A0t, st = dq.greens_tdisplaced_all(K, 0.1, V, k)
+    assert int(st) == 0 and Att.shape == (inst.M + 1, inst.N, inst.N)
+    Gtt, Gt0, G0t, _ = dq.greens_tdisplaced(K, 0.1, V, k, want_0t=True)
+    for j, l in enumerate(od.tau_grid(inst.M, k)):
+        assert torch.equal(Att[l], Gtt[j]) and torch.equal(At0[l], Gt0[j]) and torch.equal(A0t[l], G0t[j])
+    Att, At0, A0t = (x.cpu().numpy() for x in (Att, At0, A0t))
+    for l in range(inst.M + 1):
+        Ott = od.greens(inst.K, 0.1, inst.V, k, l=l + 1)[0]
+        Ot0 = od.greens_displaced(inst.K, 0.1, inst.V, k, l, 0)
+        O0t = od.greens_displaced_back(inst.K, 0.1, inst.V, k, 0, l)
+        assert _cmp(Att[l], Ott) <= GTOL, ("tt", l)
+        assert _cmp(At0[l], Ot0) <= GTOL, ("t0", l)
+        assert _cmp(A0t[l], O0t) <= GTOL, ("0t", l)
+
+
+def test_all_tau_full_size_sampled(dq):
+    """8x8, U=4, beta=40, k=10, 256 instances: G(tau_l, 0) and G(0, tau_l) at every
+    l = 0..400; instances 0 and 255 against the oracle at off-grid l."""
+    insts = [di.batch_n64_tdisplaced(i) for i in range(256)]
+    K = _dev(insts[0].K)
+    V = _dev(np.stack([x.V for x in insts]))
+    _, At0, A0t, st = dq.greens_tdisplaced_all(K, 0.1, V, 10, want_tt=False)
+    assert int((st != 0).sum()) == 0 and At0.shape == (256, 401, 64, 64)
+    for b in (0, 255):
+        x = insts[b]
+        for l in (1, 9, 137, 255, 399):
+            assert _cmp(At0[b, l].cpu().numpy(), od.greens_displaced(x.K, 0.1, x.V, 10, l, 0)) <= GTOL
+            assert _cmp(A0t[b, l].cpu().numpy(), od.greens_displaced_back(x.K, 0.1, x.V, 10, 0, l)) <= GTOL
