@@ -66,7 +66,8 @@ enum dqmc_status_bits {
   DQMC_STATUS_SINGULAR = 1 << 2,         /* an LU pivot or QR diagonal was exactly 0 */
   DQMC_STATUS_NONFINITE_OUTPUT = 1 << 3, /* G or log det is not finite */
   DQMC_STATUS_BAD_K = 1 << 4,            /* K not symmetric/finite, or ||dtau K||_1 > 2048 */
-  DQMC_STATUS_TIMEOUT = 1 << 5           /* a bounded wait of a tensor-core kernel gave up */
+  DQMC_STATUS_TIMEOUT = 1 << 5,          /* a bounded wait of a tensor-core kernel gave up */
+  DQMC_STATUS_NOT_CONVERGED = 1 << 6     /* the Jacobi SVD stabiliser hit its sweep limit */
 };
 
 /* Precision of the k-slice chain products (a mixed-precision option; the
@@ -150,6 +151,21 @@ dqmc_status dqmc_set_chain_fold(dqmc_handle h, int mode);
  * (Sec. 5.2).  Invalid scheme: DQMC_ERR_ARG. */
 typedef enum { DQMC_INV_LOH = 0, DQMC_INV_PLAIN = 1 } dqmc_inversion_scheme;
 dqmc_status dqmc_set_inversion_scheme(dqmc_handle h, int scheme);
+
+/* Decomposition that stabilises the chains (Sec. 4.2):
+ *   DQMC_DECOMP_QR      (default) column-pivoted Householder QR, U D X with X
+ *                       triangular up to the pivot permutation (Sec. 4.2.2);
+ *   DQMC_DECOMP_JACOBI  one-sided Jacobi SVD, U D V^T with X = V^T orthogonal
+ *                       (the accurate SVD variant of Sec. 4.2.1); about ten
+ *                       sweeps of N^2/2 plane rotations each, so 10-50x the
+ *                       QR's cost: an accuracy reference, not a fast path.
+ * Applies to every chain (equal-time, both stacks, ragged); the tree fold
+ * and the intermediate decompositions of the inversion schemes keep QR.
+ * JACOBI needs the FP64 chain precision (else DQMC_ERR_UNSUPPORTED at the
+ * call) and N <= 512.  A decomposition that does not converge in 60 sweeps
+ * sets DQMC_STATUS_NOT_CONVERGED.  Invalid value: DQMC_ERR_ARG. */
+typedef enum { DQMC_DECOMP_QR = 0, DQMC_DECOMP_JACOBI = 1 } dqmc_decomposition;
+dqmc_status dqmc_set_decomposition(dqmc_handle h, int decomposition);
 /* Number of kernel launches issued by the most recent compute call. */
 long long dqmc_last_launch_count(dqmc_handle h);
 /* Bytes of device workspace the handle currently holds. */

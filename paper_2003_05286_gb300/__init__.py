@@ -37,7 +37,8 @@ class Handle:
     """Owns a dqmc_handle (workspace + settings) bound to the current device."""
 
     def __init__(self, chain_precision: int = _abi.CHAIN_FP64, graphs: bool = False,
-                 fold: int = _abi.FOLD_AUTO, inversion: int = _abi.INV_LOH):
+                 fold: int = _abi.FOLD_AUTO, inversion: int = _abi.INV_LOH,
+                 decomposition: int = _abi.DECOMP_QR):
         self._lib = lib()
         h = C.c_void_p()
         _abi.check(self._lib.dqmc_create(C.byref(h)), "dqmc_create")
@@ -51,6 +52,13 @@ class Handle:
             self.set_chain_fold(fold)
         if inversion != _abi.INV_LOH:
             self.set_inversion_scheme(inversion)
+        if decomposition != _abi.DECOMP_QR:
+            self.set_decomposition(decomposition)
+
+    def set_decomposition(self, decomposition: int):
+        """Chain stabiliser: DECOMP_QR (pivoted QR, default) or DECOMP_JACOBI (one-sided SVD)."""
+        _abi.check(self._lib.dqmc_set_decomposition(self.h, int(decomposition)),
+                   "dqmc_set_decomposition")
 
     def set_inversion_scheme(self, scheme: int):
         """INV_LOH (D+/D- split, default) or INV_PLAIN (Eq. (inversion) / Eq. (inversion_tdgf))."""

@@ -15,7 +15,7 @@ STATUS_STRINGS = {
 }
 STATUS_BITS = {
     "NONFINITE_INPUT": 1 << 0, "NONFINITE_SCALE": 1 << 1, "SINGULAR": 1 << 2,
-    "NONFINITE_OUTPUT": 1 << 3, "BAD_K": 1 << 4, "TIMEOUT": 1 << 5,
+    "NONFINITE_OUTPUT": 1 << 3, "BAD_K": 1 << 4, "TIMEOUT": 1 << 5, "NOT_CONVERGED": 1 << 6,
 }
 CHAIN_FP64 = 0
 CHAIN_BF16X3 = 3
@@ -23,6 +23,7 @@ PTR_DEVICE = 0
 PTR_HOST = 1
 FOLD_SEQUENTIAL, FOLD_TREE, FOLD_AUTO = 0, 1, 2
 INV_LOH, INV_PLAIN = 0, 1
+DECOMP_QR, DECOMP_JACOBI = 0, 1
 
 
 class DqmcInstance(C.Structure):
@@ -45,6 +46,7 @@ SIGNATURES = {
     "dqmc_set_gemm_tile": (_I, [_P, _I]),
     "dqmc_set_chain_fold": (_I, [_P, _I]),
     "dqmc_set_inversion_scheme": (_I, [_P, _I]),
+    "dqmc_set_decomposition": (_I, [_P, _I]),
     "dqmc_last_launch_count": (C.c_longlong, [_P]),
     "dqmc_workspace_bytes": (C.c_longlong, [_P]),
     "dqmc_status_string": (C.c_char_p, [_I]),

@@ -40,6 +40,7 @@ struct dqmc_handle_s {
   int gemm_tile = 0;
   int fold = DQMC_FOLD_AUTO;               // equal-time chain: sequential or tree
   int inv = DQMC_INV_LOH;                  // inversion scheme of G and G(tau,0)
+  int decomp = DQMC_DECOMP_QR;             // chain stabiliser
   char* ws = nullptr;
   size_t ws_bytes = 0;
   long long launches = 0;
@@ -375,6 +376,21 @@ dqmc_status chunk_qr(dqmc_handle h, int dir, int batch, int N, int k, int c, con
   q.perm = w.perm; q.sperm = N;
   q.status = status;
   q.lim = lim; q.lim_at = c * k + 1;
+  if (h->decomp == DQMC_DECOMP_JACOBI) {
+    // U' D' V'^T by one-sided Jacobi; V'^T goes where T' would
+    JacobiArgs j;
+    j.N = N; j.batch = batch;
+    j.A = A; j.sA = NN;
+    j.Din = q.Din; j.sDin = q.sDin;
+    j.W = w.W; j.sW = NN;
+    j.U = q.U; j.sU = q.sU;
+    j.D = q.D; j.sD = q.sD;
+    j.Vt = w.T; j.sVt = NN;
+    j.status = status;
+    j.lim = lim; j.lim_at = q.lim_at;
+    CKP(PC_QRP, 8.0 / 3.0 * N * N * (double)N * batch, jacobi_svd_f64(j, st));
+    return DQMC_OK;
+  }
   CKP(PC_QRP, 8.0 / 3.0 * N * N * (double)N * batch, qrp_f64(q, st));
   return DQMC_OK;
 }
@@ -399,12 +415,13 @@ dqmc_status chunk_xupdate(dqmc_handle h, int dir, int batch, int N, int k, int c
                    N, batch, slotX(s, dst), s.instX, status, st));
     return DQMC_OK;
   }
+  const bool jac = h->decomp == DQMC_DECOMP_JACOBI;   // X' = V'^T X: dense, no pivots
   GemmArgs g;
   g.M = g.N = g.K = N;
   g.batch = batch;
-  g.A = w.T; g.lda = N; g.sA = NN; g.upperA = 1;
+  g.A = w.T; g.lda = N; g.sA = NN; g.upperA = jac ? 0 : 1;
   g.B = slotX(s, src); g.ldb = N; g.sB = s.instX;
-  g.permB = w.perm; g.sperm = N;
+  g.permB = jac ? nullptr : w.perm; g.sperm = N;
   g.C = slotX(s, dst); g.ldc = N; g.sC = s.instX;
   g.lim = lim; g.lim_at = c * k + 1;
   CKP(PC_XUPD, (double)N * N * (double)N * batch, gemm_f64(g, st));
@@ -675,7 +692,7 @@ dqmc_status run_chain_tree(dqmc_handle h, int batch, int N, int M, int k, const 
 // QRs of all chunks of the batch fit in one wave of CTAs and the chain has at
 // least four chunks.
 bool use_tree(dqmc_handle h, int batch, int nc) {
-  if (h->prec != DQMC_CHAIN_FP64) return false;
+  if (h->prec != DQMC_CHAIN_FP64 || h->decomp != DQMC_DECOMP_QR) return false;
   if (h->fold == DQMC_FOLD_TREE) return nc > 1;
   if (h->fold == DQMC_FOLD_SEQUENTIAL) return false;
   return nc >= 4 && (long long)batch * nc <= 152;
@@ -873,6 +890,8 @@ dqmc_status check_common(dqmc_handle h, int batch, int N, int M, const double* K
   if (!(dtau == dtau) || dtau < 0.0) return DQMC_ERR_ARG;
   if (batch > 0 && (!K || !V)) return DQMC_ERR_ARG;
   if (((uintptr_t)K | (uintptr_t)V) & 7) return DQMC_ERR_ARG;
+  if (h->decomp == DQMC_DECOMP_JACOBI && (h->prec != DQMC_CHAIN_FP64 || N > 512))
+    return DQMC_ERR_UNSUPPORTED;
   return DQMC_OK;
 }
 
@@ -976,6 +995,13 @@ dqmc_status dqmc_set_chain_precision(dqmc_handle h, dqmc_chain_prec prec) {
   return DQMC_OK;
 }
 
+dqmc_status dqmc_set_decomposition(dqmc_handle h, int decomposition) {
+  if (!h || (decomposition != DQMC_DECOMP_QR && decomposition != DQMC_DECOMP_JACOBI))
+    return DQMC_ERR_ARG;
+  h->decomp = decomposition;
+  return DQMC_OK;
+}
+
 dqmc_status dqmc_set_inversion_scheme(dqmc_handle h, int scheme) {
   if (!h || (scheme != DQMC_INV_LOH && scheme != DQMC_INV_PLAIN)) return DQMC_ERR_ARG;
   h->inv = scheme;
@@ -1039,6 +1065,7 @@ static dqmc_status graph_call(dqmc_handle h, GraphKey key, F&& body) {
   key.add((unsigned long long)h->gemm_tile);
   key.add((unsigned long long)h->fold);
   key.add((unsigned long long)h->inv);
+  key.add((unsigned long long)h->decomp);
   key.add((unsigned long long)pipeline_enabled() * 16 + (unsigned long long)pipeline_jobs(h->prec != DQMC_CHAIN_FP64));
   key.addp(h->ws);
   key.addp(h->stream);

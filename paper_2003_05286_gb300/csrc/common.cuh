@@ -71,6 +71,23 @@ struct QrpArgs {
 
 cudaError_t qrp_f64(const QrpArgs& a, cudaStream_t st);
 
+// One-sided Jacobi SVD, one CTA per instance (jacobi_f64.cu):
+//   A diag(Din) = U diag(D) V^T,  V^T written to Vt (row-major); W is an N x N
+// workspace per instance.  N <= 512.
+struct JacobiArgs {
+  int N = 0, batch = 0, max_sweeps = 60;
+  const double* A = nullptr; long long sA = 0;
+  const double* Din = nullptr; long long sDin = 0;   // nullable
+  double* W = nullptr; long long sW = 0;
+  double* U = nullptr; long long sU = 0;
+  double* D = nullptr; long long sD = 0;
+  double* Vt = nullptr; long long sVt = 0;
+  int* status = nullptr; int status_div = 1;          // nullable
+  const int* lim = nullptr; int lim_at = 0;           // skip instance b when lim[b] < lim_at
+};
+
+cudaError_t jacobi_svd_f64(const JacobiArgs& a, cudaStream_t st);
+
 // ---------------------------------------------------------------------------
 // LU with partial pivoting and solve, one CTA per instance:
 //   opA(A) Z = opR(R)   (A: N x N, R: N x nrhs), Z stored as opZ.
