@@ -67,6 +67,7 @@ struct QrpArgs {
   int* perm = nullptr; long long sperm = 0;
   int* status = nullptr; int status_div = 1;          // nullable
   const int* lim = nullptr; int lim_at = 0;           // skip instance b when lim[b] < lim_at
+  int smem_mats = 0;                                  // set by the launcher
 };
 
 cudaError_t qrp_f64(const QrpArgs& a, cudaStream_t st);
@@ -104,6 +105,7 @@ struct LuArgs {
   double* W = nullptr; long long sW = 0;
   double* logabsdet = nullptr; int* sign = nullptr;   // per instance, nullable
   int* status = nullptr; int status_div = 1;
+  int smem_w = 0;                                     // set by the launcher
 };
 
 cudaError_t lu_solve_f64(const LuArgs& a, cudaStream_t st);

@@ -19,7 +19,10 @@ template <int NT, int RPT>
 __global__ void __launch_bounds__(NT) lu_kernel(const LuArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int N = a.N, nr = a.nrhs, Wd = N + nr;
-  double* lbuf = reinterpret_cast<double*>(smem_raw);   // multipliers of the current column
+  // a.smem_w: the augmented matrix lives in shared memory (else in the
+  // workspace, L2-resident); the kernel reads it through a plain pointer
+  double* smW = reinterpret_cast<double*>(smem_raw);
+  double* lbuf = smW + (a.smem_w ? (long long)N * Wd : 0);   // multipliers of the current column
   double* dinv = lbuf + N;                              // 1 / u_jj
   __shared__ unsigned long long sk[32];
   __shared__ int si[32];
@@ -31,7 +34,7 @@ __global__ void __launch_bounds__(NT) lu_kernel(const LuArgs a) {
 
   for (int b = blockIdx.x; b < a.batch; b += gridDim.x) {
     const double* __restrict__ A = a.A + (long long)b * a.sA;
-    double* __restrict__ W = a.W + (long long)b * a.sW;
+    double* __restrict__ W = a.smem_w ? smW : a.W + (long long)b * a.sW;
     if (tid == 0) { s_flag = 0; s_sign = 1; s_lad = 0.0; }
 
     // ---- load [opA(A) | opR(R)] ------------------------------------------
@@ -187,9 +190,15 @@ __global__ void __launch_bounds__(NT) lu_kernel(const LuArgs a) {
   }
 }
 
-cudaError_t lu_solve_f64(const LuArgs& a, cudaStream_t st) {
-  if (a.batch <= 0 || a.N <= 0) return cudaSuccess;
+cudaError_t lu_solve_f64(const LuArgs& a0, cudaStream_t st) {
+  if (a0.batch <= 0 || a0.N <= 0) return cudaSuccess;
+  LuArgs a = a0;
   size_t sm = (size_t)a.N * 2 * sizeof(double) + 16;
+  // the augmented matrix in shared memory when it fits (227 KB per CTA): every
+  // elimination step reads and updates the trailing block
+  const size_t wb = (size_t)a.N * (a.N + a.nrhs) * sizeof(double);
+  a.smem_w = sm + wb <= 227 * 1024 ? 1 : 0;
+  if (a.smem_w) sm += wb;
   int grid = a.batch < (1 << 30) ? a.batch : (1 << 30);
   if (a.N + a.nrhs <= 64) {
     cudaFuncSetAttribute(lu_kernel<64, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

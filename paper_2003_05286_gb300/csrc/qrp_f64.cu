@@ -465,8 +465,14 @@ __global__ void __launch_bounds__(NT) qrp_fused_kernel(const QrpArgs a) {
   constexpr int NW = NT / 32, CPW = 32 / TPC, BATCH = 8;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int N = a.N;
+  // a.smem_mats: 0 = W and U in global memory, 1 = W in shared memory,
+  // 2 = W and U in shared memory (U copied out at the end).  The kernel reads
+  // both through plain pointers, so only where they point changes.
+  const long long NNs = (long long)N * N;
+  double* smW = reinterpret_cast<double*>(smem_raw);
+  double* smU = smW + (a.smem_mats >= 1 ? NNs : 0);
   // per column in pivoted (logical) order; swapped together with the columns
-  double* nrm2 = reinterpret_cast<double*>(smem_raw);
+  double* nrm2 = smW + a.smem_mats * NNs;
   double* ref2 = nrm2 + N;
   double* dsc = ref2 + N;
   double* wsm = dsc + N;     // w_c of the current step
@@ -488,8 +494,9 @@ __global__ void __launch_bounds__(NT) qrp_fused_kernel(const QrpArgs a) {
   for (int b = blockIdx.x; b < a.batch; b += gridDim.x) {
     if (a.lim && a.lim[b] < a.lim_at) continue;   // chain of this instance already finished
     const double* __restrict__ A = a.A + (long long)b * a.sA;
-    double* __restrict__ W = a.W + (long long)b * a.sW;
-    double* __restrict__ U = a.U + (long long)b * a.sU;
+    double* __restrict__ W = a.smem_mats >= 1 ? smW : a.W + (long long)b * a.sW;
+    double* __restrict__ Uout = a.U + (long long)b * a.sU;
+    double* __restrict__ U = a.smem_mats >= 2 ? smU : Uout;
     double* __restrict__ Dout = a.D + (long long)b * a.sD;
     double* __restrict__ T = a.T + (long long)b * a.sT;   // v_j in row j until the end
     int* __restrict__ pout = a.perm + (long long)b * a.sperm;
@@ -703,6 +710,7 @@ __global__ void __launch_bounds__(NT) qrp_fused_kernel(const QrpArgs a) {
     for (long long e = tid; e < NN; e += NT) {
       const int i = (int)(e / N), cc = (int)(e % N);
       T[e] = cc >= i ? W[e] * nrm2[i] * (dsc[cc] * ref2[i]) : 0.0;
+      if (a.smem_mats >= 2) Uout[e] = U[e];
     }
     __syncthreads();
     if (tid == 0 && s_flag && a.status) atomicOr(&a.status[b / a.status_div], s_flag);
@@ -714,9 +722,19 @@ static size_t qrp_fused_smem(int N) {
   return (size_t)N * (7 * sizeof(double) + sizeof(float) + sizeof(int)) + 16;
 }
 
+// Shared memory a CTA may use (opt-in limit of the SM).
+constexpr size_t kSmemLimit = 227 * 1024;
+
+// The working matrix W (and, when both fit, the accumulated Q) in shared
+// memory: every step of the factorisation reads and updates the trailing
+// columns, and from L2 each of those passes costs a round trip the step has
+// to wait for.  N <= 160 fits W, N <= 112 fits W and Q.
 template <int NT, int TPC, int NQ>
-static cudaError_t launch_qrp_fused(const QrpArgs& a, cudaStream_t st) {
-  const size_t sm = qrp_fused_smem(a.N);
+static cudaError_t launch_qrp_fused(const QrpArgs& a0, cudaStream_t st) {
+  QrpArgs a = a0;
+  const size_t base = qrp_fused_smem(a.N), mat = (size_t)a.N * a.N * sizeof(double);
+  a.smem_mats = base + 2 * mat <= kSmemLimit ? 2 : (base + mat <= kSmemLimit ? 1 : 0);
+  const size_t sm = base + a.smem_mats * mat;
   const int grid = a.batch < (1 << 30) ? a.batch : (1 << 30);
   cudaError_t e = cudaFuncSetAttribute(qrp_fused_kernel<NT, TPC, NQ>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
