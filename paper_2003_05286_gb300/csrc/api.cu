@@ -194,6 +194,11 @@ void take_expm(Arena& ar, int N, ExpmWs& w) {
 dqmc_status run_expm(dqmc_handle h, const double* K, int N, double dtau, double sgn,
                      const ExpmWs& w, int* status, int batch) {
   cudaStream_t st = h->cur;
+  if (N <= 16) {
+    CK(expm_small(K, N, dtau, sgn, EXPM_TERMS, EXPM_SQUARINGS, w.t0, w.asym, status, batch,
+                  DQMC_STATUS_BAD_K, st));
+    return DQMC_OK;
+  }
   CK(expm_prepare(K, N, dtau, sgn, w.s, w.scale, w.asym, st));
   CK(set_identity(w.t0, 0, N, 1, st));
   double* cur = w.t0;

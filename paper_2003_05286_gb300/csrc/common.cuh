@@ -164,6 +164,11 @@ cudaError_t scatter_tau(const double* cur, long long Q, int nt, int N, int k, in
 // 1-norm based scaling for the matrix exponential: s = max(0, ceil(log2(||dtau K||_1 / 0.5))),
 // scale = sgn * dtau / 2^s; writes s (int) and scale (double) to device memory;
 // also writes the symmetry defect flag into *asym (1 if K != K^T).
+// exp(sgn dtau K) for N <= 16 in one CTA (see elementwise.cu); status |= bad_bit
+// for every instance when K is not symmetric/finite or needs > max_sq squarings.
+cudaError_t expm_small(const double* K, int N, double dtau, double sgn, int terms, int max_sq,
+                       double* E, int* asym, int* status, int batch, int bad_bit,
+                       cudaStream_t st);
 cudaError_t expm_prepare(const double* K, int N, double dtau, double sgn,
                          int* s_out, double* scale_out, int* asym, cudaStream_t st);
 // Right-hand sides of the two-stack inversion (see api.cu), problems q = 0..Q-1.

@@ -339,6 +339,88 @@ cudaError_t expm_prepare(const double* K, int N, double dtau, double sgn, int* s
   return cudaGetLastError();
 }
 
+// The whole matrix exponential of a small K (N <= 16) in one CTA: the same
+// scaling as expm_prepare, the same Horner steps T <- I + (scale/m) K T and
+// squarings T <- T T as the product kernels compute them (each entry an FMA
+// chain over k = 0..N-1, then the scale, then the identity), in shared memory.
+// Replaces ~30 dependent launches of tiny products for a single small lattice.
+__global__ void expm_small_kernel(const double* K, int N, double dtau, double sgn, int terms,
+                                  int max_sq, double* E, int* asym, int* status, int batch,
+                                  int bad_bit) {
+  __shared__ double Ks[256], T0[256], T1[256], red[256];
+  __shared__ int bad, s_sq;
+  __shared__ double s_scale;
+  const int tid = threadIdx.x;
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  double mx = 0.0;
+  for (int c = tid; c < N; c += blockDim.x) {
+    double sm = 0.0;
+    for (int r = 0; r < N; ++r) {
+      const double x = K[(long long)r * N + c];
+      sm += fabs(x);
+      if (x != K[(long long)c * N + r] || !isfinite(x)) bad = 1;
+    }
+    mx = fmax(mx, sm);
+  }
+  red[tid] = mx;
+  for (int e = tid; e < N * N; e += blockDim.x) {
+    Ks[e] = K[e];
+    T0[e] = (e / N == e % N) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+    if (tid < off) red[tid] = fmax(red[tid], red[tid + off]);
+    __syncthreads();
+  }
+  if (tid == 0) {
+    double nrm = fabs(dtau) * red[0];
+    int sc = 0;
+    while (nrm > 0.5 && sc < 60) { nrm *= 0.5; ++sc; }
+    s_sq = sc < max_sq ? sc : max_sq;
+    s_scale = sgn * dtau * ldexp(1.0, -sc);
+    const int flag = bad || (sc > max_sq);
+    *asym = flag;
+    if (flag && status)
+      for (int b = 0; b < batch; ++b) status[b] |= bad_bit;
+  }
+  __syncthreads();
+  double* cur = T0;
+  double* nxt = T1;
+  const int i = tid / N, j = tid % N;
+  const bool own = tid < N * N;
+  for (int m = terms; m >= 1; --m) {
+    if (own) {
+      double acc = 0.0;
+      for (int k = 0; k < N; ++k) acc = fma(Ks[i * N + k], cur[k * N + j], acc);
+      double v = acc * ((1.0 / m) * s_scale);
+      if (i == j) v += 1.0;
+      nxt[tid] = v;
+    }
+    __syncthreads();
+    double* t = cur; cur = nxt; nxt = t;
+  }
+  for (int q = 0; q < s_sq; ++q) {
+    if (own) {
+      double acc = 0.0;
+      for (int k = 0; k < N; ++k) acc = fma(cur[i * N + k], cur[k * N + j], acc);
+      nxt[tid] = acc;
+    }
+    __syncthreads();
+    double* t = cur; cur = nxt; nxt = t;
+  }
+  if (own) E[tid] = cur[tid];
+}
+
+cudaError_t expm_small(const double* K, int N, double dtau, double sgn, int terms, int max_sq,
+                       double* E, int* asym, int* status, int batch, int bad_bit,
+                       cudaStream_t st) {
+  if (N > 16) return cudaErrorInvalidValue;
+  expm_small_kernel<<<1, 256, 0, st>>>(K, N, dtau, sgn, terms, max_sq, E, asym, status, batch,
+                                       bad_bit);
+  return cudaGetLastError();
+}
+
 __global__ void or_status_kernel(int* status, int batch, const int* flag, int bit) {
   if (*flag == 0) return;
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < batch; b += gridDim.x * blockDim.x)
