@@ -243,6 +243,23 @@ dqmc_status dqmc_greens_tdisplaced_all(dqmc_handle h, int batch, int N, int M,
                                        int k, double* Gtt, double* Gt0, double* G0t,
                                        int* status);
 
+/* Time-displaced Green's functions from another origin tau_{l0}: for instance
+ * b with origin l0[b] (0 <= l0[b] < M; l0 is a device array, or host in host
+ * pointer mode), on the grid d_j = min(j k, M) dtau (every_tau = 0, n_tau
+ * entries) or at every d_l = l dtau (every_tau != 0, M + 1 entries):
+ *   Gtt[j] = G(tau_{l0} + d_j, tau_{l0} + d_j),
+ *   Gt0[j] = G(tau_{l0} + d_j, tau_{l0}),   G0t[j] = G(tau_{l0}, tau_{l0} + d_j),
+ * layouts as in dqmc_greens_tdisplaced(_all).  This is the computation from
+ * origin 0 on the cyclically shifted chain (slice m taken as B_{m + l0}):
+ * the products of Eq. (etgf_tau) and of the two cases of Eq. (tdgf_propagate)
+ * depend only on that cyclic order.  Times past beta continue anti-periodically,
+ * G(tau + beta, tau') = -G(tau, tau').  Together with l0 over the grid this
+ * gives G(tau_1, tau_2) for every pair of grid times. */
+dqmc_status dqmc_greens_tdisplaced_from(dqmc_handle h, int batch, int N, int M,
+                                        const double* K, double dtau, const double* V,
+                                        int k, const int* l0, int every_tau, double* Gtt,
+                                        double* Gt0, double* G0t, int* status);
+
 /* Gradient dV[(b*M + (l-1))*N + i] = d log|det(1 + B_M...B_1)| / dV_l(i)
  * = 1 - G_l(i,i) for every slice l (derived from Eqs. (etgf), (etgf_tau)):
  * G_l at the k-grid from the two stacks, then G_{l+1} = B_l G_l B_l^{-1}

@@ -19,6 +19,7 @@ import torch
 from . import _abi
 
 __all__ = ["Handle", "greens", "logdet", "greens_tdisplaced", "greens_tdisplaced_all",
+           "greens_tdisplaced_from",
            "logdet_grad", "greens_ragged",
            "greens_tdisplaced_ragged", "logdet_grad_ragged", "selftest_wait_timeout", "LogDet",
            "n_tau", "lib"]
@@ -230,6 +231,36 @@ def greens_tdisplaced_all(K, dtau: float, V, k: int, *, handle: Handle | None = 
     _abi.check(h._lib.dqmc_greens_tdisplaced_all(h.h, B, N, M, _ptr(K), float(dtau), _ptr(V),
                                                  int(k), _ptr(Gtt), _ptr(Gt0), _ptr(G0t),
                                                  _ptr(st)), "dqmc_greens_tdisplaced_all")
+    res = (Gtt, Gt0, G0t)
+    if sq:
+        return tuple(x[0] if x is not None else None for x in res) + (st[0],)
+    return res + (st,)
+
+
+def greens_tdisplaced_from(K, dtau: float, V, k: int, l0, *, every_tau: bool = False,
+                           handle: Handle | None = None, want_tt: bool = True,
+                           want_t0: bool = True, want_0t: bool = True):
+    """G(tau_l0 + d, tau_l0 + d), G(tau_l0 + d, tau_l0) and G(tau_l0, tau_l0 + d) from the
+    origin tau_l0 of each instance (dqmc_greens_tdisplaced_from), d on the k-grid or at
+    every slice; l0 an int sequence or tensor of length B.  Times past beta continue
+    anti-periodically.  Returns tensors (B, n_tau or M+1, N, N) (None where not wanted)
+    and status."""
+    K, V, sq = _prep(K, V)
+    B, M, N = V.shape
+    h = _handle(handle)
+    l0 = torch.as_tensor(l0, dtype=torch.int32, device=V.device).reshape(-1).contiguous()
+    if l0.numel() != B:
+        raise ValueError(f"l0 has {l0.numel()} entries for {B} instances")
+    nt = M + 1 if every_tau else n_tau(M, k)
+
+    def out(want):
+        return torch.empty((B, nt, N, N), dtype=torch.float64, device=V.device) if want else None
+    Gtt, Gt0, G0t = out(want_tt), out(want_t0), out(want_0t)
+    st = torch.empty(B, dtype=torch.int32, device=V.device)
+    _abi.check(h._lib.dqmc_greens_tdisplaced_from(h.h, B, N, M, _ptr(K), float(dtau), _ptr(V),
+                                                  int(k), _ptr(l0), int(every_tau), _ptr(Gtt),
+                                                  _ptr(Gt0), _ptr(G0t), _ptr(st)),
+               "dqmc_greens_tdisplaced_from")
     res = (Gtt, Gt0, G0t)
     if sq:
         return tuple(x[0] if x is not None else None for x in res) + (st[0],)

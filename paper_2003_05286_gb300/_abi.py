@@ -59,6 +59,7 @@ SIGNATURES = {
     "dqmc_greens_tdisplaced": (_I, [_P, _I, _I, _I, _P, _D, _P, _I, _P, _P, _P]),
     "dqmc_greens_tdisplaced_ex": (_I, [_P, _I, _I, _I, _P, _D, _P, _I, _P, _P, _P, _P]),
     "dqmc_greens_tdisplaced_all": (_I, [_P, _I, _I, _I, _P, _D, _P, _I, _P, _P, _P, _P]),
+    "dqmc_greens_tdisplaced_from": (_I, [_P, _I, _I, _I, _P, _D, _P, _I, _P, _I, _P, _P, _P, _P]),
     "dqmc_logdet_grad": (_I, [_P, _I, _I, _I, _P, _D, _P, _I, _P, _P, _P, _P]),
     "dqmc_greens_ragged": (_I, [_P, _I, C.POINTER(DqmcInstance), _P, _P, _P, _P, _P, _P]),
     "dqmc_greens_noalloc": (_I, [_P, _I, _I, _I, _P, _D, _P, _I, _P, _P, _P, _P]),

@@ -1674,7 +1674,23 @@ extern "C" {
 
 static dqmc_status tdisplaced_impl(dqmc_handle h, int batch, int N, int M, const double* K,
                                    double dtau, const double* V, int k, double* Gtt, double* Gt0,
-                                   double* G0t, int* status, bool all_tau = false);
+                                   double* G0t, int* status, bool all_tau = false,
+                                   const int* shift = nullptr);
+
+dqmc_status dqmc_greens_tdisplaced_from(dqmc_handle h, int batch, int N, int M, const double* K,
+                                        double dtau, const double* V, int k, const int* l0,
+                                        int every_tau, double* Gtt, double* Gt0, double* G0t,
+                                        int* status) {
+  if (!h) return DQMC_ERR_ARG;
+  if (batch > 0 && !l0) return DQMC_ERR_ARG;
+  GraphKey key = key_of(6, batch, N, M, K, dtau, V, k);
+  key.addp(l0); key.add((unsigned long long)every_tau);
+  key.addp(Gtt); key.addp(Gt0); key.addp(G0t); key.addp(status);
+  return graph_call(h, key, [&] {
+    return tdisplaced_impl(h, batch, N, M, K, dtau, V, k, Gtt, Gt0, G0t, status, every_tau != 0,
+                           l0);
+  });
+}
 
 dqmc_status dqmc_greens_tdisplaced_all(dqmc_handle h, int batch, int N, int M, const double* K,
                                        double dtau, const double* V, int k, double* Gtt,
@@ -1706,7 +1722,7 @@ dqmc_status dqmc_greens_tdisplaced(dqmc_handle h, int batch, int N, int M, const
 
 static dqmc_status tdisplaced_impl(dqmc_handle h, int batch, int N, int M, const double* K,
                                    double dtau, const double* V, int k, double* Gtt, double* Gt0,
-                                   double* G0t, int* status, bool all_tau) {
+                                   double* G0t, int* status, bool all_tau, const int* shift) {
   CKS(check_common(h, batch, N, M, K, dtau, V, k));
   if (h->prec != DQMC_CHAIN_FP64 && N > 256) return DQMC_ERR_UNSUPPORTED;
   h->launches = 0;
@@ -1727,6 +1743,7 @@ static dqmc_status tdisplaced_impl(dqmc_handle h, int batch, int N, int M, const
   double *expV, *expmV = nullptr, *Gttd = nullptr, *Gt0d = nullptr, *G0td = nullptr;
   double *gq[3] = {nullptr, nullptr, nullptr}, *gtmp = nullptr;   // grid values (all_tau)
   int* stat;
+  int* shiftd = nullptr;
   auto layout = [&](Arena& ar) {
     take_expm(ar, N, ew);
     expV = ar.take<double>(Mp * N * batch);
@@ -1751,6 +1768,7 @@ static dqmc_status tdisplaced_impl(dqmc_handle h, int batch, int N, int M, const
     if (host) {
       io.K = ar.take<double>(NN);
       io.V = ar.take<double>((long long)M * N * batch);
+      if (shift) shiftd = ar.take<int>(batch);
       Gttd = Gtt ? ar.take<double>(batch * outlen) : nullptr;
       Gt0d = Gt0 ? ar.take<double>(batch * outlen) : nullptr;
       G0td = G0t ? ar.take<double>(batch * outlen) : nullptr;
@@ -1774,11 +1792,15 @@ static dqmc_status tdisplaced_impl(dqmc_handle h, int batch, int N, int M, const
         cudaMemcpyAsync(io.V, V, (size_t)M * N * batch * sizeof(double), cudaMemcpyHostToDevice,
                         st) != cudaSuccess)
       return DQMC_ERR_CUDA;
+    if (shift && cudaMemcpyAsync(shiftd, shift, batch * sizeof(int), cudaMemcpyHostToDevice,
+                                 st) != cudaSuccess)
+      return DQMC_ERR_CUDA;
     Kd = io.K; Vd = io.V; Gtto = Gttd; Gt0o = Gt0d; G0to = G0td; stout = stat;
   }
   if (cudaMemsetAsync(stout, 0, sizeof(int) * batch, st) != cudaSuccess) return DQMC_ERR_CUDA;
   CKS(run_expm(h, Kd, N, dtau, -1.0, ew, stout, batch));
-  CK(exp_pad(Vd, expV, batch, M, (int)Mp, N, 1.0, stout, st));
+  const int* sh = host ? shiftd : shift;   // time translation of the chain (nullable)
+  CK(exp_pad(Vd, expV, batch, M, (int)Mp, N, 1.0, stout, st, sh));
   CKS(run_stacks(h, batch, N, M, k, ew.t0, expV, Mp * N, sw, cw, cw2, stout));
   double* out[3] = {Gtto, Gt0o, G0to};
   if (all_tau)
@@ -1792,7 +1814,7 @@ static dqmc_status tdisplaced_impl(dqmc_handle h, int batch, int N, int M, const
     //   G_{l+1} = B_l G_l B_l^{-1}   (Eqs. (tdgf_propagate), (etgf_tau)),
     // with B_l = E e^{V_l} and B_l^{-1} = e^{-V_l} E^{-1}.
     CKS(run_expm(h, Kd, N, dtau, +1.0, ewi, nullptr, batch));
-    if (expmV) CK(exp_pad(Vd, expmV, batch, M, (int)Mp, N, -1.0, nullptr, st));
+    if (expmV) CK(exp_pad(Vd, expmV, batch, M, (int)Mp, N, -1.0, nullptr, st, sh));
     double* dst[3] = {Gtto, Gt0o, G0to};
     const double f2 = 2.0 * N * (double)N * N * Q;
     for (int s = 0; s < k; ++s) {

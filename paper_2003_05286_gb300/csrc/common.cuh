@@ -136,9 +136,10 @@ cudaError_t axpby2(const Axpby2Args& a, cudaStream_t st);
 // out[b*n + i] = f(D[b*sD + i]) with mode as in Axpby2Args (4: 1/D).
 cudaError_t dsplit_vec(const double* D, long long sD, int n, int batch, double* out, int mode,
                        cudaStream_t st);
-// exp(sgn*V) of a batch x M x N field into a batch x Mp x N array (padding = 1).
+// exp(sgn*V) of a batch x M x N field into a batch x Mp x N array (padding = 1);
+// with shift (device, per instance) slice l is taken from slice l + shift[b] mod M.
 cudaError_t exp_pad(const double* V, double* out, int batch, int M, int Mp, int N, double sgn,
-                    int* status, cudaStream_t st);
+                    int* status, cudaStream_t st, const int* shift = nullptr);
 // y = 1 - diag(G) for a batch of N x N matrices; y_b at y + b*sy.
 cudaError_t one_minus_diag(const double* G, long long sG, int N, int batch,
                            double* y, long long sy, int ydiv, long long sy_outer,

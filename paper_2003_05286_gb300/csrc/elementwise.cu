@@ -147,7 +147,7 @@ cudaError_t dsplit_vec(const double* D, long long sD, int n, int batch, double* 
 
 // out[(b*Mp + l)*N + i] = exp(sgn * V[(b*M + l)*N + i]) for l < M, 1 for M <= l < Mp
 __global__ void exp_pad_kernel(const double* V, double* out, int batch, int M, int Mp, int N,
-                               double sgn, int* status) {
+                               double sgn, int* status, const int* shift) {
   const long long total = (long long)batch * Mp * N;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
@@ -156,7 +156,9 @@ __global__ void exp_pad_kernel(const double* V, double* out, int batch, int M, i
     int l = (int)(r / N), i = (int)(r % N);
     double v = 1.0;
     if (l < M) {
-      double x = V[(b * M + l) * N + i];
+      // shift[b]: slice l of the staged chain is slice l + shift[b] (mod M) of V
+      const int ls = shift ? (int)(((long long)l + shift[b]) % M + M) % M : l;
+      double x = V[(b * M + ls) * N + i];
       if (!isfinite(x) && status) atomicOr(&status[b], DQMC_STATUS_NONFINITE_INPUT);
       v = exp(sgn * x);
     }
@@ -165,10 +167,10 @@ __global__ void exp_pad_kernel(const double* V, double* out, int batch, int M, i
 }
 
 cudaError_t exp_pad(const double* V, double* out, int batch, int M, int Mp, int N, double sgn,
-                    int* status, cudaStream_t st) {
+                    int* status, cudaStream_t st, const int* shift) {
   long long total = (long long)batch * Mp * N;
   if (total <= 0) return cudaSuccess;
-  exp_pad_kernel<<<nblocks(total), TPB, 0, st>>>(V, out, batch, M, Mp, N, sgn, status);
+  exp_pad_kernel<<<nblocks(total), TPB, 0, st>>>(V, out, batch, M, Mp, N, sgn, status, shift);
   return cudaGetLastError();
 }
 

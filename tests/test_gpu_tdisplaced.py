@@ -255,3 +255,50 @@ def test_all_tau_full_size_sampled(dq):
         for l in (1, 9, 137, 255, 399):
             assert _cmp(At0[b, l].cpu().numpy(), od.greens_displaced(x.K, 0.1, x.V, 10, l, 0)) <= GTOL
             assert _cmp(A0t[b, l].cpu().numpy(), od.greens_displaced_back(x.K, 0.1, x.V, 10, 0, l)) <= GTOL
+
+
+# ---------------------------------------------------------------------------
+# G(tau_1, tau_2) for every pair of grid times (dqmc_greens_tdisplaced_from)
+# ---------------------------------------------------------------------------
+
+def _pair_refs(inst, k, l0, l1):
+    """Oracle G(tau_1,tau_1), G(tau_1,tau_0), G(tau_0,tau_1) for tau_1 = l1 dtau >= tau_0,
+    continued anti-periodically past beta (G(tau + beta, tau') = -G(tau, tau'))."""
+    M = inst.M
+    Gtt = od.greens(inst.K, 0.1, inst.V, k, l=l1 % M + 1)[0]
+    if l1 <= M:
+        return (Gtt, od.greens_displaced(inst.K, 0.1, inst.V, k, l1, l0),
+                od.greens_displaced_back(inst.K, 0.1, inst.V, k, l0, l1))
+    return (Gtt, -od.greens_displaced_back(inst.K, 0.1, inst.V, k, l1 - M, l0),
+            -od.greens_displaced(inst.K, 0.1, inst.V, k, l0, l1 - M))
+
+
+@pytest.mark.parametrize("every_tau", [False, True])
+def test_from_every_grid_pair(dq, every_tau):
+    """3x3 lattice, beta = 3 (M = 30), k = 10: origins on the grid and off it (7);
+    one call for all origins; origin 0 equals dqmc_greens_tdisplaced_ex bitwise."""
+    inst = di.hubbard_instance(3, 4.0, 0.1, 3.0, 10, 9)
+    M = inst.M
+    origins = [0, 7, 10, 20]
+    K = _dev(inst.K)
+    V = _dev(np.stack([inst.V] * len(origins)))
+    Att, At0, A0t, st = dq.greens_tdisplaced_from(K, 0.1, V, 10, origins, every_tau=every_tau)
+    assert int((st != 0).sum()) == 0
+    offs = list(range(M + 1)) if every_tau else od.tau_grid(M, 10)
+    for b, l0 in enumerate(origins):
+        for j, d in enumerate(offs):
+            if every_tau and d % 3:
+                continue
+            rtt, rt0, r0t = _pair_refs(inst, 10, l0, l0 + d)
+            assert _cmp(Att[b, j].cpu().numpy(), rtt) <= GTOL, ("tt", l0, d)
+            assert _cmp(At0[b, j].cpu().numpy(), rt0) <= GTOL, ("t0", l0, d)
+            assert _cmp(A0t[b, j].cpu().numpy(), r0t) <= GTOL, ("0t", l0, d)
+    if not every_tau:
+        a, b_, c, _ = dq.greens_tdisplaced(K, 0.1, V[0], 10, want_0t=True)
+        assert torch.equal(Att[0], a) and torch.equal(At0[0], b_) and torch.equal(A0t[0], c)
+
+
+def test_from_rejects_missing_origins(dq):
+    inst = di.hubbard_instance(2, 4.0, 0.1, 2.0, 10, 1)
+    with pytest.raises(ValueError):
+        dq.greens_tdisplaced_from(_dev(inst.K), 0.1, _dev(inst.V[None]), 10, [0, 1])
