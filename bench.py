@@ -640,7 +640,9 @@ def run_gpu_other(args, wl, rank, world):
                            l2="flushed between timed steps (256 MB write)", **extra),
             "roofline": {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
                          "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
-                         "kernel": "whole step (all kernels), algorithmic FP64 flops"},
+                         "kernel": "whole step (all kernels), algorithmic FP64 flops"
+                                   + ("" if prec == 0 else "; the chain products run on the tensor "
+                                      "cores, so FP64-equivalent flops can exceed the FP64 peak")},
             "gpu_launches": launches * args.steps, "clocks": clk,
             "status_nonzero": int((st != 0).sum().item()), "e2e": None,
             "cpu_baseline": cpu_baseline_line(wl, args)
