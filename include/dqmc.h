@@ -130,7 +130,8 @@ dqmc_status dqmc_set_gemm_tile(dqmc_handle h, int tile);
  *                         (U_2 D_2 X_2)(U_1 D_1 X_1) = (U_2 u) d (x X_1),
  *                         u d x = udt(D_2 (X_2 U_1) D_1), in ceil(log2(ceil(M/k)))
  *                         levels: fewer dependent steps, more arithmetic;
- *   DQMC_FOLD_AUTO        (default) tree when batch * ceil(M/k) <= 152 and
+ *   DQMC_FOLD_AUTO        (default) tree when batch * ceil(M/k) is at most
+ *                         the device's SM count (152 on GB300) and
  *                         ceil(M/k) >= 4, else sequential.
  * Both give G and log det of the same definition; they differ by rounding.
  * Invalid mode: DQMC_ERR_ARG. */

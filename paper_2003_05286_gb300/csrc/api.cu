@@ -34,6 +34,7 @@ struct ProfRec {
 
 struct dqmc_handle_s {
   int device = 0;
+  int sms = 152;                           // SM count of the device (queried at creation)
   cudaStream_t stream = nullptr;
   dqmc_pointer_mode pmode = DQMC_PTR_DEVICE;
   dqmc_chain_prec prec = DQMC_CHAIN_FP64;
@@ -694,13 +695,13 @@ dqmc_status run_chain_tree(dqmc_handle h, int batch, int N, int M, int k, const 
 }
 
 // Tree fold for the equal-time chain: by setting, or (auto) when the level-0
-// QRs of all chunks of the batch fit in one wave of CTAs and the chain has at
-// least four chunks.
+// QRs of all chunks of the batch fit in one wave of CTAs (one per SM) and the
+// chain has at least four chunks.
 bool use_tree(dqmc_handle h, int batch, int nc) {
   if (h->prec != DQMC_CHAIN_FP64 || h->decomp != DQMC_DECOMP_QR) return false;
   if (h->fold == DQMC_FOLD_TREE) return nc > 1;
   if (h->fold == DQMC_FOLD_SEQUENTIAL) return false;
-  return nc >= 4 && (long long)batch * nc <= 152;
+  return nc >= 4 && (long long)batch * nc <= h->sms;
 }
 
 // ---------------------------------------------------------------------------
@@ -923,7 +924,8 @@ dqmc_status dqmc_create(dqmc_handle* h) {
   *h = nullptr;
   dqmc_handle x = new (std::nothrow) dqmc_handle_s();
   if (!x) return DQMC_ERR_NOMEM;
-  if (cudaGetDevice(&x->device) != cudaSuccess) {
+  if (cudaGetDevice(&x->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&x->sms, cudaDevAttrMultiProcessorCount, x->device) != cudaSuccess) {
     cudaGetLastError();
     delete x;
     return DQMC_ERR_CUDA;

@@ -188,7 +188,18 @@ static void launch_gemm(const GemmArgs& a, int zb, cudaStream_t st) {
 // 16-tile with one output per thread (8 warps, two per sub-partition); outputs
 // of at most 32 x 32 take a 256-thread 32-tile with 2 x 2 per thread while the
 // batch leaves most SMs idle.  The K order per output is unchanged.
-constexpr int kSmallTileCtas = 2 * 152;
+static int small_tile_ctas() {
+  static const int n = [] {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();
+      sms = 152;
+    }
+    return 2 * sms;
+  }();
+  return n;
+}
 
 cudaError_t gemm_f64(const GemmArgs& a, cudaStream_t st) {
   if (a.batch <= 0 || a.M <= 0 || a.N <= 0) return cudaSuccess;
@@ -197,7 +208,7 @@ cudaError_t gemm_f64(const GemmArgs& a, cudaStream_t st) {
     launch_gemm<16, 16, 1, 1>(a, zb, st);                      // 256 threads, 1 output each
     return cudaGetLastError();
   }
-  if (!a.tile && a.M <= 32 && a.N <= 32 && a.batch < kSmallTileCtas) {
+  if (!a.tile && a.M <= 32 && a.N <= 32 && a.batch < small_tile_ctas()) {
     launch_gemm<32, 32, 2, 2>(a, zb, st);                      // 256 threads, 2x2 each
     return cudaGetLastError();
   }
