@@ -136,6 +136,11 @@ class BruteForce:
         G1, _, _ = self.greens(1)
         return self.chain(range(1, l1 + 1)) * G1
 
+    def displaced_pair(self, l1: int, l2: int):
+        """G(tau_{l1}, tau_{l2}), l1 >= l2: B_{l1}...B_{l2+1} G_{l2+1} (Eq. (tdgf_propagate))."""
+        G, _, _ = self.greens(l2 + 1)
+        return self.chain(range(l2 + 1, l1 + 1)) * G
+
     def displaced_back(self, l1: int, l2: int):
         """G(tau_{l1}, tau_{l2}), l2 >= l1: -(1 - G_{l1+1}) (B_{l2}...B_{l1+1})^{-1}."""
         mp = self.mp

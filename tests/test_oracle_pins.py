@@ -360,3 +360,44 @@ def test_inv_sum_degrades_mid_tau(l1, sum_ok):
     e_sum = np.abs(od.greens_displaced(K, 0.1, V, 10, l1, 0, scheme="sum") - Gx).max()
     assert e_loh < 1e-12
     assert (e_sum < 1e-12) if sum_ok else (e_sum > 1e-9)
+
+
+# ---------------------------------------------------------------------------
+# G(tau_1, tau_2) for pairs away from tau = 0, and time translation
+# ---------------------------------------------------------------------------
+
+def test_brute_force_general_pairs():
+    """P4 for both cases of Eq. (tdgf_propagate) with neither time at 0."""
+    K = di.chain_hopping(4)
+    V = 1.1 * di.ising_field(12, 36, 4)
+    bf = ex.BruteForce(K, 0.1, V)
+    for l1, l2 in ((20, 7), (36, 12), (15, 15), (33, 1)):
+        # single-species G reaches |G| ~ 1e2 here: the bound is relative to its largest entry
+        R = bf.to_numpy(bf.displaced_pair(l1, l2))
+        G = od.greens_displaced(K, 0.1, V, 6, l1, l2)
+        assert np.abs(G - R).max() < 1e-12 * max(1.0, np.abs(R).max()), (l1, l2)
+        Rb = bf.to_numpy(bf.displaced_back(l2, l1))
+        Gb = od.greens_displaced_back(K, 0.1, V, 6, l2, l1)
+        assert np.abs(Gb - Rb).max() < 1e-12 * max(1.0, np.abs(Rb).max()), (l2, l1)
+
+
+def test_time_translation():
+    """The products of Eqs. (etgf_tau) and (tdgf_propagate) depend only on the cyclic
+    order of the slices: G(tau_{l0+d}, tau_{l0}) of V is G(tau_d, 0) of V shifted by l0,
+    and past beta the shifted result is the anti-periodic continuation."""
+    K, V = _hubbard(3, 4.0, 3.0, seed=9)
+    M = V.shape[0]
+    for l0 in (4, 13, 29):
+        Vs = np.roll(V, -l0, axis=0)
+        for d in (0, 6, M - l0, M):
+            l1 = l0 + d
+            G = od.greens_displaced(K, 0.1, Vs, 10, d, 0)
+            G0 = od.greens_displaced_back(K, 0.1, Vs, 10, 0, d)
+            if l1 <= M:
+                R = od.greens_displaced(K, 0.1, V, 10, l1, l0)
+                R0 = od.greens_displaced_back(K, 0.1, V, 10, l0, l1)
+            else:
+                R = -od.greens_displaced_back(K, 0.1, V, 10, l1 - M, l0)
+                R0 = -od.greens_displaced(K, 0.1, V, 10, l0, l1 - M)
+            assert np.abs(G - R).max() < 1e-12 * max(1.0, np.abs(R).max()), (l0, d)
+            assert np.abs(G0 - R0).max() < 1e-12 * max(1.0, np.abs(R0).max()), (l0, d)
