@@ -9,6 +9,11 @@ G = [1 + B_80...B_1]^{-1} (Eq. (etgf)) and log|det(1 + B_80...B_1)| with its
 sign, from the naive product at the precision oracle.exact.required_dps picks.
 First row: logdet, sign; then the 256 entries of G in row-major order.
 
+single_n16_displaced_mpmath.txt -- the same instance: G(tau_l, 0) = B_l...B_1 G_1
+and G(0, tau_l) = -(1 - G_1)(B_l...B_1)^{-1} (both cases of Eq. (tdgf_propagate))
+for l = 10, 40, 70, from the same naive products.  One block per (function, l):
+a header line "t0 <l>" or "0t <l>", then 256 entries row-major.
+
 Run from the repository root:  python tests/golden/make_golden.py
 """
 import os
@@ -35,6 +40,21 @@ def main():
         for v in G.ravel():
             f.write(f"{v:.17e}\n")
     print("wrote", out, "dps", bf.dps)
+
+    mp = bf.mp
+    G1 = bf.greens(1)[0]
+    one_minus = mp.eye(bf.N) - G1
+    out = os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                       "single_n16_displaced_mpmath.txt")
+    with open(out, "w") as f:
+        f.write(f"# mpmath dps={bf.dps}; blocks 't0 l' = G(tau_l, 0), '0t l' = G(0, tau_l)\n")
+        for l in (10, 40, 70):
+            C = bf.chain(range(1, l + 1))
+            for name, A in (("t0", C * G1), ("0t", -(one_minus * mp.inverse(C)))):
+                f.write(f"{name} {l}\n")
+                for v in bf.to_numpy(A).ravel():
+                    f.write(f"{v:.17e}\n")
+    print("wrote", out)
 
 
 if __name__ == "__main__":

@@ -302,3 +302,28 @@ def test_from_rejects_missing_origins(dq):
     inst = di.hubbard_instance(2, 4.0, 0.1, 2.0, 10, 1)
     with pytest.raises(ValueError):
         dq.greens_tdisplaced_from(_dev(inst.K), 0.1, _dev(inst.V[None]), 10, [0, 1])
+
+
+def test_displaced_n16_against_mpmath(dq):
+    """The 4x4, U=4, beta=8, k=10 workload: G(tau_l, 0) and G(0, tau_l) at l = 10, 40, 70
+    (grid points j = 1, 4, 7) against the stored mpmath values."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "single_n16_displaced_mpmath.txt")
+    gold, cur = {}, None
+    for ln in open(path):
+        if ln.startswith("#"):
+            continue
+        parts = ln.split()
+        if len(parts) == 2:
+            cur = (parts[0], int(parts[1]))
+            gold[cur] = []
+        else:
+            gold[cur].append(float(parts[0]))
+    inst = di.single_n16()
+    _, Gt0, G0t, st = dq.greens_tdisplaced(_dev(inst.K), inst.dtau, _dev(inst.V), inst.k,
+                                           want_tt=False, want_0t=True)
+    assert int(st) == 0
+    for (name, l), vals in gold.items():
+        Gx = np.array(vals).reshape(16, 16)
+        A = (Gt0 if name == "t0" else G0t)[l // inst.k].cpu().numpy()
+        assert _cmp(A, Gx) <= GTOL, (name, l)

@@ -401,3 +401,32 @@ def test_time_translation():
                 R0 = -od.greens_displaced(K, 0.1, V, 10, l0, l1 - M)
             assert np.abs(G - R).max() < 1e-12 * max(1.0, np.abs(R).max()), (l0, d)
             assert np.abs(G0 - R0).max() < 1e-12 * max(1.0, np.abs(R0).max()), (l0, d)
+
+
+def _golden_displaced():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "single_n16_displaced_mpmath.txt")
+    blocks, cur = {}, None
+    for ln in open(path):
+        if ln.startswith("#"):
+            continue
+        parts = ln.split()
+        if len(parts) == 2:
+            cur = (parts[0], int(parts[1]))
+            blocks[cur] = []
+        else:
+            blocks[cur].append(float(parts[0]))
+    return {key: np.array(v).reshape(16, 16) for key, v in blocks.items()}
+
+
+def test_golden_displaced_n16():
+    """4x4 lattice, U=4, beta=8, k=10: G(tau,0) and G(0,tau) of the oracle against the
+    stored mpmath values (tests/golden/make_golden.py, Eq. (tdgf_propagate))."""
+    inst = di.single_n16()
+    gold = _golden_displaced()
+    for (name, l), Gx in gold.items():
+        if name == "t0":
+            G = od.greens_displaced(inst.K, inst.dtau, inst.V, inst.k, l, 0)
+        else:
+            G = od.greens_displaced_back(inst.K, inst.dtau, inst.V, inst.k, 0, l)
+        assert np.abs(G - Gx).max() < 1e-12 * max(1.0, np.abs(Gx).max()), (name, l)
