@@ -327,13 +327,20 @@ dqmc_status dqmc_logdet_grad_ragged(dqmc_handle h, int batch, const dqmc_instanc
  * 32 MiB (32 * 2^20 bytes) that each GPU loading the library holds until the
  * process exits.  The call issues no cudaMalloc, cudaFree or other allocating
  * routine.
- *   - Size limit: about batch * 8 * (N*(ceil(M/k)+1)*k + 11*N*N) + 16*N*N bytes must
- *     fit in 32 MiB (e.g. N=256, M=200, k=10: batch <= 5; N=64, M=400:
- *     batch <= 58).  Larger problems return DQMC_ERR_SCRATCH before anything
- *     is launched.
- *   - First call on a device: it resolves the array's device address
- *     (cudaGetSymbolAddress) once for the current device; make that first call
- *     before any stream capture on the device.
+ *   - Size limit: with r(x) = x rounded up to a multiple of 256 and
+ *     Mp = (ceil(M/k) + 1) * k, the intermediates take
+ *       S = 2 r(8N^2) + 768 + r(8 Mp N b) + 9 r(8 N^2 b) + r(16 N^2 b)
+ *           + 2 r(8 N b) + r(4 N b) + r(8 b) + 3 r(4 b)      bytes (b = batch),
+ *     which must not exceed 32 MiB = 33554432 bytes (e.g. N=256, M=200, k=10:
+ *     batch <= 5; N=64, M=400, k=10: batch <= 58).  Larger problems return
+ *     DQMC_ERR_SCRATCH before anything is launched.
+ *   - Pointers: K, V, G, logdet, sign and status must be device (or managed)
+ *     memory; anything else (a host buffer, pinned or not) returns DQMC_ERR_ARG
+ *     before any launch.
+ *   - Address of the array: looked up in the current context on every call
+ *     (cudaGetSymbolAddress), never cached.  The first call in a context may
+ *     load the library's device code, so make that first call before any
+ *     stream capture on the device.
  *   - Every call shares the one array, which keeps the previous call's
  *     contents; the call clears what must start at zero itself.  Calls that
  *     overlap on the GPU (other streams, other host threads) race on the array

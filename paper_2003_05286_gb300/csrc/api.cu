@@ -1294,6 +1294,21 @@ static dqmc_status greens_impl(dqmc_handle h, int batch, int N, int M, const dou
 // stream (no pipelining, so no stream or event is created), and no
 // cudaMalloc: when the problem needs more than ws_bytes it returns
 // DQMC_ERR_SCRATCH before launching anything.
+namespace {
+// True when p is NULL or memory the device can address directly (device or
+// managed); a host pointer given to a kernel would fault the context, so the
+// handle-free entry point rejects it with an error code instead.
+bool device_addressable(const void* p) {
+  if (!p) return true;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+}  // namespace
+
 namespace dqmc {
 dqmc_status greens_on_workspace(void* stream, void* ws, size_t ws_bytes, int batch, int N, int M,
                                 const double* K, double dtau, const double* V, int k, double* G,
@@ -1304,6 +1319,11 @@ dqmc_status greens_on_workspace(void* stream, void* ws, size_t ws_bytes, int bat
   CKS(check_common(h, batch, N, M, K, dtau, V, k));
   h->cur = h->stream;
   if (batch == 0) return DQMC_OK;
+  if ((((uintptr_t)G | (uintptr_t)logdet) & 7) || (((uintptr_t)sign | (uintptr_t)status) & 3))
+    return DQMC_ERR_ARG;
+  for (const void* p : {(const void*)K, (const void*)V, (const void*)G, (const void*)logdet,
+                        (const void*)sign, (const void*)status})
+    if (!device_addressable(p)) return DQMC_ERR_ARG;
   const long long NN = (long long)N * N;
   const int nc = n_chunks(M, k);
   const long long Mp = (long long)(nc + 1) * k;

@@ -16,34 +16,24 @@ namespace {
 constexpr size_t kScratchBytes = 32ull << 20;
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-// Device address of g_scratch per device (host code only ever holds the
-// symbol's host-side stand-in otherwise, which must not reach a kernel).
-constexpr int kMaxDevices = 64;
-void* g_scratch_addr[kMaxDevices] = {nullptr};
-
 }  // namespace
 
 extern "C" dqmc_status dqmc_greens_noalloc(void* stream, int batch, int N, int M, const double* K,
                                            double dtau, const double* V, int k, double* G,
                                            double* logdet, int* sign, int* status) {
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess) {
+  // In host code g_scratch names a host-side stand-in, not device memory, so
+  // the array's device address is looked up in the current context on every
+  // call.  Once the module is loaded this is a table lookup; no address is
+  // cached, so a context created later on the same device (an application
+  // that binds its own context, or one re-created after cudaDeviceReset)
+  // never receives a stale address.  The first call in a context may load the
+  // module, which is why it has to come before any stream capture.
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+  if (e != cudaSuccess || p == nullptr) {
     cudaGetLastError();
     return DQMC_ERR_CUDA;
   }
-  if (dev < 0 || dev >= kMaxDevices) return DQMC_ERR_UNSUPPORTED;
-  if (!g_scratch_addr[dev]) {
-    // one-time set-up on this device (the current one): resolve the array's
-    // device address.  Racing first calls from two host threads store the
-    // same value.
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-    if (e != cudaSuccess || p == nullptr) {
-      cudaGetLastError();
-      return DQMC_ERR_CUDA;
-    }
-    g_scratch_addr[dev] = p;
-  }
-  return dqmc::greens_on_workspace(stream, g_scratch_addr[dev], kScratchBytes, batch, N, M, K,
-                                   dtau, V, k, G, logdet, sign, status);
+  return dqmc::greens_on_workspace(stream, p, kScratchBytes, batch, N, M, K, dtau, V, k, G,
+                                   logdet, sign, status);
 }
