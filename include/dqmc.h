@@ -364,6 +364,20 @@ dqmc_status dqmc_greens_noalloc(void* stream, int batch, int N, int M, const dou
  * Returns DQMC_ERR_ARG for a NULL status, DQMC_ERR_CUDA if the launch fails. */
 dqmc_status dqmc_selftest_wait_timeout(void* stream, int* status);
 
+/* FP64 arithmetic rate of the current device, the denominator of the FP64
+ * rooflines.  The paper has no counterpart: this measures the machine.
+ *   kind 0  DFMA: fma.rn.f64 on independent chains, 2 flop per lane;
+ *   kind 1  DMMA: mma.sync m8n8k4 f64 (512 flop per warp instruction);
+ *   kind 2  DMMA: mma.sync m16n8k8 f64 (2048 flop per warp instruction).
+ * One warm-up launch and one timed launch of `iters` loop iterations (about
+ * 40 MFLOP per iteration for kinds 0 and 1, 160 MFLOP for kind 2) on 4 CTAs
+ * of 256 threads per SM, on `stream` (a cudaStream_t, NULL = legacy default
+ * stream), timed with CUDA events.  Synchronous: returns the achieved rate in
+ * *tflops (TFLOP/s) and the launch time in *ms (may be NULL).  Allocates and
+ * frees a small device buffer.  Errors: DQMC_ERR_ARG (NULL tflops, kind not
+ * 0..2, iters outside 1..2^24), DQMC_ERR_NOMEM, DQMC_ERR_CUDA. */
+dqmc_status dqmc_selftest_fp64_rate(void* stream, int kind, int iters, double* tflops, double* ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -21,7 +21,8 @@ from . import _abi
 __all__ = ["Handle", "greens", "logdet", "greens_tdisplaced", "greens_tdisplaced_all",
            "greens_tdisplaced_from",
            "logdet_grad", "greens_ragged",
-           "greens_tdisplaced_ragged", "logdet_grad_ragged", "selftest_wait_timeout", "LogDet",
+           "greens_tdisplaced_ragged", "logdet_grad_ragged", "selftest_wait_timeout",
+           "selftest_fp64_rate", "LogDet",
            "n_tau", "lib"]
 
 
@@ -415,13 +416,26 @@ def selftest_wait_timeout(status: torch.Tensor, stream: torch.cuda.Stream | None
 class LogDet(torch.autograd.Function):
     """log|det(1 + B_M...B_1)| as a differentiable function of V (B, M, N).
 
-    backward uses the library's adjoint kernel: d logdet / dV_l(i) = 1 - G_l(i,i)."""
+    backward uses the library's adjoint kernel: d logdet / dV_l(i) = 1 - G_l(i,i).
+    When no gradient with respect to V is wanted (V does not require grad, or
+    under torch.no_grad) the forward pass is the log det alone (dqmc_logdet:
+    one chain and one inversion); otherwise it computes log det and the
+    gradient in one dqmc_logdet_grad call and keeps the gradient for backward."""
+
+    @classmethod
+    def apply(cls, V, K, dtau, k, handle=None):
+        # forward runs with grad mode off, so whether a gradient is wanted at
+        # all (V requires grad and grad mode is on) is decided here
+        if not (torch.is_grad_enabled() and V.requires_grad):
+            ld, sg, st = logdet(K, dtau, V, k, handle=handle)
+            return ld
+        return super().apply(V, K, dtau, k, handle)
 
     @staticmethod
     def forward(ctx, V, K, dtau, k, handle=None):
+        ctx.squeeze = V.dim() == 2
         ld, sg, dV, st = logdet_grad(K, dtau, V, k, handle=handle)
         ctx.save_for_backward(dV)
-        ctx.squeeze = V.dim() == 2
         return ld
 
     @staticmethod
@@ -430,3 +444,20 @@ class LogDet(torch.autograd.Function):
         if ctx.squeeze:
             return gout * dV, None, None, None, None
         return gout[:, None, None] * dV, None, None, None, None
+
+
+FP64_RATE_KINDS = {"dfma": 0, "dmma_m8n8k4": 1, "dmma_m16n8k8": 2}
+
+
+def selftest_fp64_rate(kind: str = "dfma", iters: int | None = None) -> tuple[float, float]:
+    """Measured FP64 rate of the current device: (TFLOP/s, launch ms) of the
+    DFMA or FP64 mma.sync loop kernel, on the current torch stream."""
+    code = FP64_RATE_KINDS[kind]
+    if iters is None:
+        iters = 1500 if code == 2 else 6000
+    tf = C.c_double()
+    ms = C.c_double()
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    _abi.check(lib().dqmc_selftest_fp64_rate(stream, code, int(iters), C.byref(tf), C.byref(ms)),
+               "dqmc_selftest_fp64_rate")
+    return tf.value, ms.value

@@ -64,6 +64,7 @@ SIGNATURES = {
     "dqmc_greens_ragged": (_I, [_P, _I, C.POINTER(DqmcInstance), _P, _P, _P, _P, _P, _P]),
     "dqmc_greens_noalloc": (_I, [_P, _I, _I, _I, _P, _D, _P, _I, _P, _P, _P, _P]),
     "dqmc_selftest_wait_timeout": (_I, [_P, _P]),
+    "dqmc_selftest_fp64_rate": (_I, [_P, _I, _I, C.POINTER(_D), C.POINTER(_D)]),
     "dqmc_set_graph_mode": (_I, [_P, _I]),
     "dqmc_greens_tdisplaced_ragged": (_I, [_P, _I, C.POINTER(DqmcInstance), _P, _P, _P, _P, _P]),
     "dqmc_greens_tdisplaced_ragged_ex": (_I, [_P, _I, C.POINTER(DqmcInstance), _P, _P, _P, _P, _P,

@@ -8,6 +8,19 @@
 
 namespace dqmc {
 
+// SM count of the current device (queried once per device index and kept:
+// it is a property of the GPU, not of a context).
+int device_sms();
+
+// Grid of a grid-stride element-wise kernel over n items with tpb threads per
+// block: enough blocks for n, at most 64 per SM of the current device.
+inline int grid_stride_blocks(long long n, int tpb) {
+  long long g = (n + tpb - 1) / tpb;
+  const long long cap = 64LL * device_sms();
+  if (g > cap) g = cap;
+  return (int)(g < 1 ? 1 : g);
+}
+
 // ---------------------------------------------------------------------------
 // Batched FP64 GEMM with fused diagonal scalings (the slice-chain product of
 // Sec. 2, Eq. (Ztr) and every dense product of the inversion schemes).

@@ -8,13 +8,29 @@
 
 namespace dqmc {
 
+int device_sms() {
+  constexpr int kMaxDev = 64;
+  static int cache[kMaxDev] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 152;
+  }
+  if (dev >= 0 && dev < kMaxDev && __atomic_load_n(&cache[dev], __ATOMIC_RELAXED) > 0)
+    return __atomic_load_n(&cache[dev], __ATOMIC_RELAXED);
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      sms <= 0) {
+    cudaGetLastError();
+    return 152;
+  }
+  if (dev >= 0 && dev < kMaxDev) __atomic_store_n(&cache[dev], sms, __ATOMIC_RELAXED);
+  return sms;
+}
+
 namespace {
 constexpr int TPB = 256;
-inline int nblocks(long long n) {
-  long long g = (n + TPB - 1) / TPB;
-  if (g > 152LL * 64) g = 152LL * 64;
-  return (int)(g < 1 ? 1 : g);
-}
+inline int nblocks(long long n) { return grid_stride_blocks(n, TPB); }
 
 __device__ __forceinline__ double dmode(double d, int mode) {
   switch (mode) {

@@ -7,11 +7,7 @@ namespace dqmc {
 
 namespace {
 constexpr int TPB = 256;
-inline int nblocks(long long n) {
-  long long g = (n + TPB - 1) / TPB;
-  if (g > 152LL * 64) g = 152LL * 64;
-  return (int)(g < 1 ? 1 : g);
-}
+inline int nblocks(long long n) { return grid_stride_blocks(n, TPB); }
 }  // namespace
 
 // out[(b*Mp + l)*N + i] = exp(V_pool[offV[b] + l*N + i]) for l < Mb[b], 1 beyond.

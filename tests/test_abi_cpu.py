@@ -62,3 +62,15 @@ def test_product_path_has_no_cpu_fallback():
         src = open(f).read()
         assert "oracle" not in src.replace("oracle`", ""), f
         assert "numpy.linalg" not in src and "scipy" not in src, f
+
+
+def test_fp64_rate_rejects_bad_arguments(lib):
+    """Argument checks run before any CUDA call (no GPU needed)."""
+    f = lib.dqmc_selftest_fp64_rate
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                  ctypes.POINTER(ctypes.c_double)]
+    tf = ctypes.c_double()
+    assert f(None, 0, 100, None, None) == 1                 # NULL result pointer
+    assert f(None, 3, 100, ctypes.byref(tf), None) == 1     # unknown kind
+    assert f(None, 0, 0, ctypes.byref(tf), None) == 1       # no iterations

@@ -43,6 +43,12 @@ def test_reference_metric_matches_workload():
     assert (d["metric"], d["unit"]) == bench.METRICS["grad_n144"] == ("logdet_gradients_per_second",
                                                                       "grads/s")
     assert d["impl"] == "reference" and d["value"] > 0
-    # one sample is a fraction of a gradient: 2 of the M = 200 slices
-    assert abs(d["config"]["instances_per_step"] - 2 / 200) < 1e-12
+    # one sample is a fraction of a gradient: 2 of the M = 200 slices; a step
+    # is one sample (mode B) or one sample per process of the pool (mode A)
+    per = d["config"]["instances_per_step"] / (2 / 200)
+    assert abs(per - round(per)) < 1e-9 and round(per) >= 1
+    assert d["config"]["cpu_mode"] in ("pool", "threads")
+    if d["config"]["cpu_mode"] == "threads":
+        assert round(per) == 1
     assert d["cpu_baseline"]["unit"] == "grads/s"
+    assert d["cpu_baseline"]["cpu_model"]

@@ -70,6 +70,33 @@ def test_logdet_autograd(dq):
     assert torch.allclose(V.grad[1], -2.0 * dV[1], atol=0, rtol=0)
 
 
+def test_logdet_forward_paths(dq):
+    """LogDet.forward: the log det alone when no gradient is wanted, log det +
+    gradient otherwise; both against the oracle, and the forward-only call
+    launches fewer kernels (one chain and one inversion, no stacks or wraps)."""
+    inst = di.gaussian_instance(4, 1.5, 0.1, 3.0, 10, 11)
+    K = _dev(inst.K)
+    ldo, _ = od.logdet(inst.K, 0.1, inst.V, 10)
+    dVo = od.logdet_grad(inst.K, 0.1, inst.V, 10)
+    h = dq.Handle()
+    V0 = _dev(inst.V)                                   # no grad wanted
+    ld0 = dq.LogDet.apply(V0, K, 0.1, 10, h)
+    n_fwd = h.last_launch_count
+    assert not ld0.requires_grad
+    assert abs(float(ld0) - ldo) <= 1e-9 * max(1.0, abs(ldo))
+    V1 = _dev(inst.V).requires_grad_(True)
+    with torch.no_grad():
+        ld1 = dq.LogDet.apply(V1, K, 0.1, 10, h)
+    assert h.last_launch_count == n_fwd
+    assert float(ld1) == float(ld0)
+    ld2 = dq.LogDet.apply(V1, K, 0.1, 10, h)
+    assert h.last_launch_count > n_fwd
+    assert abs(float(ld2) - ldo) <= 1e-9 * max(1.0, abs(ldo))
+    ld2.backward()
+    assert np.abs(V1.grad.cpu().numpy() - dVo).max() <= DTOL
+    h.close()
+
+
 def test_grad_full_size_sampled(dq):
     """12x12 lattice, phi ~ N(0,1), g=1.5, dtau=0.1, beta=20 (M=200), k=10, 64
     instances in one call; instance 0 and 63 checked at sampled slices."""
