@@ -268,13 +268,19 @@ def oracle_sampler(name: str, n_inst: int = 4):
     from oracle import dqmc as od
     wl = WORKLOADS[name]
     if name == "ragged_1024":
-        insts = [di.ragged_instance(i, 10) for i in range(n_inst)]
+        # the first RAGGED_SAMPLE instances of the workload itself, so that the
+        # sample has the workload's mix of N and M (built on first use)
+        insts = {}
 
         def run(i):
-            x = insts[i % len(insts)]
+            j = i % RAGGED_SAMPLE
+            if j not in insts:
+                insts[j] = di.ragged_instance(j, 10)
+            x = insts[j]
             od.greens(x.K, x.dtau, x.V, x.k)
             return 1.0
-        return run, "equal-time G of the uneven-size instances one after another (k = 10)"
+        return run, (f"equal-time G of instances i mod {RAGGED_SAMPLE} of the uneven-size "
+                     f"workload (its own mix of N and M, k = 10)")
     if name == "grad_n144":
         insts = [di.gaussian_instance(wl["L"], wl["g"], wl["dtau"], wl["beta"], wl["k"], sd)
                  for sd in rank_seeds(wl, 0, n_inst)]
@@ -321,6 +327,7 @@ def cpu_rate_threads(name: str, seconds: float):
 
 
 _POOL_SAMPLERS = {}
+RAGGED_SAMPLE = 64      # instances of the ragged workload in its CPU sample
 
 
 def _pool_run(name: str):
@@ -384,6 +391,14 @@ class OraclePool:
                                  chunksize=1))
 
     def timed(self, name: str, seconds: float):
+        if name == "ragged_1024":
+            # every instance of the sample once (their costs differ by ~100x,
+            # so a time budget per process would bias the mix)
+            t0 = time.perf_counter()
+            units = sum(self.pool.map(_pool_sample, [(name, i) for i in range(RAGGED_SAMPLE)],
+                                      chunksize=1))
+            wall = time.perf_counter() - t0
+            return units / wall, RAGGED_SAMPLE, wall
         res = self.pool.map(_pool_timed, [(name, w, self.cores, seconds)
                                           for w in range(self.cores)], chunksize=1)
         units = sum(r[0] for r in res)
@@ -635,8 +650,8 @@ def run_gpu(args, wl, rank, world):
         # error against the CPU oracle on sampled instances (outside the timed region)
         if args.oracle_samples > 0:
             from oracle import dqmc as od
-            picks = sorted({0, batch - 1} | set(range(0, batch, max(1, batch // max(1, args.oracle_samples)))))
-            picks = picks[:max(2, args.oracle_samples)]
+            n_pick = max(2, args.oracle_samples)
+            picks = sorted({round(i * (batch - 1) / (n_pick - 1)) for i in range(n_pick)})
             eg, el, e64 = [], [], []
             for b in picks:
                 Go, ldo, so = od.greens(insts[b].K, insts[b].dtau, insts[b].V, insts[b].k)
