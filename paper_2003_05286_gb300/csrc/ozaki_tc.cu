@@ -231,6 +231,7 @@ ozaki_gemm_kernel(const __nv_bfloat16* __restrict__ As, long long sA, int P128,
   uint64_t* done = bars + 2 * OZ_STAGES;    // [1]
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * OZ_STAGES + 1);
   int* s_fail = reinterpret_cast<int*>(tmem_holder + 1);
+  int* s_used = s_fail + 1;   // K-blocks whose operands the MMA issuer has waited for
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int n0 = blockIdx.x * OZ_BN, m0 = blockIdx.y * OZ_BM, b = blockIdx.z;
@@ -245,6 +246,7 @@ ozaki_gemm_kernel(const __nv_bfloat16* __restrict__ As, long long sA, int P128,
     }
     mbar_init(done, 1);
     *s_fail = 0;
+    *s_used = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -298,6 +300,7 @@ ozaki_gemm_kernel(const __nv_bfloat16* __restrict__ As, long long sA, int P128,
         atomicOr(s_fail, 1);
         break;
       }
+      *(volatile int*)s_used = kb + 1;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       // descriptors: the stage's base descriptor plus tile offsets in its
       // start-address field (address >> 4; shared addresses stay below 256 KB,
@@ -382,9 +385,13 @@ ozaki_gemm_kernel(const __nv_bfloat16* __restrict__ As, long long sA, int P128,
   } else if (tid == 0 && status) {
     atomicOr(&status[b], DQMC_STATUS_TIMEOUT);
   }
-  // on failure, let in-flight copies land before the CTA exits (bounded)
+  // on failure, let copies in flight land before the CTA exits (bounded).  A
+  // stage is refilled only after the MMAs consumed its previous contents, so
+  // only the K-blocks s_used and s_used + 1 can still have copies on the way.
   if (!ok && warp == 0 && lane == 0) {
-    for (int i = 0; i < OZ_STAGES; ++i) mbar_wait(&full[i], 0);
+    const int used = *(volatile int*)s_used;
+    for (int kb = used; kb < used + OZ_STAGES && kb < nkb; ++kb)
+      mbar_wait(&full[kb % OZ_STAGES], (kb / OZ_STAGES) & 1);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -398,60 +405,108 @@ ozaki_gemm_kernel(const __nv_bfloat16* __restrict__ As, long long sA, int P128,
 // ---------------------------------------------------------------------------
 // Splitting kernel: X (FP64, element (m, j) at X[g(m)*ldm + j*ldj], g the
 // optional row gather gm, identity if null) times an optional scale sc[m]
-// -> s BF16 slice planes of PJ x PM (zero padded), each stored as tiles of R
+// -> S BF16 slice planes of PJ x PM (zero padded), each stored as tiles of R
 // rows j by 32 consecutive m (tile (j / R, m / 32) at ((j / R)(PM / 32) +
 // m / 32) R 32 elements; inside, row r's 16-byte chunk c at chunk c ^ ((r >> 1)
 // & 3): the 64-byte swizzle), and column exponents e[j] with
 // max_m |x_mj| < 2^{e_j}.
-// One CTA per 32 columns j of one instance; 256 threads.
+// One CTA per 32 columns j of one instance; 256 threads.  Phase 1 stages the
+// 32 columns in shared memory (coalesced rows) and finds each column's
+// exponent; phase 2 gives every thread whole 16-byte chunks (8 consecutive m
+// of one column j), so each digit plane gets one 16-byte store per chunk and
+// the four lanes of a column cover one 64-byte tile row (a warp writes 512
+// contiguous bytes per plane).  Digits and their BF16 encodings are built with
+// integer operations only.
 // ---------------------------------------------------------------------------
+namespace {
+// BF16 bits of an integer d with |d| <= 128 (exact: at most 8 significant bits)
+__device__ __forceinline__ uint32_t small_int_bf16(int d) {
+  if (d == 0) return 0u;
+  const uint32_t sgn = d < 0 ? 0x8000u : 0u;
+  const uint32_t a = (uint32_t)(d < 0 ? -d : d);
+  const int e = 31 - __clz((int)a);                     // 0..7
+  const uint32_t mant = (a << (7 - e)) & 0x7Fu;
+  return sgn | ((uint32_t)(e + 127) << 7) | mant;
+}
+}  // namespace
+
+template <int SL>
 __global__ void __launch_bounds__(256)
 ozaki_split_kernel(const double* __restrict__ X, long long ldm, long long ldj, long long sX,
-                   const double* __restrict__ sc, long long ssc, int N, int PJ, int PM, int R, int s,
+                   const double* __restrict__ sc, long long ssc, int N, int PJ, int PM, int R,
                    __nv_bfloat16* __restrict__ S, long long sS, int* __restrict__ e,
                    long long se, const int* __restrict__ gm, long long sgm) {
   extern __shared__ double tile[];   // [PM][33]
   __shared__ int emax[8][32];
   const int b = blockIdx.y;
   const int j0 = blockIdx.x * 32;
-  const int tid = threadIdx.x, jj = tid & 31, rg = tid >> 5;
+  const int tid = threadIdx.x;
   const double* Xb = X + (long long)b * sX;
   const double* scb = sc ? sc + (long long)b * ssc : nullptr;
   const int* gmb = gm ? gm + (long long)b * sgm : nullptr;
-  const int j = j0 + jj;
-  int mx = -2000;
-  for (int m = rg; m < PM; m += 8) {
-    double v = 0.0;
-    if (m < N && j < N) {
-      const int mr = gmb ? gmb[m] : m;
-      v = (mr >= 0 && mr < N) ? Xb[(long long)mr * ldm + (long long)j * ldj] : 0.0;
-      if (scb) v *= scb[m];
+  {
+    // rows rg, rg + 8, ...: eight loads (and their gather indices) in flight
+    // per thread before any is used, so a thread waits for one memory round
+    // trip per eight rows instead of one per row
+    const int jj = tid & 31, rg = tid >> 5;
+    const int j = j0 + jj;
+    int mx = 0;
+    for (int mb = rg; mb < PM; mb += 64) {
+      int mr[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int m = mb + 8 * u;
+        mr[u] = (m < N && j < N) ? (gmb ? gmb[m] : m) : -1;
+      }
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        v[u] = (mr[u] >= 0 && mr[u] < N) ? Xb[(long long)mr[u] * ldm + (long long)j * ldj] : 0.0;
+      if (scb) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int m = mb + 8 * u;
+          if (m < N) v[u] *= scb[m];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int m = mb + 8 * u;
+        if (m < PM) tile[m * 33 + jj] = v[u];
+        // biased exponent from the bits (0 for zeros): no FP64 compare
+        const int ex = (int)((__double_as_longlong(v[u]) >> 52) & 0x7ff);
+        mx = ex > mx ? ex : mx;
+      }
     }
-    tile[m * 33 + jj] = v;
-    if (v != 0.0) {
-      int ex = (int)((__double_as_longlong(v) >> 52) & 0x7ff);
-      if (ex > mx) mx = ex;
-    }
+    emax[rg][jj] = mx;
   }
-  emax[rg][jj] = mx;
   __syncthreads();
   if (tid < 32) {
     int m2 = emax[0][tid];
     for (int r = 1; r < 8; ++r) m2 = max(m2, emax[r][tid]);
     // biased exponent E of the largest entry: max < 2^{E-1022}, so the scaled
-    // entries x 2^{-(E-1021)} lie in (-1/2, 1/2)
-    emax[0][tid] = (m2 == -2000 || m2 == 0) ? 0 : m2 - 1021;
-    if (j0 + tid < PJ) e[(long long)b * se + j0 + tid] = (m2 == -2000 || m2 == 0) ? 0 : m2 - 1021;
+    // entries x 2^{-(E-1021)} lie in (-1/2, 1/2); an all-zero (or denormal)
+    // column keeps exponent 0
+    const int ecol = m2 == 0 ? 0 : m2 - 1021;
+    emax[0][tid] = ecol;
+    if (j0 + tid < PJ) e[(long long)b * se + j0 + tid] = ecol;
   }
   __syncthreads();
   __nv_bfloat16* Sb = S + (long long)b * sS;
   const long long plane = (long long)PJ * PM;
-  for (int c = 0; c < 32; ++c) {
-    const int jc = j0 + c;
-    if (jc >= PJ) break;
-    const int ecol = emax[0][c];
-    for (int m = tid; m < PM; m += 256) {
-      const double v = tile[m * 33 + c];
+  // work items: (column jj, K-block kb) pairs; 4 lanes per item, lane ch = chunk
+  const int ch = tid & 3;
+  const int nkb = PM / 32;
+  for (int it = tid >> 2; it < 32 * nkb; it += 64) {
+    const int jj = it & 31, kb = it >> 5;
+    const int jc = j0 + jj;
+    if (jc >= PJ) continue;
+    const int ecol = emax[0][jj];
+    const int m0 = kb * 32 + ch * 8;
+    long long Sv[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const double v = tile[(m0 + k) * 33 + jj];
       unsigned long long F = 0;   // |v| 2^{-ecol} * 2^63, below 2^62
       const long long bits = __double_as_longlong(v);
       const int E = (int)((bits >> 52) & 0x7ff);
@@ -460,19 +515,27 @@ ozaki_split_kernel(const double* __restrict__ X, long long ldm, long long ldj, l
         const int sh = E - 1012 - ecol;   // F = m53 * 2^sh, sh <= 9
         F = sh >= 0 ? (m53 << sh) : (sh > -64 ? (m53 >> (-sh)) : 0ull);
       }
-      long long S = bits < 0 ? -(long long)F : (long long)F;
-      // element (row jc, k = m) of the R x 32 tile (row block jc / R, K-block
-      // m / 32), rows of 64 bytes whose 16-byte chunks are permuted as the
-      // tensor core's 64-byte swizzle expects them in shared memory
-      const int jr = jc % R, mk = m & 31, ch = mk >> 3;
-      const long long tile_off = ((long long)(jc / R) * (PM / 32) + (m >> 5)) * (R * 32) +
-                                 jr * 32 + ((ch ^ ((jr >> 1) & 3)) << 3) + (mk & 7);
-      for (int q = 0; q < s; ++q) {
-        const int sh = 56 - 7 * q;                      // digit weight 2^{-7(q+1)}
-        const long long d = (S + (1ll << (sh - 1))) >> sh;   // nearest, in [-64, 64]
-        S -= d << sh;
-        Sb[q * plane + tile_off] = __int2bfloat16_rn((int)d);
+      Sv[k] = bits < 0 ? -(long long)F : (long long)F;
+    }
+    // element (row jc, k = m) of the R x 32 tile (row block jc / R, K-block kb):
+    // this thread's 8 values form 16-byte chunk ch of tile row jr, stored at
+    // chunk ch ^ ((jr >> 1) & 3) (the 64-byte swizzle)
+    const int jr = jc % R;
+    const long long tile_off = ((long long)(jc / R) * nkb + kb) * (R * 32) + jr * 32 +
+                               ((ch ^ ((jr >> 1) & 3)) << 3);
+#pragma unroll
+    for (int q = 0; q < SL; ++q) {
+      const int sh = 56 - 7 * q;                        // digit weight 2^{-7(q+1)}
+      uint32_t w[4];
+#pragma unroll
+      for (int k = 0; k < 8; k += 2) {
+        const long long d0 = (Sv[k] + (1ll << (sh - 1))) >> sh;       // nearest, in [-64, 64]
+        const long long d1 = (Sv[k + 1] + (1ll << (sh - 1))) >> sh;
+        Sv[k] -= d0 << sh;
+        Sv[k + 1] -= d1 << sh;
+        w[k >> 1] = small_int_bf16((int)d0) | (small_int_bf16((int)d1) << 16);
       }
+      *reinterpret_cast<uint4*>(Sb + q * plane + tile_off) = make_uint4(w[0], w[1], w[2], w[3]);
     }
   }
 }
@@ -523,12 +586,27 @@ cudaError_t ozaki_split(const double* X, long long ldm, long long ldj, long long
                         __nv_bfloat16* S, long long sS, int* e, long long se, int batch,
                         cudaStream_t st, const int* gm, long long sgm) {
   if (R < 8 || PJ % R || PM % 32) return cudaErrorInvalidValue;
-  size_t sm = (size_t)PM * 33 * sizeof(double);
-  cudaFuncSetAttribute(ozaki_split_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  dim3 grid((PJ + 31) / 32, batch);
-  ozaki_split_kernel<<<grid, 256, sm, st>>>(X, ldm, ldj, sX, sc, ssc, N, PJ, PM, R, s, S, sS, e,
-                                            se, gm, sgm);
-  return cudaGetLastError();
+  if (s < 1 || s > 8) return cudaErrorInvalidValue;
+  // 16-byte chunk stores: plane and instance strides must keep 16-byte alignment
+  if (((long long)PJ * PM) % 8 || sS % 8 || (reinterpret_cast<uintptr_t>(S) & 15))
+    return cudaErrorInvalidValue;
+  const size_t sm = (size_t)PM * 33 * sizeof(double);
+  const dim3 grid((PJ + 31) / 32, batch);
+  auto go = [&](auto kern) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    kern<<<grid, 256, sm, st>>>(X, ldm, ldj, sX, sc, ssc, N, PJ, PM, R, S, sS, e, se, gm, sgm);
+    return cudaGetLastError();
+  };
+  switch (s) {
+    case 1: return go(ozaki_split_kernel<1>);
+    case 2: return go(ozaki_split_kernel<2>);
+    case 3: return go(ozaki_split_kernel<3>);
+    case 4: return go(ozaki_split_kernel<4>);
+    case 5: return go(ozaki_split_kernel<5>);
+    case 6: return go(ozaki_split_kernel<6>);
+    case 7: return go(ozaki_split_kernel<7>);
+    default: return go(ozaki_split_kernel<8>);
+  }
 }
 
 // C_b = 2^{eA_b} As_b * (2^{eB_b} Bs_b)  for b < batch.  As: s planes of

@@ -402,16 +402,35 @@ namespace {
 // N): x_r -= va[r] w (stored if store), returns sum vb[r] x_r over the updated
 // values and sets xpick to the updated value of row rpick if this thread has
 // it.  Loads run one batch of B rows ahead of the stores.
+//
+// Every FP64 warp instruction holds the sub-partition's FP64 pipe for 64
+// cycles on this part whether or not its lanes are predicated off, so the
+// full batches carry no row guards and the last n mod B rows are processed in
+// unguarded blocks of 4, 2 and 1 (register shifts keep the indices static)
+// instead of B guarded slots.
+template <int TPC>
+__device__ __forceinline__ void fused_row(double* __restrict__ M, int N, int c, int r,
+                                          const double* va, double w, const double* vb, int rpick,
+                                          double& xpick, bool store, double xv, double& acc) {
+  const double x = fma(-va[r], w, xv);
+  if (store) M[(long long)r * N + c] = x;
+  acc = fma(vb[r], x, acc);
+  if (r == rpick) xpick = x;
+}
+
 template <int TPC, int B>
 __device__ __forceinline__ double fused_pass(double* __restrict__ M, int N, int c, int r0,
                                              const double* va, double w, const double* vb,
                                              int rpick, double& xpick, bool store) {
+  static_assert(B == 8, "the tail decomposition assumes batches of 8 rows");
   const int n = r0 < N ? (N - r0 + TPC - 1) / TPC : 0;
+  const int nfull = n - n % B;
   double acc0 = 0.0, acc1 = 0.0;
   double xc[B];
 #pragma unroll
   for (int k = 0; k < B; ++k) xc[k] = k < n ? M[(long long)(r0 + k * TPC) * N + c] : 0.0;
-  for (int i = 0; i < n; i += B) {
+  int i = 0;
+  for (; i < nfull; i += B) {
     double xn[B];
 #pragma unroll
     for (int k = 0; k < B; ++k) {
@@ -419,18 +438,32 @@ __device__ __forceinline__ double fused_pass(double* __restrict__ M, int N, int 
       xn[k] = t < n ? M[(long long)(r0 + t * TPC) * N + c] : 0.0;
     }
 #pragma unroll
-    for (int k = 0; k < B; ++k) {
-      if (i + k < n) {
-        const int r = r0 + (i + k) * TPC;
-        const double x = fma(-va[r], w, xc[k]);
-        if (store) M[(long long)r * N + c] = x;
-        if (k & 1) acc1 = fma(vb[r], x, acc1); else acc0 = fma(vb[r], x, acc0);
-        if (r == rpick) xpick = x;
-      }
-    }
+    for (int k = 0; k < B; ++k)
+      fused_row<TPC>(M, N, c, r0 + (i + k) * TPC, va, w, vb, rpick, xpick, store, xc[k],
+                     (k & 1) ? acc1 : acc0);
 #pragma unroll
     for (int k = 0; k < B; ++k) xc[k] = xn[k];
   }
+  // tail: rows i .. n-1 (fewer than B), already loaded into xc[0 ..]
+  const int rem = n - i;
+  if (rem & 4) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      fused_row<TPC>(M, N, c, r0 + (i + k) * TPC, va, w, vb, rpick, xpick, store, xc[k],
+                     (k & 1) ? acc1 : acc0);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) xc[k] = xc[k + 4];
+    i += 4;
+  }
+  if (rem & 2) {
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+      fused_row<TPC>(M, N, c, r0 + (i + k) * TPC, va, w, vb, rpick, xpick, store, xc[k],
+                     (k & 1) ? acc1 : acc0);
+    xc[0] = xc[2];
+    i += 2;
+  }
+  if (rem & 1) fused_row<TPC>(M, N, c, r0 + i * TPC, va, w, vb, rpick, xpick, store, xc[0], acc0);
   return acc0 + acc1;
 }
 
@@ -616,47 +649,53 @@ __global__ void __launch_bounds__(NT) qrp_fused_kernel(const QrpArgs a) {
 
     // ---- steps j = 0 .. N-2 ------------------------------------------------
     for (int j = 0; j + 1 < N; ++j) {
-      const double tau = taus[j];
       const bool act = own && c > j;
-      const double w = tau * dc;
-      const double rjc = xj - w;
-      const double n_old = act ? nrm2[c] : 0.0, r_old = act ? ref2[c] : 0.0;
-      double n2 = fma(-rjc, rjc, n_old);
-      const bool redo = act && n2 <= 1.4901161193847656e-8 * r_old;
-      if (__any_sync(FULL, redo)) {
-        // exact norm of the updated rows below j where the downdate lost too
-        // many digits (the safeguard of LAPACK's xLAQP2)
-        double ex = 0.0;
-        if (redo)
-          for (int r = j + 1 + ((rg - j - 1) % TPC + TPC) % TPC; r < N; r += TPC) {
-            const double x = fma(-vcur[r], w, W[(long long)r * N + c]);
-            ex = fma(x, x, ex);
-          }
-        ex = group_sum<TPC>(ex);
-        if (redo) n2 = ex;
-      }
-      __syncwarp();
       float key = -INFINITY;
       int idx = 0x7fffffff;
-      if (act) {
-        if (rg == 0) {
-          wsm[c] = w;
-          nrm2[c] = n2;
-          if (redo) ref2[c] = n2;
+      // warps whose columns are all at or left of j skip the column scalars
+      // (each of them would still hold an FP64 pipe for 64 cycles)
+      if (__any_sync(FULL, act)) {
+        const double tau = taus[j];
+        const double w = tau * dc;
+        const double rjc = xj - w;
+        const double n_old = act ? nrm2[c] : 0.0, r_old = act ? ref2[c] : 0.0;
+        double n2 = fma(-rjc, rjc, n_old);
+        const bool redo = act && n2 <= 1.4901161193847656e-8 * r_old;
+        if (__any_sync(FULL, redo)) {
+          // exact norm of the updated rows below j where the downdate lost too
+          // many digits (the safeguard of LAPACK's xLAQP2)
+          double ex = 0.0;
+          if (redo)
+            for (int r = j + 1 + ((rg - j - 1) % TPC + TPC) % TPC; r < N; r += TPC) {
+              const double x = fma(-vcur[r], w, W[(long long)r * N + c]);
+              ex = fma(x, x, ex);
+            }
+          ex = group_sum<TPC>(ex);
+          if (redo) n2 = ex;
         }
-        key = logd[c] + 0.5f * log2_wide(n2);
-        idx = c;
+        __syncwarp();
+        if (act) {
+          if (rg == 0) {
+            wsm[c] = w;
+            nrm2[c] = n2;
+            if (redo) ref2[c] = n2;
+          }
+          key = logd[c] + 0.5f * log2_wide(n2);
+          idx = c;
+        }
       }
       vote_and_reflect(key, idx, j + 1);
       // ---- fused pass: update with v_j, dot with v_{j+1} --------------------
-      double dn = 0.0, xn = 0.0;
-      if (own && c > j + 1) {
-        const int r0 = j + ((rg - j) % TPC + TPC) % TPC;   // first row >= j in this row group
-        dn = fused_pass<TPC, BATCH>(W, N, c, r0, vcur, wsm[c], vnxt, j + 1, xn, true);
+      if (__any_sync(FULL, own && c > j + 1)) {
+        double dn = 0.0, xn = 0.0;
+        if (own && c > j + 1) {
+          const int r0 = j + ((rg - j) % TPC + TPC) % TPC;   // first row >= j in this row group
+          dn = fused_pass<TPC, BATCH>(W, N, c, r0, vcur, wsm[c], vnxt, j + 1, xn, true);
+        }
+        dn = group_sum<TPC>(dn);
+        xj = __shfl_sync(FULL, xn, (lane % CPW) + CPW * ((j + 1) % TPC));
+        dc = dn;
       }
-      dn = group_sum<TPC>(dn);
-      xj = __shfl_sync(FULL, xn, (lane % CPW) + CPW * ((j + 1) % TPC));
-      dc = dn;
       double* t = vcur; vcur = vnxt; vnxt = t;
     }
     __syncthreads();
@@ -682,16 +721,18 @@ __global__ void __launch_bounds__(NT) qrp_fused_kernel(const QrpArgs a) {
         double* vs = vq((N + 1 - j) % 3);
         for (int r = tid; r < N; r += NT) vs[r] = r >= j - 2 ? T[(long long)(j - 2) * N + r] : 0.0;
       }
-      if (own && c >= j) {
-        if (c == j) dq = 1.0;
-        const double w = taus[j] * dq;
-        const int r0 = j + ((rg - j) % TPC + TPC) % TPC;
-        double xdummy = 0.0;
-        // rows >= j of column c; the dot with v_{j-1} needs no row j-1 (zero
-        // in every column c >= j at this point)
-        dq = fused_pass<TPC, BATCH>(U, N, c, r0, vj, w, j > 0 ? vm : vj, -1, xdummy, true);
+      if (__any_sync(FULL, own && c >= j)) {
+        if (own && c >= j) {
+          if (c == j) dq = 1.0;
+          const double w = taus[j] * dq;
+          const int r0 = j + ((rg - j) % TPC + TPC) % TPC;
+          double xdummy = 0.0;
+          // rows >= j of column c; the dot with v_{j-1} needs no row j-1 (zero
+          // in every column c >= j at this point)
+          dq = fused_pass<TPC, BATCH>(U, N, c, r0, vj, w, j > 0 ? vm : vj, -1, xdummy, true);
+        }
+        dq = group_sum<TPC>(dq);
       }
-      dq = group_sum<TPC>(dq);
       __syncthreads();
     }
 
