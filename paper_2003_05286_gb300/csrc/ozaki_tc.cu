@@ -53,6 +53,10 @@ constexpr int OZ_STAGES = 2;
 constexpr int OZ_THREADS = 256;   // 8 warps: two per TMEM lane quarter in the epilogue
 constexpr int OZ_A_TILE = OZ_BM * OZ_BK * 2;   // 8 KB
 constexpr int OZ_B_TILE = OZ_BN * OZ_BK * 2;   // 4 KB
+// B tile slots of a stage: OZ_BZERO zero tiles, then the digit tiles 0 .. s-1,
+// then zero tiles up to slot OZ_BSLOTS - 1 (see the MMA issuer)
+constexpr int OZ_BZERO = 3;
+constexpr int OZ_BSLOTS = OZ_BZERO + 8;
 // FP64 result tile staged in shared memory for coalesced row stores (padded rows)
 constexpr int OZ_C_LD = OZ_BN + 1;
 constexpr int OZ_C_TILE = OZ_BM * OZ_C_LD * 8;   // 66.5 KB
@@ -223,7 +227,9 @@ ozaki_gemm_kernel(const __nv_bfloat16* __restrict__ As, long long sA, int P128,
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   const int s = pr.s;
-  const int stage_bytes = s * (OZ_A_TILE + OZ_B_TILE);
+  const int a_bytes = s * OZ_A_TILE;
+  const int stage_bytes = a_bytes + OZ_BSLOTS * OZ_B_TILE;   // shared memory per stage
+  const int copy_bytes = s * (OZ_A_TILE + OZ_B_TILE);        // bytes copied into a stage
   const int data_bytes = OZ_STAGES * stage_bytes > OZ_C_TILE ? OZ_STAGES * stage_bytes : OZ_C_TILE;
   uint64_t* bars = reinterpret_cast<uint64_t*>(base + data_bytes);
   uint64_t* full = bars;                    // [OZ_STAGES]
@@ -236,8 +242,9 @@ ozaki_gemm_kernel(const __nv_bfloat16* __restrict__ As, long long sA, int P128,
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int n0 = blockIdx.x * OZ_BN, m0 = blockIdx.y * OZ_BM, b = blockIdx.z;
   const int bA = a_batched ? b : 0;   // instance of the A operand (shared when not batched)
-  uint32_t tmem_cols = 32;
-  while (tmem_cols < (uint32_t)(pr.ngroups * OZ_BN)) tmem_cols <<= 1;
+  // accumulators: weight group g in columns [g OZ_BN, (g + 1) OZ_BN); the MMAs
+  // write groups in aligned blocks of four, so more than four groups take all 512
+  const uint32_t tmem_cols = s > 4 ? 512u : 256u;
 
   if (tid == 0) {
     for (int i = 0; i < OZ_STAGES; ++i) {
@@ -256,6 +263,16 @@ ozaki_gemm_kernel(const __nv_bfloat16* __restrict__ As, long long sA, int P128,
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
+  // zero B tile slots of both stages (never written by the copies), made
+  // visible to the tensor core's (async proxy) reads
+  for (int st = 0; st < OZ_STAGES; ++st) {
+    uint4* zb = reinterpret_cast<uint4*>(base + st * stage_bytes + a_bytes);
+    for (int i = tid; i < OZ_BSLOTS * OZ_B_TILE / 16; i += OZ_THREADS) {
+      const int slot = i / (OZ_B_TILE / 16);
+      if (slot < OZ_BZERO || slot >= OZ_BZERO + s) zb[i] = make_uint4(0u, 0u, 0u, 0u);
+    }
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -271,7 +288,7 @@ ozaki_gemm_kernel(const __nv_bfloat16* __restrict__ As, long long sA, int P128,
       }
       if (*(volatile int*)s_fail) break;
       unsigned char* sb = base + st * stage_bytes;
-      mbar_arrive_expect_tx(&full[st], (uint32_t)stage_bytes);
+      mbar_arrive_expect_tx(&full[st], (uint32_t)copy_bytes);
       // tile (row block, K-block kb) of every digit plane: one contiguous copy each
       const long long PK = (long long)nkb * OZ_BK;
       const __nv_bfloat16* a0 = As + (long long)bA * sA +
@@ -281,19 +298,23 @@ ozaki_gemm_kernel(const __nv_bfloat16* __restrict__ As, long long sA, int P128,
       for (int p = 0; p < s; ++p)
         bulk_load(sb + p * OZ_A_TILE, a0 + (long long)p * P128 * PK, OZ_A_TILE, &full[st]);
       for (int q = 0; q < s; ++q)
-        bulk_load(sb + s * OZ_A_TILE + q * OZ_B_TILE, b0 + (long long)q * PN * PK, OZ_B_TILE,
-                  &full[st]);
+        bulk_load(sb + a_bytes + (OZ_BZERO + q) * OZ_B_TILE, b0 + (long long)q * PN * PK,
+                  OZ_B_TILE, &full[st]);
     }
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer ---------------------------------------------------------
-    // The pairs (p, q) of one A digit p go to the consecutive weight groups
-    // g = p + q (q = 0 .. s-1-p), whose accumulators are adjacent OZ_BN-column
-    // blocks of TMEM, and their B digit tiles are adjacent in the stage: one
-    // MMA with N = n OZ_BN (n <= 4) covers n pairs and reads the A tile once
-    // instead of n times (the operand reads from shared memory, not the
-    // arithmetic, bound the product).
-    const uint32_t idesc1 = oz_idesc(OZ_BN), idesc2 = oz_idesc(2 * OZ_BN),
-                   idesc3 = oz_idesc(3 * OZ_BN), idesc4 = oz_idesc(4 * OZ_BN);
+    // Every MMA has N = 4 OZ_BN and writes one aligned block of four weight
+    // groups: block r (groups 4r .. 4r+3) receives, for each A digit p, one
+    // MMA with the B digits q = 4r - p .. 4r - p + 3, whose products have
+    // weights p + q = 4r .. 4r + 3.  Digits outside 0 .. s-1 read the zero
+    // tiles around the B digits, so every kept pair (p + q <= s - 1) is formed
+    // exactly once.  Consecutive MMAs then either accumulate into the same
+    // block with the same shape, which the tensor core chains at full rate, or
+    // write a disjoint block; MMAs into partially overlapping accumulator
+    // ranges of different widths waited for one another and ran at about a
+    // third of the rate.  The zero padding costs a quarter of the issued work.
+    const uint32_t idesc = oz_idesc(4 * OZ_BN);
+    const int nblk = s > 4 ? 2 : 1;
     for (int kb = 0; kb < nkb; ++kb) {
       const int st = kb % OZ_STAGES;
       if (!mbar_wait(&full[st], (kb / OZ_STAGES) & 1)) {
@@ -306,19 +327,18 @@ ozaki_gemm_kernel(const __nv_bfloat16* __restrict__ As, long long sA, int P128,
       // start-address field (address >> 4; shared addresses stay below 256 KB,
       // so the field never carries)
       const uint64_t dA = smem_desc_sw64(smem_u32(base + st * stage_bytes));
-      const uint64_t dB = dA + (uint64_t)((s * OZ_A_TILE) >> 4);
+      const uint64_t dB = dA + (uint64_t)(a_bytes >> 4);
       for (int kk = 0; kk < OZ_BK / 16; ++kk) {
         const uint64_t dAk = dA + (uint64_t)(kk * 2), dBk = dB + (uint64_t)(kk * 2);
         const bool first_k = kb == 0 && kk == 0;
-        for (int pd = 0; pd < s; ++pd) {
-          const uint64_t ad = dAk + (uint64_t)(pd * (OZ_A_TILE >> 4));
-          // p = 0 reaches every group first: it starts the accumulation
-          const uint32_t acc = (first_k && pd == 0) ? 0u : 1u;
-          for (int q0 = 0; q0 < s - pd; q0 += 4) {
-            const int n = (s - pd - q0) < 4 ? (s - pd - q0) : 4;
-            const uint32_t idesc = n == 4 ? idesc4 : (n == 3 ? idesc3 : (n == 2 ? idesc2 : idesc1));
-            umma(tmem + (uint32_t)(pd + q0) * OZ_BN, ad,
-                 dBk + (uint64_t)(q0 * (OZ_B_TILE >> 4)), idesc, acc);
+        for (int r = 0; r < nblk; ++r) {
+          for (int pd = 0; pd < s; ++pd) {
+            const int q0 = 4 * r - pd;
+            if (q0 + 3 < 0 || q0 > s - 1) continue;   // no digit of this block for pd
+            // p = 0 reaches every block first: it starts the accumulation
+            const uint32_t acc = (first_k && pd == 0) ? 0u : 1u;
+            umma(tmem + (uint32_t)(4 * r) * OZ_BN, dAk + (uint64_t)(pd * (OZ_A_TILE >> 4)),
+                 dBk + (uint64_t)((OZ_BZERO + q0) * (OZ_B_TILE >> 4)), idesc, acc);
           }
         }
       }
@@ -577,7 +597,7 @@ OzPairs oz_pairs(int s, int N) {
 int oz_groups(int s, int N) { return oz_pairs(s, N).ngroups; }
 
 size_t oz_gemm_smem(int s) {
-  const size_t stages = (size_t)OZ_STAGES * s * (OZ_A_TILE + OZ_B_TILE);
+  const size_t stages = (size_t)OZ_STAGES * (s * OZ_A_TILE + OZ_BSLOTS * OZ_B_TILE);
   return (stages > (size_t)OZ_C_TILE ? stages : (size_t)OZ_C_TILE) + 1024 + 256;
 }
 
