@@ -439,14 +439,14 @@ ozaki_gemm_kernel(const __nv_bfloat16* __restrict__ As, long long sA, int P128,
 // integer operations only.
 // ---------------------------------------------------------------------------
 namespace {
-// BF16 bits of an integer d with |d| <= 128 (exact: at most 8 significant bits)
+// BF16 bits of an integer d with |d| <= 128.  The FP32 value with bits
+// 0x4B400000 + d is 1.5 * 2^23 + d exactly (|d| < 2^22), so subtracting
+// 1.5 * 2^23 leaves d as an exact FP32 number; with at most 8 significant
+// bits its low 16 mantissa bits are zero and the upper half is the BF16
+// encoding (0 for d = 0).  One integer add, one FP32 subtract, one shift.
 __device__ __forceinline__ uint32_t small_int_bf16(int d) {
-  if (d == 0) return 0u;
-  const uint32_t sgn = d < 0 ? 0x8000u : 0u;
-  const uint32_t a = (uint32_t)(d < 0 ? -d : d);
-  const int e = 31 - __clz((int)a);                     // 0..7
-  const uint32_t mant = (a << (7 - e)) & 0x7Fu;
-  return sgn | ((uint32_t)(e + 127) << 7) | mant;
+  const float f = __int_as_float(0x4B400000 + d) - 12582912.0f;
+  return __float_as_uint(f) >> 16;
 }
 }  // namespace
 
@@ -543,17 +543,34 @@ ozaki_split_kernel(const double* __restrict__ X, long long ldm, long long ldj, l
     const int jr = jc % R;
     const long long tile_off = ((long long)(jc / R) * nkb + kb) * (R * 32) + jr * 32 +
                                ((ch ^ ((jr >> 1) & 3)) << 3);
+    // digits 0..4 on the 64-bit value; after digit 4 (weight 2^{-35}) the
+    // remainder is below 2^27 in magnitude, so the rest runs in 32 bits
+    int Sr[8];
 #pragma unroll
     for (int q = 0; q < SL; ++q) {
       const int sh = 56 - 7 * q;                        // digit weight 2^{-7(q+1)}
       uint32_t w[4];
 #pragma unroll
       for (int k = 0; k < 8; k += 2) {
-        const long long d0 = (Sv[k] + (1ll << (sh - 1))) >> sh;       // nearest, in [-64, 64]
-        const long long d1 = (Sv[k + 1] + (1ll << (sh - 1))) >> sh;
-        Sv[k] -= d0 << sh;
-        Sv[k + 1] -= d1 << sh;
-        w[k >> 1] = small_int_bf16((int)d0) | (small_int_bf16((int)d1) << 16);
+        int d0, d1;
+        if (q <= 4) {
+          const long long e0 = (Sv[k] + (1ll << (sh - 1))) >> sh;     // nearest, in [-64, 64]
+          const long long e1 = (Sv[k + 1] + (1ll << (sh - 1))) >> sh;
+          Sv[k] -= e0 << sh;
+          Sv[k + 1] -= e1 << sh;
+          d0 = (int)e0;
+          d1 = (int)e1;
+          if (q == 4) {
+            Sr[k] = (int)Sv[k];
+            Sr[k + 1] = (int)Sv[k + 1];
+          }
+        } else {
+          d0 = (Sr[k] + (1 << (sh - 1))) >> sh;
+          d1 = (Sr[k + 1] + (1 << (sh - 1))) >> sh;
+          Sr[k] -= d0 << sh;
+          Sr[k + 1] -= d1 << sh;
+        }
+        w[k >> 1] = small_int_bf16(d0) | (small_int_bf16(d1) << 16);
       }
       *reinterpret_cast<uint4*>(Sb + q * plane + tile_off) = make_uint4(w[0], w[1], w[2], w[3]);
     }
