@@ -59,8 +59,9 @@ WORKLOADS = {
     "tdisplaced_n64": dict(L=8, U=4.0, dtau=0.1, beta=40.0, k=10, batch=256, config=2),
     # log det + gradient for all N*M field entries (continuous field)
     "grad_n144": dict(L=12, g=1.5, dtau=0.1, beta=20.0, k=10, batch=64, config=5),
-    # 1024 instances of uneven N and M in one call, k autotuned per N
-    "ragged_1024": dict(batch=1024, config=3),
+    # 1024 instances of uneven N and M in one call, k autotuned per N; recorded
+    # once as a CUDA graph and replayed
+    "ragged_1024": dict(batch=1024, config=3, graphs=True),
     # one small configuration: launch bound, so recorded once as a CUDA graph and replayed
     "n16_beta8": dict(L=4, U=4.0, dtau=0.1, beta=8.0, k=10, batch=1, config=1, graphs=True),
 }
@@ -784,11 +785,12 @@ def other_workloads(args, peak, pool=None) -> dict:
     """BASELINE's other configurations, each at few timed steps, for the one JSON line."""
     import torch
     out = {}
-    for name in ("n16_beta8", "tdisplaced_n64", "grad_n144", "ragged_1024"):
+    for entry in ("n16_beta8", "tdisplaced_n64", "grad_n144", "ragged_1024", "ragged_1024_bf16x8"):
+        name = entry.split("_bf16")[0]
         sub = argparse.Namespace(**vars(args))
         sub.workload = name
         sub.batch = None
-        sub.precision = "fp64"
+        sub.precision = "bf16x8" if entry.endswith("bf16x8") else "fp64"
         sub.steps = min(args.steps, 3)
         sub.warmup = 3
         sub.fold = "auto"
@@ -797,8 +799,8 @@ def other_workloads(args, peak, pool=None) -> dict:
         line = measure_other(sub, WORKLOADS[name], 0, 1, peak)
         line["driver_wall_s"] = time.perf_counter() - t0
         line["cpu_baseline"] = (cpu_baseline_line(name, args.workload_cpu_seconds, pool)
-                                if pool is not None else None)
-        out[name] = line
+                                if pool is not None and entry == name else None)
+        out[entry] = line
         torch.cuda.empty_cache()
     return out
 
@@ -811,7 +813,7 @@ def measure_other(args, wl, rank, world, peak=None):
     torch.cuda.set_device(dev)
     batch = args.batch or wl["batch"]
     name = args.workload
-    prec = 0 if args.precision == "fp64" or name == "ragged_1024" else int(args.precision[-1])
+    prec = 0 if args.precision == "fp64" else int(args.precision[-1])
     graphs = use_graphs(args, wl)
     if peak is None:
         peak = measure_fp64_peak(dev.index)
@@ -838,11 +840,11 @@ def measure_other(args, wl, rank, world, peak=None):
         Kby = {}   # one hopping matrix per lattice size, shared by its instances
         for x in insts:
             Kby.setdefault(x.N, torch.tensor(x.K, device=dev))
-        items = [(Kby[x.N], x.dtau, torch.tensor(x.V, device=dev), x.k) for x in insts]
+        rb = dq.RaggedBatch([(Kby[x.N], x.dtau, torch.tensor(x.V, device=dev), x.k) for x in insts])
         fl = sum(flops_per_greens(x.N, x.M, x.k) for x in insts)
 
         def step():
-            return dq.greens_ragged(items, handle=h)
+            return rb.run(handle=h)
     else:
         if name == "grad_n144":
             insts = [di.gaussian_instance(wl["L"], wl["g"], wl["dtau"], wl["beta"], wl["k"], sd)

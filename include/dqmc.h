@@ -77,9 +77,10 @@ enum dqmc_status_bits {
  * scales), the digit products accumulate exactly in FP32 on the tcgen05
  * tensor cores and are recombined in FP64; a product is accurate to about
  * N 2^{-7s-1} of (row max x column max), normwise rather than elementwise.
- * Supported for N <= 256 in dqmc_greens, dqmc_logdet, dqmc_greens_tdisplaced
- * and dqmc_logdet_grad (both stacks); dqmc_greens_ragged and N > 256 return
- * DQMC_ERR_UNSUPPORTED (dqmc_greens_noalloc takes no handle and is FP64). */
+ * Supported for N <= 256 in dqmc_greens, dqmc_logdet, dqmc_greens_tdisplaced,
+ * dqmc_logdet_grad (both stacks) and dqmc_greens_ragged (every instance N <= 256);
+ * N > 256 returns DQMC_ERR_UNSUPPORTED (dqmc_greens_noalloc takes no handle
+ * and is FP64). */
 typedef enum {
   DQMC_CHAIN_FP64 = 0,
   DQMC_CHAIN_BF16X3 = 3,
@@ -111,9 +112,11 @@ dqmc_status dqmc_set_chain_precision(dqmc_handle h, dqmc_chain_prec prec);
  * reads its inputs when it runs: write new fields into the same V buffer to
  * get new results.  A call with different arguments is captured again (the
  * executable graph is updated in place when its shape allows).  Results are
- * bitwise identical to graph mode off.  Host pointer mode, the profiler and
- * dqmc_greens_ragged always run without a graph.  The stream may be the legacy
- * default stream. */
+ * bitwise identical to graph mode off.  dqmc_greens_ragged is recorded the
+ * same way (keyed by its descriptor contents and pointers; the host-side
+ * grouping and the upload of its index tables happen before the recording,
+ * not in the graph).  Host pointer mode and the profiler always run without a
+ * graph.  The stream may be the legacy default stream. */
 dqmc_status dqmc_set_graph_mode(dqmc_handle h, int enable);
 /* Tile edge of the FP64 products: 0 = chosen by size (default: the edge that
  * pads N least), 32, 48 or 64.  A tuning knob for the autotuner
@@ -276,7 +279,12 @@ dqmc_status dqmc_logdet_grad(dqmc_handle h, int batch, int N, int M,
  * V_pool its M*N field at off_V, G_pool its N*N output at off_G).
  * Instances with equal (N, k, dtau, off_K) run as one batched chain (their M
  * may differ): instances with the same hopping matrix should point at one
- * copy of it.  logdet/sign/status are indexed by instance and may be NULL. */
+ * copy of it.  logdet/sign/status are indexed by instance and may be NULL.
+ * The chain precision of the handle applies (a mixed precision needs every
+ * N <= 256); in CUDA-graph mode an identical second call (same descriptor
+ * contents, pools and outputs) is a single graph launch.  The call
+ * synchronises the handle's stream when it sees a descriptor set different
+ * from the previous ragged call's (to upload the per-group index tables). */
 typedef struct {
   int N, M, k, pad;
   double dtau;

@@ -20,7 +20,7 @@ from . import _abi
 
 __all__ = ["Handle", "greens", "logdet", "greens_tdisplaced", "greens_tdisplaced_all",
            "greens_tdisplaced_from",
-           "logdet_grad", "greens_ragged",
+           "logdet_grad", "greens_ragged", "RaggedBatch",
            "greens_tdisplaced_ragged", "logdet_grad_ragged", "selftest_wait_timeout",
            "selftest_fp64_rate", "LogDet",
            "n_tau", "lib"]
@@ -284,44 +284,67 @@ def logdet_grad(K, dtau: float, V, k: int, *, handle: Handle | None = None):
     return ld, sg, dV, st
 
 
+class RaggedBatch:
+    """A ragged batch packed once into device pools (dqmc_greens_ragged).
+
+    ``instances``: list of (K, dtau, V, k) with CUDA float64 K (N,N), V (M,N).
+    Instances that pass the same K tensor share one copy of it in the K pool,
+    which lets the library batch them (groups are keyed by N, k, dtau, K).
+    ``run`` calls the library on the same pools and outputs every time, so in
+    CUDA-graph mode a second ``run`` is a single graph launch; ``set_fields``
+    writes new fields into the V pool in place."""
+
+    def __init__(self, instances, device=None):
+        device = device or instances[0][0].device
+        self.descs = (_abi.DqmcInstance * len(instances))()
+        offK = offV = offG = 0
+        Ks, Vs = [], []
+        seenK = {}
+        for i, (K, dtau, V, k) in enumerate(instances):
+            N = K.shape[0]
+            M = V.shape[0]
+            key = (K.data_ptr(), tuple(K.shape), tuple(K.stride()))
+            if key not in seenK:
+                seenK[key] = offK
+                Ks.append(K.reshape(-1))
+                offK += N * N
+            self.descs[i] = _abi.DqmcInstance(N, M, int(k), 0, float(dtau), seenK[key], offV, offG)
+            Vs.append(V.reshape(-1))
+            offV += M * N
+            offG += N * N
+        self.K = torch.cat(Ks).to(device=device, dtype=torch.float64).contiguous()
+        self.V = torch.cat(Vs).to(device=device, dtype=torch.float64).contiguous()
+        self.Gp = torch.empty(offG, dtype=torch.float64, device=device)
+        B = len(instances)
+        self.ld = torch.empty(B, dtype=torch.float64, device=device)
+        self.sg = torch.empty(B, dtype=torch.int32, device=device)
+        self.st = torch.empty(B, dtype=torch.int32, device=device)
+        self.Gs = [self.Gp[d.off_G: d.off_G + d.N * d.N].view(d.N, d.N) for d in self.descs]
+
+    def __len__(self):
+        return len(self.descs)
+
+    def set_fields(self, fields):
+        """Copy new fields (list of (M, N) tensors, same shapes) into the V pool."""
+        for d, V in zip(self.descs, fields):
+            self.V[d.off_V: d.off_V + d.M * d.N].copy_(V.reshape(-1))
+
+    def run(self, handle: Handle | None = None):
+        """(list of G views into the output pool, logdet, sign, status)."""
+        h = _handle(handle)
+        _abi.check(h._lib.dqmc_greens_ragged(h.h, len(self.descs), self.descs, _ptr(self.K),
+                                             _ptr(self.V), _ptr(self.Gp), _ptr(self.ld),
+                                             _ptr(self.sg), _ptr(self.st)), "dqmc_greens_ragged")
+        return self.Gs, self.ld, self.sg, self.st
+
+
 def greens_ragged(instances, *, handle: Handle | None = None, device=None):
     """Ragged batch.  ``instances``: list of (K, dtau, V, k) with CUDA float64 K (N,N), V (M,N).
 
     Packs the pools on the device and returns (list of G, logdet, sign, status).
-    Instances that pass the same K tensor are batched together (per N, k, dtau)."""
-    device = device or instances[0][0].device
-    descs = (_abi.DqmcInstance * len(instances))()
-    offK = offV = offG = 0
-    Ks, Vs = [], []
-    seenK = {}   # K storage -> pool offset: instances sharing a K tensor share its offset,
-    #              which lets the library batch them (groups are keyed by N, k, dtau, off_K)
-    for i, (K, dtau, V, k) in enumerate(instances):
-        N = K.shape[0]
-        M = V.shape[0]
-        key = (K.data_ptr(), tuple(K.shape), tuple(K.stride()))
-        if key not in seenK:
-            seenK[key] = offK
-            Ks.append(K.reshape(-1))
-            offK += N * N
-        descs[i] = _abi.DqmcInstance(N, M, int(k), 0, float(dtau), seenK[key], offV, offG)
-        Vs.append(V.reshape(-1))
-        offV += M * N
-        offG += N * N
-    Kp = torch.cat(Ks).to(device=device, dtype=torch.float64).contiguous()
-    Vp = torch.cat(Vs).to(device=device, dtype=torch.float64).contiguous()
-    Gp = torch.empty(offG, dtype=torch.float64, device=device)
-    B = len(instances)
-    ld = torch.empty(B, dtype=torch.float64, device=device)
-    sg = torch.empty(B, dtype=torch.int32, device=device)
-    st = torch.empty(B, dtype=torch.int32, device=device)
-    h = _handle(handle)
-    _abi.check(h._lib.dqmc_greens_ragged(h.h, B, descs, _ptr(Kp), _ptr(Vp), _ptr(Gp), _ptr(ld),
-                                         _ptr(sg), _ptr(st)), "dqmc_greens_ragged")
-    Gs = []
-    for i in range(B):
-        N = descs[i].N
-        Gs.append(Gp[descs[i].off_G: descs[i].off_G + N * N].view(N, N))
-    return Gs, ld, sg, st
+    Instances that pass the same K tensor are batched together (per N, k, dtau).
+    For repeated calls on the same instances (CUDA-graph replay) use RaggedBatch."""
+    return RaggedBatch(instances, device).run(handle)
 
 
 def _pack_ragged(instances, device, out_len):

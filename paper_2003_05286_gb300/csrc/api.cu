@@ -68,6 +68,14 @@ struct dqmc_handle_s {
   // uniform path they call may grow)
   char* rws = nullptr;
   size_t rws_bytes = 0;
+  // per-group index tables of dqmc_greens_ragged (chain lengths, instance
+  // indices, pool offsets): uploaded before the launches (and before a graph
+  // capture) and kept apart from ws; rtab_key is the hash of the descriptor
+  // set whose tables the buffer holds, so a replayed graph finds them intact
+  char* rtab = nullptr;
+  size_t rtab_bytes = 0;
+  unsigned long long rtab_key = 0;
+  cudaEvent_t rfork = nullptr;
 };
 
 namespace {
@@ -321,8 +329,11 @@ dqmc_status chunk_products(dqmc_handle h, int dir, int batch, int N, int M, int 
   int nb = 0;
   for (int i = 0; i <= hi - lo; ++i) {
     const int l = dir > 0 ? lo + i : hi - i;
-    if (w.oz_s > 0 && lim == nullptr) {
+    if (w.oz_s > 0) {
       // a12 on the tensor cores.  Forward: B' = diag(e^{V_l}) A, C = E B'.
+      // Ragged chains (lim): slices past an instance's own M_b copy the FP64
+      // input through, as the FP64 product does, so that a last partial
+      // chunk ends with B_{M_b} ... B_{ck+1} U.
       // Backward (B_l^T = diag(e^{V_l}) E^T): C = E^T B' with B' = A scaled by
       // the previous slice's e^{V}; the last slice's scale is applied below.
       const int PK = w.oz_PK, sl = w.oz_s;
@@ -333,7 +344,7 @@ dqmc_status chunk_products(dqmc_handle h, int dir, int batch, int N, int M, int 
                      w.ozeB, PK, batch, st));
       CKP(PC_CHAIN, 2.0 * N * N * (double)N * batch,
           ozaki_gemm(w.ozA, w.ozeA, 0, 0, w.oz_P128, w.ozB, w.ozeB, PK, PK, PK, sl, N, batch,
-                     bufs[nb], NN, status, st));
+                     bufs[nb], NN, status, st, lim, l, prev, sprev));
       prev = bufs[nb];
       sprev = NN;
       nb ^= 1;
@@ -408,9 +419,10 @@ dqmc_status chunk_xupdate(dqmc_handle h, int dir, int batch, int N, int k, int c
   const long long NN = (long long)N * N;
   const int src = dir > 0 ? c : c + 1;
   const int dst = dir > 0 ? c + 1 : c;
-  if (w.oz_s > 0 && lim == nullptr) {
+  if (w.oz_s > 0) {
     // tensor cores: slices of T' (A operand, per instance; row i of T' is a
-    // "column" of the splitter) and of the rows of X_src gathered by perm
+    // "column" of the splitter) and of the rows of X_src gathered by perm.
+    // Ragged chains (lim): ended instances copy X_src through unchanged.
     const int P1 = w.oz_P128, PK = w.oz_PK, sl = w.oz_s;
     CK(ozaki_split(w.T, 1, N, NN, nullptr, 0, N, P1, PK, 128, sl, w.ozT, (long long)sl * P1 * PK,
                    w.ozeT, P1, batch, st));
@@ -418,7 +430,8 @@ dqmc_status chunk_xupdate(dqmc_handle h, int dir, int batch, int N, int k, int c
                    (long long)sl * PK * PK, w.ozeB, PK, batch, st, w.perm, N));
     CKP(PC_XUPD, (double)N * N * (double)N * batch,
         ozaki_gemm(w.ozT, w.ozeT, (long long)sl * P1 * PK, P1, P1, w.ozB, w.ozeB, PK, PK, PK, sl,
-                   N, batch, slotX(s, dst), s.instX, status, st));
+                   N, batch, slotX(s, dst), s.instX, status, st, lim, c * k + 1,
+                   slotX(s, src), s.instX));
     return DQMC_OK;
   }
   const bool jac = h->decomp == DQMC_DECOMP_JACOBI;   // X' = V'^T X: dense, no pivots
@@ -947,6 +960,8 @@ dqmc_status dqmc_destroy(dqmc_handle h) {
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->gstream) cudaStreamDestroy(h->gstream);
   if (h->rws) cudaFree(h->rws);
+  if (h->rtab) cudaFree(h->rtab);
+  if (h->rfork) cudaEventDestroy(h->rfork);
   delete h;
   return DQMC_OK;
 }
@@ -2012,10 +2027,53 @@ static dqmc_status grad_impl(dqmc_handle h, int batch, int N, int M, const doubl
   return DQMC_OK;
 }
 
+}  // extern "C"
+
 // Ragged batch: instances are grouped by (N, k, dtau, K); each group runs the
 // uniform equal-time path with per-instance chain lengths M_b on its own
 // stream, so that small-N groups (latency-bound QR) overlap with large-N
 // groups (FP64-bound products).  Results are scattered to the pools.
+//
+// The host work (grouping, workspace sizing, the per-group index tables in
+// the handle's rtab buffer) happens before any launch, so the launches alone
+// can be recorded as one CUDA graph in graph mode; the graph is keyed by a
+// hash of the descriptors together with every pointer, and replayed for an
+// identical call.
+namespace {
+
+// FNV-1a over the bytes of the descriptor array
+unsigned long long hash_desc(const dqmc_instance* d, int batch) {
+  unsigned long long x = 1469598103934665603ull;
+  const unsigned char* p = reinterpret_cast<const unsigned char*>(d);
+  const size_t n = (size_t)batch * sizeof(dqmc_instance);
+  for (size_t i = 0; i < n; ++i) {
+    x ^= p[i];
+    x *= 1099511628211ull;
+  }
+  return x ^ (unsigned long long)batch;
+}
+
+struct RaggedGroup {
+  int N, k;
+  double dtau;
+  long long offK;
+  std::vector<int> idx;
+  int Mmax = 0;
+};
+
+struct RaggedGroupWs {
+  ExpmWs ew; ChainWs cw; LohWs lw; PlainWs pw;
+  double *expV, *U, *D, *X0, *X1, *G, *ld;
+  int *sg, *st;
+  // index tables (in rtab)
+  int *Mb, *gidx;
+  long long *offV, *offG;
+};
+
+}  // namespace
+
+extern "C" {
+
 dqmc_status dqmc_greens_ragged(dqmc_handle h, int batch, const dqmc_instance* desc,
                                const double* K_pool, const double* V_pool, double* G_pool,
                                double* logdet, int* sign, int* status) {
@@ -2025,46 +2083,37 @@ dqmc_status dqmc_greens_ragged(dqmc_handle h, int batch, const dqmc_instance* de
   if (batch == 0) return DQMC_OK;
   if (!desc || !K_pool || !V_pool) return DQMC_ERR_ARG;
   if (h->pmode == DQMC_PTR_HOST) return DQMC_ERR_UNSUPPORTED;
-  if (h->prec != DQMC_CHAIN_FP64) return DQMC_ERR_UNSUPPORTED;   // mixed chain: uniform batches only
+  const bool mixed = h->prec != DQMC_CHAIN_FP64;
+  if (mixed && h->decomp == DQMC_DECOMP_JACOBI) return DQMC_ERR_UNSUPPORTED;
   for (int b = 0; b < batch; ++b) {
     const dqmc_instance& d = desc[b];
     if (d.N < 1 || d.N > 1024 || d.M < 1 || d.k < 1 || d.k > d.M || !(d.dtau >= 0.0) ||
         d.off_K < 0 || d.off_V < 0 || d.off_G < 0)
       return DQMC_ERR_ARG;
+    if (mixed && d.N > 256) return DQMC_ERR_UNSUPPORTED;   // tensor-core chain: N <= 256
+    if (h->decomp == DQMC_DECOMP_JACOBI && d.N > 512) return DQMC_ERR_UNSUPPORTED;
   }
   // ---- groups ---------------------------------------------------------------
-  struct Group {
-    int N, k;
-    double dtau;
-    long long offK;
-    std::vector<int> idx;
-    int Mmax = 0;
-  };
-  std::vector<Group> groups;
+  std::vector<RaggedGroup> groups;
   for (int b = 0; b < batch; ++b) {
     const dqmc_instance& d = desc[b];
-    Group* g = nullptr;
+    RaggedGroup* g = nullptr;
     for (auto& x : groups)
       if (x.N == d.N && x.k == d.k && x.dtau == d.dtau && x.offK == d.off_K) { g = &x; break; }
     if (!g) {
-      groups.push_back(Group{d.N, d.k, d.dtau, d.off_K, {}, 0});
+      groups.push_back(RaggedGroup{d.N, d.k, d.dtau, d.off_K, {}, 0});
       g = &groups.back();
     }
     g->idx.push_back(b);
     if (d.M > g->Mmax) g->Mmax = d.M;
   }
-  // ---- workspace: one region per group ----------------------------------------
-  struct GroupWs {
-    ExpmWs ew; ChainWs cw; LohWs lw; PlainWs pw;
-    double *expV, *U, *D, *X0, *X1, *G, *ld;
-    int *sg, *st, *Mb, *gidx;
-    long long *offV, *offG;
-  };
-  std::vector<GroupWs> gw(groups.size());
+  const int s_digits = mixed ? (int)h->prec : 0;
+  // ---- workspace (h->ws) and index tables (h->rtab): one region per group ----
+  std::vector<RaggedGroupWs> gw(groups.size());
   auto layout = [&](Arena& ar) {
     for (size_t i = 0; i < groups.size(); ++i) {
-      const Group& g = groups[i];
-      GroupWs& w = gw[i];
+      const RaggedGroup& g = groups[i];
+      RaggedGroupWs& w = gw[i];
       const int nb = (int)g.idx.size(), N = g.N;
       const long long NN = (long long)N * N;
       const long long Mp = (long long)(n_chunks(g.Mmax, g.k) + 1) * g.k;
@@ -2075,86 +2124,134 @@ dqmc_status dqmc_greens_ragged(dqmc_handle h, int batch, const dqmc_instance* de
       w.X0 = ar.take<double>(NN * nb);
       w.X1 = ar.take<double>(NN * nb);
       take_chain(ar, nb, N, w.cw);
+      if (mixed) take_ozaki(ar, nb, N, s_digits, w.cw);
       take_loh(ar, nb, N, w.lw);
       if (h->inv == DQMC_INV_PLAIN) take_plain(ar, nb, N, w.pw);
       w.G = ar.take<double>(NN * nb);
       w.ld = ar.take<double>(nb);
       w.sg = ar.take<int>(nb);
       w.st = ar.take<int>(nb);
-      w.Mb = ar.take<int>(nb);
-      w.gidx = ar.take<int>(nb);
-      w.offV = ar.take<long long>(nb);
-      w.offG = ar.take<long long>(nb);
     }
   };
-  Arena measure;
+  auto layout_tables = [&](Arena& ar) {
+    for (size_t i = 0; i < groups.size(); ++i) {
+      const int nb = (int)groups[i].idx.size();
+      gw[i].Mb = ar.take<int>(nb);
+      gw[i].gidx = ar.take<int>(nb);
+      gw[i].offV = ar.take<long long>(nb);
+      gw[i].offG = ar.take<long long>(nb);
+    }
+  };
+  Arena measure, measure_t;
   layout(measure);
+  layout_tables(measure_t);
   CKS(ensure_ws(h, measure.off));
   Arena ar;
   ar.base = h->ws;
   layout(ar);
-  // ---- streams ---------------------------------------------------------------
+  if (measure_t.off > h->rtab_bytes) {
+    if (h->capturing) return DQMC_ERR_UNSUPPORTED;
+    if (h->rtab) {
+      cudaStreamSynchronize(h->stream);
+      cudaFree(h->rtab);
+      h->rtab = nullptr;
+      h->rtab_bytes = 0;
+    }
+    h->rtab_key = 0;
+    if (cudaMalloc(&h->rtab, measure_t.off) != cudaSuccess) {
+      cudaGetLastError();
+      h->rtab = nullptr;
+      return DQMC_ERR_NOMEM;
+    }
+    h->rtab_bytes = measure_t.off;
+  }
+  Arena art;
+  art.base = h->rtab;
+  layout_tables(art);
+  const unsigned long long dkey = hash_desc(desc, batch);
+  if (h->rtab_key != dkey) {
+    // the tables of this descriptor set; the copies finish before the host
+    // vectors go out of scope, and before any launch that reads them
+    h->rtab_key = 0;
+    cudaStreamSynchronize(h->stream);
+    for (size_t i = 0; i < groups.size(); ++i) {
+      const RaggedGroup& g = groups[i];
+      const int nb = (int)g.idx.size();
+      std::vector<int> Mb(nb), gidx(nb);
+      std::vector<long long> offV(nb), offG(nb);
+      for (int j = 0; j < nb; ++j) {
+        const dqmc_instance& d = desc[g.idx[j]];
+        Mb[j] = d.M; gidx[j] = g.idx[j]; offV[j] = d.off_V; offG[j] = d.off_G;
+      }
+      const bool ok =
+          cudaMemcpy(gw[i].Mb, Mb.data(), nb * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess &&
+          cudaMemcpy(gw[i].gidx, gidx.data(), nb * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess &&
+          cudaMemcpy(gw[i].offV, offV.data(), nb * sizeof(long long), cudaMemcpyHostToDevice) == cudaSuccess &&
+          cudaMemcpy(gw[i].offG, offG.data(), nb * sizeof(long long), cudaMemcpyHostToDevice) == cudaSuccess;
+      if (!ok) return DQMC_ERR_CUDA;
+    }
+    h->rtab_key = dkey;
+  }
+  // ---- streams and the fork event (created outside any capture) --------------
   const size_t nstreams = groups.size() < 8 ? groups.size() : 8;
   CKS(ensure_aux(h, nstreams));
-  cudaEvent_t fork = nullptr;
-  if (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess) return DQMC_ERR_CUDA;
-  // per-group index tables (uploaded on the main stream, before the fork)
-  for (size_t i = 0; i < groups.size(); ++i) {
-    const Group& g = groups[i];
-    const int nb = (int)g.idx.size();
-    std::vector<int> Mb(nb), gidx(nb);
-    std::vector<long long> offV(nb), offG(nb);
-    for (int j = 0; j < nb; ++j) {
-      const dqmc_instance& d = desc[g.idx[j]];
-      Mb[j] = d.M; gidx[j] = g.idx[j]; offV[j] = d.off_V; offG[j] = d.off_G;
+  if (!h->rfork && cudaEventCreateWithFlags(&h->rfork, cudaEventDisableTiming) != cudaSuccess) {
+    h->rfork = nullptr;
+    return DQMC_ERR_CUDA;
+  }
+  GraphKey key;
+  key.add(9);
+  key.add((unsigned long long)batch);
+  key.add(dkey);
+  key.addp(K_pool); key.addp(V_pool); key.addp(G_pool);
+  key.addp(logdet); key.addp(sign); key.addp(status);
+  key.addp(h->rtab);
+  return graph_call(h, key, [&]() -> dqmc_status {
+    h->launches = 0;
+    h->cur = h->stream;
+    // the handle's stream may be a capture stream here: every launch below
+    // forks from it through rfork and joins back through auxev
+    if (cudaEventRecord(h->rfork, h->stream) != cudaSuccess) return DQMC_ERR_CUDA;
+    for (size_t q = 0; q < nstreams; ++q) cudaStreamWaitEvent(h->aux[q], h->rfork, 0);
+    dqmc_status rc = DQMC_OK;
+    for (size_t i = 0; i < groups.size() && rc == DQMC_OK; ++i) {
+      const RaggedGroup& g = groups[i];
+      RaggedGroupWs& w = gw[i];
+      const int nb = (int)g.idx.size(), N = g.N, k = g.k;
+      const long long NN = (long long)N * N;
+      const int ncmax = n_chunks(g.Mmax, k);
+      const long long Mp = (long long)(ncmax + 1) * k;
+      h->cur = h->aux[i % nstreams];
+      cudaStream_t st = h->cur;
+      rc = [&]() -> dqmc_status {
+        if (cudaMemsetAsync(w.st, 0, nb * sizeof(int), st) != cudaSuccess) return DQMC_ERR_CUDA;
+        CKS(run_expm(h, K_pool + g.offK, N, g.dtau, -1.0, w.ew, w.st, nb));
+        CK(exp_gather(V_pool, w.offV, w.Mb, nb, (int)Mp, N, w.expV, w.st, st));
+        if (mixed) CK(split_E(w.ew.t0, N, 0, w.cw, st));   // E slices, shared by the group
+        CK(set_identity(w.U, NN, N, nb, st));
+        CK(set_const(w.D, (long long)N * nb, 1.0, st));
+        CK(set_identity(w.X0, NN, N, nb, st));
+        Slots sl;
+        sl.U = w.U; sl.slotU = 0; sl.instU = NN;
+        sl.D = w.D; sl.slotD = 0; sl.instD = N;
+        sl.X = w.X0; sl.slotX = 0; sl.instX = NN;
+        sl.X2 = w.X1;
+        CKS(run_chain(h, +1, nb, N, g.Mmax, k, w.ew.t0, w.expV, Mp * N, sl, w.cw, w.st, w.Mb));
+        const double* Xf = (ncmax & 1) ? w.X1 : w.X0;
+        CKS(run_inversion(h, nb, N, w.U, NN, w.D, N, Xf, NN, G_pool ? w.G : nullptr, w.ld, w.sg,
+                          w.st, w.lw, w.pw));
+        if (G_pool) CK(scatter_mats(w.G, w.offG, N, nb, G_pool, st));
+        CK(scatter_scalars(w.gidx, nb, w.ld, w.sg, w.st, logdet, sign, status, st));
+        return DQMC_OK;
+      }();
     }
-    bool ok = cudaMemcpyAsync(gw[i].Mb, Mb.data(), nb * sizeof(int), cudaMemcpyHostToDevice, h->stream) == cudaSuccess &&
-              cudaMemcpyAsync(gw[i].gidx, gidx.data(), nb * sizeof(int), cudaMemcpyHostToDevice, h->stream) == cudaSuccess &&
-              cudaMemcpyAsync(gw[i].offV, offV.data(), nb * sizeof(long long), cudaMemcpyHostToDevice, h->stream) == cudaSuccess &&
-              cudaMemcpyAsync(gw[i].offG, offG.data(), nb * sizeof(long long), cudaMemcpyHostToDevice, h->stream) == cudaSuccess &&
-              cudaMemsetAsync(gw[i].st, 0, nb * sizeof(int), h->stream) == cudaSuccess;
-    if (!ok) { cudaEventDestroy(fork); return DQMC_ERR_CUDA; }
-  }
-  cudaStreamSynchronize(h->stream);   // host staging vectors go out of scope per group
-  cudaEventRecord(fork, h->stream);
-  for (size_t s = 0; s < nstreams; ++s) cudaStreamWaitEvent(h->aux[s], fork, 0);
-  dqmc_status rc = DQMC_OK;
-  for (size_t i = 0; i < groups.size() && rc == DQMC_OK; ++i) {
-    const Group& g = groups[i];
-    GroupWs& w = gw[i];
-    const int nb = (int)g.idx.size(), N = g.N, k = g.k;
-    const long long NN = (long long)N * N;
-    const int ncmax = n_chunks(g.Mmax, k);
-    const long long Mp = (long long)(ncmax + 1) * k;
-    h->cur = h->aux[i % nstreams];
-    cudaStream_t st = h->cur;
-    rc = [&]() -> dqmc_status {
-      CKS(run_expm(h, K_pool + g.offK, N, g.dtau, -1.0, w.ew, w.st, nb));
-      CK(exp_gather(V_pool, w.offV, w.Mb, nb, (int)Mp, N, w.expV, w.st, st));
-      CK(set_identity(w.U, NN, N, nb, st));
-      CK(set_const(w.D, (long long)N * nb, 1.0, st));
-      CK(set_identity(w.X0, NN, N, nb, st));
-      Slots sl;
-      sl.U = w.U; sl.slotU = 0; sl.instU = NN;
-      sl.D = w.D; sl.slotD = 0; sl.instD = N;
-      sl.X = w.X0; sl.slotX = 0; sl.instX = NN;
-      sl.X2 = w.X1;
-      CKS(run_chain(h, +1, nb, N, g.Mmax, k, w.ew.t0, w.expV, Mp * N, sl, w.cw, w.st, w.Mb));
-      const double* Xf = (ncmax & 1) ? w.X1 : w.X0;
-      CKS(run_inversion(h, nb, N, w.U, NN, w.D, N, Xf, NN, G_pool ? w.G : nullptr, w.ld, w.sg,
-                        w.st, w.lw, w.pw));
-      if (G_pool) CK(scatter_mats(w.G, w.offG, N, nb, G_pool, st));
-      CK(scatter_scalars(w.gidx, nb, w.ld, w.sg, w.st, logdet, sign, status, st));
-      return DQMC_OK;
-    }();
-  }
-  for (size_t s = 0; s < nstreams; ++s) {
-    cudaEventRecord(h->auxev[s], h->aux[s]);
-    cudaStreamWaitEvent(h->stream, h->auxev[s], 0);
-  }
-  cudaEventDestroy(fork);
-  h->cur = h->stream;
-  return rc;
+    for (size_t q = 0; q < nstreams; ++q) {
+      cudaEventRecord(h->auxev[q], h->aux[q]);
+      cudaStreamWaitEvent(h->stream, h->auxev[q], 0);
+    }
+    h->cur = h->stream;
+    return rc;
+  });
 }
 
 }  // extern "C"

@@ -223,10 +223,14 @@ cudaError_t ozaki_split(const double* X, long long ldm, long long ldj, long long
                         const double* sc, long long ssc, int N, int PJ, int PM, int R, int s,
                         __nv_bfloat16* S, long long sS, int* e, long long se, int batch,
                         cudaStream_t st, const int* gm = nullptr, long long sgm = 0);
+// lim (nullable, device, per instance) + lim_at: instances with lim[b] < lim_at
+// are skipped; when csrc is set their output is the FP64 copy of
+// csrc + b * scsrc (the copy-through of ragged chains that have ended).
 cudaError_t ozaki_gemm(const __nv_bfloat16* As, const int* eA, long long sA, long long seA,
                        int P128, const __nv_bfloat16* Bs, const int* eB, long long seB, int PN,
                        int PK, int s, int N, int batch, double* C, long long sC, int* status,
-                       cudaStream_t st);
+                       cudaStream_t st, const int* lim = nullptr, int lim_at = 0,
+                       const double* csrc = nullptr, long long scsrc = 0);
 int oz_groups(int s, int N);
 // One CTA of ozaki_gemm_kernel whose loads are never issued: its bounded
 // waits run out and it ORs DQMC_STATUS_TIMEOUT into *status (device int).

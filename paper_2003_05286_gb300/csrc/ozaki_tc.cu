@@ -221,7 +221,8 @@ ozaki_gemm_kernel(const __nv_bfloat16* __restrict__ As, long long sA, int P128,
                   const __nv_bfloat16* __restrict__ Bs, int PN, const OzPairs pr, int N, int nkb,
                   const int* __restrict__ eA, long long seA, int a_batched,
                   const int* __restrict__ eB, long long seB, double* __restrict__ C,
-                  long long sC, int* status) {
+                  long long sC, int* status, const int* __restrict__ lim, int lim_at,
+                  const double* __restrict__ csrc, long long scsrc) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte aligned stage buffers
   unsigned char* base = reinterpret_cast<unsigned char*>(
@@ -241,6 +242,20 @@ ozaki_gemm_kernel(const __nv_bfloat16* __restrict__ As, long long sA, int P128,
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int n0 = blockIdx.x * OZ_BN, m0 = blockIdx.y * OZ_BM, b = blockIdx.z;
+  // an instance whose (shorter) chain has already ended: copy its FP64 source
+  // tile through when one is given, else leave the output alone.  The test
+  // is uniform over the CTA and comes before any barrier or TMEM allocation.
+  if (lim && lim[b] < lim_at) {
+    if (csrc) {
+      const double* src = csrc + (long long)b * scsrc;
+      double* dst = C + (long long)b * sC;
+      for (int e = tid; e < OZ_BM * OZ_BN; e += OZ_THREADS) {
+        const int r = m0 + e / OZ_BN, c = n0 + e % OZ_BN;
+        if (r < N && c < N) dst[(long long)r * N + c] = src[(long long)r * N + c];
+      }
+    }
+    return;
+  }
   const int bA = a_batched ? b : 0;   // instance of the A operand (shared when not batched)
   // accumulators: weight group g in columns [g OZ_BN, (g + 1) OZ_BN); the MMAs
   // write groups in aligned blocks of four, so more than four groups take all 512
@@ -655,7 +670,8 @@ static cudaError_t ozaki_gemm_impl(const __nv_bfloat16* As, const int* eA, long 
                                    long long seA, int P128, const __nv_bfloat16* Bs, const int* eB,
                                    long long seB, int PN, int PK, int s, int N, int batch,
                                    double* C, long long sC, int* status, cudaStream_t st,
-                                   int stall) {
+                                   int stall, const int* lim = nullptr, int lim_at = 0,
+                                   const double* csrc = nullptr, long long scsrc = 0) {
   if (sA != 0 && sA < (long long)s * P128 * PK) return cudaErrorInvalidValue;
   if (P128 % OZ_BM || PN % OZ_BN || PK % OZ_BK || PK < OZ_BK) return cudaErrorInvalidValue;
   if (s < 1 || s > 8) return cudaErrorInvalidValue;
@@ -671,16 +687,18 @@ static cudaError_t ozaki_gemm_impl(const __nv_bfloat16* As, const int* eA, long 
   cudaFuncSetAttribute(ozaki_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   dim3 grid((N + OZ_BN - 1) / OZ_BN, (N + OZ_BM - 1) / OZ_BM, batch);
   ozaki_gemm_kernel<<<grid, OZ_THREADS, sm, st>>>(As, sA, P128, Bs, PN, pr, N, PK / OZ_BK, eA, seA,
-                                                  sA != 0, eB, seB, C, sC, status);
+                                                  sA != 0, eB, seB, C, sC, status, lim, lim_at,
+                                                  csrc, scsrc);
   return cudaGetLastError();
 }
 
 cudaError_t ozaki_gemm(const __nv_bfloat16* As, const int* eA, long long sA, long long seA,
                        int P128, const __nv_bfloat16* Bs, const int* eB, long long seB, int PN,
                        int PK, int s, int N, int batch, double* C, long long sC, int* status,
-                       cudaStream_t st) {
+                       cudaStream_t st, const int* lim, int lim_at, const double* csrc,
+                       long long scsrc) {
   return ozaki_gemm_impl(As, eA, sA, seA, P128, Bs, eB, seB, PN, PK, s, N, batch, C, sC, status,
-                         st, 0);
+                         st, 0, lim, lim_at, csrc, scsrc);
 }
 
 // Operands of the bounded-wait self-test: one 128 x 64 tile, one slice.

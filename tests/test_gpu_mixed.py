@@ -100,7 +100,7 @@ def test_mixed_grad(dq):
 
 
 def test_mixed_rejected_where_not_built(dq):
-    """N above 256 and ragged batches have no tensor-core chain."""
+    """N above 256 has no tensor-core chain, also inside a ragged batch."""
     h = dq.Handle(chain_precision=5)
     big = torch.zeros((1, 20, 324), dtype=torch.float64, device="cuda")
     with pytest.raises(RuntimeError):
@@ -109,4 +109,5 @@ def test_mixed_rejected_where_not_built(dq):
         dq.greens_tdisplaced(_dev(di.square_hopping(18)), 0.1, big, 10, handle=h)
     inst = di.hubbard_instance(4, 4.0, 0.1, 2.0, 10, 1)
     with pytest.raises(RuntimeError):
-        dq.greens_ragged([(_dev(inst.K), 0.1, _dev(inst.V), 10)], handle=h)
+        dq.greens_ragged([(_dev(inst.K), 0.1, _dev(inst.V), 10),
+                          (_dev(di.square_hopping(18)), 0.1, big[0], 10)], handle=h)

@@ -143,3 +143,75 @@ def test_ragged_grad(dq):
         if i < 4:
             dVo = od.logdet_grad(x.K, x.dtau, x.V, x.k)
             assert np.abs(dVs[i].cpu().numpy() - dVo).max() <= 1e-9
+
+
+def _uneven_M_items(seed, n=12):
+    """Instances of N = 9, 16 and 36 sharing one K per size, with M = 10 .. 33
+    (last chunks of several lengths inside one batched chain of k = 10)."""
+    rng = np.random.default_rng(seed)
+    insts = []
+    for i in range(n):
+        L = (3, 4, 6)[i % 3]
+        beta = round(float(rng.uniform(1.0, 3.3)), 1)
+        insts.append(di.hubbard_instance(L, float(rng.uniform(2, 6)), 0.1, beta, 10, seed * 100 + i))
+    Ks = {L: _dev(di.square_hopping(L)) for L in (3, 4, 6)}
+    items = [(Ks[int(round(x.N ** 0.5))], x.dtau, _dev(x.V), x.k) for x in insts]
+    return insts, items
+
+
+def test_ragged_mixed_precision(dq):
+    """The tensor-core chain (8 BF16 digit slices) in a ragged batch: instances of
+    one group end at different chunks, so ended instances copy their product and X
+    through.  Against the oracle to 1e-8 of max(1, max|G|) and 1e-9 relative in log det."""
+    insts, items = _uneven_M_items(31)
+    h = dq.Handle(chain_precision=8)
+    Gs, ld, sg, st = dq.greens_ragged(items, handle=h)
+    assert int((st != 0).sum()) == 0
+    for i, x in enumerate(insts):
+        Go, ldo, so = od.greens(x.K, x.dtau, x.V, x.k)
+        err = np.abs(Gs[i].cpu().numpy() - Go).max() / max(1.0, np.abs(Go).max())
+        assert err <= 1e-8, (i, x.N, x.M, err)
+        assert abs(float(ld[i]) - ldo) <= 1e-9 * max(1.0, abs(ldo))
+        assert int(sg[i]) == so
+    h.close()
+
+
+@pytest.mark.parametrize("prec", [0, 8])
+def test_ragged_graph_replay(dq, prec):
+    """In CUDA-graph mode a repeated ragged call replays its graph: bitwise the
+    eager result, and new fields written into the same V pool give the eager
+    result for those fields."""
+    insts, items = _uneven_M_items(47)
+    batch = dq.RaggedBatch(items)
+    eager = dq.Handle(chain_precision=prec)
+    G0 = [g.clone() for g in batch.run(handle=eager)[0]]
+    ld0 = batch.ld.clone()
+    hg = dq.Handle(chain_precision=prec, graphs=True)
+    for _ in range(3):                      # capture, then replays
+        Gs, ld, sg, st = batch.run(handle=hg)
+        torch.cuda.synchronize()
+        assert int((st != 0).sum()) == 0
+        assert all(torch.equal(a, b) for a, b in zip(Gs, G0))
+        assert torch.equal(ld, ld0)
+    n_graph = hg.last_launch_count
+    # new fields in place: the replayed graph reads them
+    batch.set_fields([0.5 * _dev(x.V) for x in insts])
+    G1 = [g.clone() for g in batch.run(handle=eager)[0]]
+    ld1 = batch.ld.clone()
+    Gs, ld, _, st = batch.run(handle=hg)
+    torch.cuda.synchronize()
+    assert hg.last_launch_count == n_graph
+    assert all(torch.equal(a, b) for a, b in zip(Gs, G1))
+    assert torch.equal(ld, ld1)
+    assert not all(torch.equal(a, b) for a, b in zip(G1, G0))
+    # a different descriptor set on the same handle is recorded anew
+    insts2, items2 = _uneven_M_items(48, n=7)
+    b2 = dq.RaggedBatch(items2)
+    Gs2, ld2, _, st2 = b2.run(handle=hg)
+    torch.cuda.synchronize()
+    for i, x in enumerate(insts2):
+        Go, ldo, so = od.greens(x.K, x.dtau, x.V, x.k)
+        tol = 1e-10 if prec == 0 else 1e-8
+        assert np.abs(Gs2[i].cpu().numpy() - Go).max() <= tol * max(1.0, np.abs(Go).max())
+    eager.close()
+    hg.close()
