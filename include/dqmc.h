@@ -296,6 +296,42 @@ dqmc_status dqmc_greens_ragged(dqmc_handle h, int batch, const dqmc_instance* de
                                double* G_pool, double* logdet, int* sign,
                                int* status);
 
+/* Registered hopping matrices and device-resident descriptors (the batched
+ * form of the problem statement, Sec. 2: G = [1 + B_M ... B_1]^{-1} with
+ * B_l = exp(-dtau K) exp(V_l) for many instances that share a few K).
+ *
+ * dqmc_register_K copies the N x N hopping matrix K (a device pointer, or a
+ * host pointer in host pointer mode) into the handle, computes
+ * E = exp(-dtau K) once (Taylor series with scaling and squaring, Sec. 2), and
+ * returns its id in *K_id (0, 1, ... in registration order).  Synchronous.
+ * Errors: DQMC_ERR_ARG for bad sizes/pointers, or a K that is not symmetric,
+ * not finite or has ||dtau K||_1 > 2048 (then nothing is registered);
+ * DQMC_ERR_NOMEM; DQMC_ERR_UNSUPPORTED inside a stream capture.  Registered
+ * matrices live until dqmc_destroy. */
+dqmc_status dqmc_register_K(dqmc_handle h, int N, const double* K, double dtau, int* K_id);
+
+/* One instance of dqmc_greens_batched: its size N (that of the registered
+ * K_id), M slices, stabilisation interval k, and offsets in doubles of its
+ * M x N field in V_pool and of its N x N output in G_pool. */
+typedef struct {
+  int N, M, k, K_id;
+  long long off_V, off_G;
+} dqmc_desc;
+
+/* Equal-time G, log det and sign of `batch` instances described by a DEVICE
+ * array of dqmc_desc (device pointer mode only).  dtau and exp(-dtau K) come
+ * from the registration of each K_id.  The call reads the descriptors back to
+ * the host once (after the work already queued on the handle's stream; this
+ * synchronises the stream), groups instances of equal (N, k, K_id), and runs
+ * them as dqmc_greens_ragged does (same kernels, same results for the same
+ * exponentials; CUDA-graph replay in graph mode; the handle's chain
+ * precision).  logdet, sign, status [batch] may be NULL.  Errors: DQMC_ERR_ARG
+ * (unknown K_id, N that does not match it, bad sizes), DQMC_ERR_UNSUPPORTED
+ * (host pointer mode, inside a capture, mixed precision with N > 256). */
+dqmc_status dqmc_greens_batched(dqmc_handle h, int batch, const dqmc_desc* desc,
+                                const double* V_pool, double* G_pool, double* logdet, int* sign,
+                                int* status);
+
 /* Ragged time-displaced G: instances of different N, M, k, dtau and K in one
  * call, pools and descriptors as for dqmc_greens_ragged.  Instance b writes
  * its n_tau(M_b, k_b) x N_b x N_b values of G(tau_j, tau_j) to Gtt_pool and of

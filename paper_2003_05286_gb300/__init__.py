@@ -20,7 +20,7 @@ from . import _abi
 
 __all__ = ["Handle", "greens", "logdet", "greens_tdisplaced", "greens_tdisplaced_all",
            "greens_tdisplaced_from",
-           "logdet_grad", "greens_ragged", "RaggedBatch",
+           "logdet_grad", "greens_ragged", "RaggedBatch", "Batched",
            "greens_tdisplaced_ragged", "logdet_grad_ragged", "selftest_wait_timeout",
            "selftest_fp64_rate", "LogDet",
            "n_tau", "lib"]
@@ -56,6 +56,20 @@ class Handle:
             self.set_inversion_scheme(inversion)
         if decomposition != _abi.DECOMP_QR:
             self.set_decomposition(decomposition)
+
+    def register_K(self, K: torch.Tensor, dtau: float) -> int:
+        """Registers a hopping matrix (dqmc_register_K): exp(-dtau K) is computed
+        once and kept in the handle; returns the id for dqmc_desc.K_id."""
+        if not (K.is_cuda and K.dtype == torch.float64 and K.dim() == 2 and K.shape[0] == K.shape[1]):
+            raise ValueError("K must be a square CUDA float64 tensor")
+        K = K.contiguous()
+        kid = C.c_int(-1)
+        self.bind_stream()
+        _abi.check(self._lib.dqmc_register_K(self.h, K.shape[0], _ptr(K), float(dtau), C.byref(kid)),
+                   "dqmc_register_K")
+        self._kN = getattr(self, "_kN", [])
+        self._kN.append(int(K.shape[0]))
+        return kid.value
 
     def set_decomposition(self, decomposition: int):
         """Chain stabiliser: DECOMP_QR (pivoted QR, default) or DECOMP_JACOBI (one-sided SVD)."""
@@ -335,6 +349,51 @@ class RaggedBatch:
         _abi.check(h._lib.dqmc_greens_ragged(h.h, len(self.descs), self.descs, _ptr(self.K),
                                              _ptr(self.V), _ptr(self.Gp), _ptr(self.ld),
                                              _ptr(self.sg), _ptr(self.st)), "dqmc_greens_ragged")
+        return self.Gs, self.ld, self.sg, self.st
+
+
+class Batched:
+    """Instances over hopping matrices registered on ``handle`` (dqmc_greens_batched).
+
+    ``items``: list of (K_id, V (M, N) CUDA float64, k).  The dqmc_desc array is
+    built once and kept on the device together with the V pool and the
+    outputs; ``run`` calls the library on them (a single graph launch on a
+    repeated call in graph mode)."""
+
+    def __init__(self, handle: Handle, items):
+        kN = getattr(handle, "_kN", [])
+        descs = (_abi.DqmcDesc * len(items))()
+        offV = offG = 0
+        Vs = []
+        for i, (kid, V, k) in enumerate(items):
+            if not 0 <= kid < len(kN):
+                raise ValueError(f"K_id {kid} is not registered on this handle")
+            N = kN[kid]
+            M = V.shape[0]
+            if V.dim() != 2 or V.shape[1] != N:
+                raise ValueError(f"field of instance {i} has shape {tuple(V.shape)}, N = {N}")
+            descs[i] = _abi.DqmcDesc(N, M, int(k), int(kid), offV, offG)
+            Vs.append(V.reshape(-1))
+            offV += M * N
+            offG += N * N
+        dev = Vs[0].device
+        raw = bytes(C.string_at(C.addressof(descs), C.sizeof(descs)))
+        self.desc = torch.frombuffer(bytearray(raw), dtype=torch.uint8).to(dev)
+        self.handle = handle
+        self.V = torch.cat(Vs).to(dtype=torch.float64).contiguous()
+        self.Gp = torch.empty(offG, dtype=torch.float64, device=dev)
+        B = len(items)
+        self.ld = torch.empty(B, dtype=torch.float64, device=dev)
+        self.sg = torch.empty(B, dtype=torch.int32, device=dev)
+        self.st = torch.empty(B, dtype=torch.int32, device=dev)
+        self.Gs = [self.Gp[d.off_G: d.off_G + d.N * d.N].view(d.N, d.N) for d in descs]
+
+    def run(self):
+        h = self.handle
+        h.bind_stream()
+        _abi.check(h._lib.dqmc_greens_batched(h.h, len(self.Gs), _ptr(self.desc), _ptr(self.V),
+                                              _ptr(self.Gp), _ptr(self.ld), _ptr(self.sg),
+                                              _ptr(self.st)), "dqmc_greens_batched")
         return self.Gs, self.ld, self.sg, self.st
 
 

@@ -26,6 +26,11 @@ INV_LOH, INV_PLAIN = 0, 1
 DECOMP_QR, DECOMP_JACOBI = 0, 1
 
 
+class DqmcDesc(C.Structure):
+    _fields_ = [("N", C.c_int), ("M", C.c_int), ("k", C.c_int), ("K_id", C.c_int),
+                ("off_V", C.c_longlong), ("off_G", C.c_longlong)]
+
+
 class DqmcInstance(C.Structure):
     _fields_ = [("N", C.c_int), ("M", C.c_int), ("k", C.c_int), ("pad", C.c_int),
                 ("dtau", C.c_double), ("off_K", C.c_longlong), ("off_V", C.c_longlong),
@@ -65,6 +70,8 @@ SIGNATURES = {
     "dqmc_greens_noalloc": (_I, [_P, _I, _I, _I, _P, _D, _P, _I, _P, _P, _P, _P]),
     "dqmc_selftest_wait_timeout": (_I, [_P, _P]),
     "dqmc_selftest_fp64_rate": (_I, [_P, _I, _I, C.POINTER(_D), C.POINTER(_D)]),
+    "dqmc_register_K": (_I, [_P, _I, _P, _D, C.POINTER(_I)]),
+    "dqmc_greens_batched": (_I, [_P, _I, _P, _P, _P, _P, _P, _P]),
     "dqmc_set_graph_mode": (_I, [_P, _I]),
     "dqmc_greens_tdisplaced_ragged": (_I, [_P, _I, C.POINTER(DqmcInstance), _P, _P, _P, _P, _P]),
     "dqmc_greens_tdisplaced_ragged_ex": (_I, [_P, _I, C.POINTER(DqmcInstance), _P, _P, _P, _P, _P,

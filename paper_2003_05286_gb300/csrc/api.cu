@@ -76,6 +76,13 @@ struct dqmc_handle_s {
   size_t rtab_bytes = 0;
   unsigned long long rtab_key = 0;
   cudaEvent_t rfork = nullptr;
+  // hopping matrices registered with dqmc_register_K: K and exp(-dtau K) at
+  // equal offsets (in doubles) of two grow-only device pools
+  struct KReg { int N; double dtau; long long off; };
+  std::vector<KReg> kreg;
+  double* kpool = nullptr;
+  double* epool = nullptr;
+  long long kcap = 0, kused = 0;
 };
 
 namespace {
@@ -962,6 +969,8 @@ dqmc_status dqmc_destroy(dqmc_handle h) {
   if (h->rws) cudaFree(h->rws);
   if (h->rtab) cudaFree(h->rtab);
   if (h->rfork) cudaEventDestroy(h->rfork);
+  if (h->kpool) cudaFree(h->kpool);
+  if (h->epool) cudaFree(h->epool);
   delete h;
   return DQMC_OK;
 }
@@ -2074,9 +2083,12 @@ struct RaggedGroupWs {
 
 extern "C" {
 
-dqmc_status dqmc_greens_ragged(dqmc_handle h, int batch, const dqmc_instance* desc,
-                               const double* K_pool, const double* V_pool, double* G_pool,
-                               double* logdet, int* sign, int* status) {
+// E_pool (nullable): exp(-dtau K) of every K of K_pool at the same offsets
+// (the registered hopping matrices of dqmc_greens_batched); without it each
+// group computes its exponential.
+static dqmc_status ragged_impl(dqmc_handle h, int batch, const dqmc_instance* desc,
+                               const double* K_pool, const double* E_pool, const double* V_pool,
+                               double* G_pool, double* logdet, int* sign, int* status) {
   if (!h || batch < 0) return DQMC_ERR_ARG;
   h->launches = 0;
   h->cur = h->stream;
@@ -2205,7 +2217,7 @@ dqmc_status dqmc_greens_ragged(dqmc_handle h, int batch, const dqmc_instance* de
   key.add(dkey);
   key.addp(K_pool); key.addp(V_pool); key.addp(G_pool);
   key.addp(logdet); key.addp(sign); key.addp(status);
-  key.addp(h->rtab);
+  key.addp(h->rtab); key.addp(E_pool);
   return graph_call(h, key, [&]() -> dqmc_status {
     h->launches = 0;
     h->cur = h->stream;
@@ -2225,9 +2237,10 @@ dqmc_status dqmc_greens_ragged(dqmc_handle h, int batch, const dqmc_instance* de
       cudaStream_t st = h->cur;
       rc = [&]() -> dqmc_status {
         if (cudaMemsetAsync(w.st, 0, nb * sizeof(int), st) != cudaSuccess) return DQMC_ERR_CUDA;
-        CKS(run_expm(h, K_pool + g.offK, N, g.dtau, -1.0, w.ew, w.st, nb));
+        const double* E = E_pool ? E_pool + g.offK : w.ew.t0;
+        if (!E_pool) CKS(run_expm(h, K_pool + g.offK, N, g.dtau, -1.0, w.ew, w.st, nb));
         CK(exp_gather(V_pool, w.offV, w.Mb, nb, (int)Mp, N, w.expV, w.st, st));
-        if (mixed) CK(split_E(w.ew.t0, N, 0, w.cw, st));   // E slices, shared by the group
+        if (mixed) CK(split_E(E, N, 0, w.cw, st));   // E slices, shared by the group
         CK(set_identity(w.U, NN, N, nb, st));
         CK(set_const(w.D, (long long)N * nb, 1.0, st));
         CK(set_identity(w.X0, NN, N, nb, st));
@@ -2236,7 +2249,7 @@ dqmc_status dqmc_greens_ragged(dqmc_handle h, int batch, const dqmc_instance* de
         sl.D = w.D; sl.slotD = 0; sl.instD = N;
         sl.X = w.X0; sl.slotX = 0; sl.instX = NN;
         sl.X2 = w.X1;
-        CKS(run_chain(h, +1, nb, N, g.Mmax, k, w.ew.t0, w.expV, Mp * N, sl, w.cw, w.st, w.Mb));
+        CKS(run_chain(h, +1, nb, N, g.Mmax, k, E, w.expV, Mp * N, sl, w.cw, w.st, w.Mb));
         const double* Xf = (ncmax & 1) ? w.X1 : w.X0;
         CKS(run_inversion(h, nb, N, w.U, NN, w.D, N, Xf, NN, G_pool ? w.G : nullptr, w.ld, w.sg,
                           w.st, w.lw, w.pw));
@@ -2252,6 +2265,101 @@ dqmc_status dqmc_greens_ragged(dqmc_handle h, int batch, const dqmc_instance* de
     h->cur = h->stream;
     return rc;
   });
+}
+
+dqmc_status dqmc_greens_ragged(dqmc_handle h, int batch, const dqmc_instance* desc,
+                               const double* K_pool, const double* V_pool, double* G_pool,
+                               double* logdet, int* sign, int* status) {
+  return ragged_impl(h, batch, desc, K_pool, nullptr, V_pool, G_pool, logdet, sign, status);
+}
+
+dqmc_status dqmc_register_K(dqmc_handle h, int N, const double* K, double dtau, int* K_id) {
+  if (!h || !K || !K_id || N < 1 || N > 1024 || !(dtau >= 0.0) || !(dtau < 1e300))
+    return DQMC_ERR_ARG;
+  if (((uintptr_t)K) & 7) return DQMC_ERR_ARG;
+  if (h->capturing) return DQMC_ERR_UNSUPPORTED;
+  *K_id = -1;
+  const long long NN = (long long)N * N;
+  h->cur = h->stream;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return DQMC_ERR_CUDA;
+  if (h->kused + NN > h->kcap) {
+    // grow both pools; a recorded graph may refer to the old ones
+    long long cap = h->kcap * 2 > h->kused + NN ? h->kcap * 2 : h->kused + NN;
+    double *kp = nullptr, *ep = nullptr;
+    if (cudaMalloc(&kp, cap * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&ep, cap * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      if (kp) cudaFree(kp);
+      return DQMC_ERR_NOMEM;
+    }
+    if (h->kused > 0 &&
+        (cudaMemcpy(kp, h->kpool, h->kused * sizeof(double), cudaMemcpyDeviceToDevice) != cudaSuccess ||
+         cudaMemcpy(ep, h->epool, h->kused * sizeof(double), cudaMemcpyDeviceToDevice) != cudaSuccess)) {
+      cudaFree(kp);
+      cudaFree(ep);
+      return DQMC_ERR_CUDA;
+    }
+    if (h->kpool) cudaFree(h->kpool);
+    if (h->epool) cudaFree(h->epool);
+    h->kpool = kp;
+    h->epool = ep;
+    h->kcap = cap;
+    h->gvalid = false;
+  }
+  const long long off = h->kused;
+  const cudaMemcpyKind kind =
+      h->pmode == DQMC_PTR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  if (cudaMemcpy(h->kpool + off, K, NN * sizeof(double), kind) != cudaSuccess) return DQMC_ERR_CUDA;
+  // exp(-dtau K) once, through the handle's workspace
+  ExpmWs ew;
+  Arena measure;
+  take_expm(measure, N, ew);
+  CKS(ensure_ws(h, measure.off));
+  Arena ar;
+  ar.base = h->ws;
+  take_expm(ar, N, ew);
+  CKS(run_expm(h, h->kpool + off, N, dtau, -1.0, ew, nullptr, 0));
+  int bad = 0;
+  if (cudaMemcpyAsync(h->epool + off, ew.t0, NN * sizeof(double), cudaMemcpyDeviceToDevice,
+                      h->stream) != cudaSuccess ||
+      cudaMemcpyAsync(&bad, ew.asym, sizeof(int), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess)
+    return DQMC_ERR_CUDA;
+  if (bad) return DQMC_ERR_ARG;   // not symmetric / not finite / norm beyond the squarings
+  h->kreg.push_back({N, dtau, off});
+  h->kused += NN;
+  *K_id = (int)h->kreg.size() - 1;
+  return DQMC_OK;
+}
+
+dqmc_status dqmc_greens_batched(dqmc_handle h, int batch, const dqmc_desc* desc,
+                                const double* V_pool, double* G_pool, double* logdet, int* sign,
+                                int* status) {
+  if (!h || batch < 0) return DQMC_ERR_ARG;
+  h->launches = 0;
+  if (batch == 0) return DQMC_OK;
+  if (!desc || !V_pool) return DQMC_ERR_ARG;
+  if (h->pmode == DQMC_PTR_HOST) return DQMC_ERR_UNSUPPORTED;
+  if (h->capturing) return DQMC_ERR_UNSUPPORTED;
+  // the descriptors live on the device: read them back once, after whatever
+  // the caller queued on the stream before this call
+  std::vector<dqmc_desc> d(batch);
+  if (cudaMemcpyAsync(d.data(), desc, (size_t)batch * sizeof(dqmc_desc), cudaMemcpyDeviceToHost,
+                      h->stream) != cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return DQMC_ERR_ARG;
+  }
+  std::vector<dqmc_instance> inst(batch);
+  for (int b = 0; b < batch; ++b) {
+    const dqmc_desc& x = d[b];
+    if (x.K_id < 0 || x.K_id >= (int)h->kreg.size() || x.N != h->kreg[x.K_id].N)
+      return DQMC_ERR_ARG;
+    const auto& r = h->kreg[x.K_id];
+    inst[b] = dqmc_instance{x.N, x.M, x.k, 0, r.dtau, r.off, x.off_V, x.off_G};
+  }
+  return ragged_impl(h, batch, inst.data(), h->kpool, h->epool, V_pool, G_pool, logdet, sign,
+                     status);
 }
 
 }  // extern "C"

@@ -215,3 +215,45 @@ def test_ragged_graph_replay(dq, prec):
         assert np.abs(Gs2[i].cpu().numpy() - Go).max() <= tol * max(1.0, np.abs(Go).max())
     eager.close()
     hg.close()
+
+
+def test_registered_K_batched(dq):
+    """dqmc_register_K + dqmc_greens_batched with a device-resident descriptor
+    array: against the oracle, bitwise equal to the ragged call on the same
+    instances (same exponentials, same kernels), replayed as a graph."""
+    insts, items = _uneven_M_items(53)
+    for graphs in (False, True):
+        h = dq.Handle(graphs=graphs)
+        ids = {}
+        for x in insts:
+            L = int(round(x.N ** 0.5))
+            if L not in ids:
+                ids[L] = h.register_K(_dev(di.square_hopping(L)), 0.1)
+        bt = dq.Batched(h, [(ids[int(round(x.N ** 0.5))], _dev(x.V), x.k) for x in insts])
+        for _ in range(2):
+            Gs, ld, sg, st = bt.run()
+            torch.cuda.synchronize()
+            assert int((st != 0).sum()) == 0
+        Gr, ldr, sgr, _ = dq.greens_ragged(items, handle=dq.Handle())
+        for i, x in enumerate(insts):
+            assert torch.equal(Gs[i], Gr[i]), i
+            assert float(ld[i]) == float(ldr[i]) and int(sg[i]) == int(sgr[i])
+            Go, ldo, so = od.greens(x.K, x.dtau, x.V, x.k)
+            assert np.abs(Gs[i].cpu().numpy() - Go).max() <= GTOL * max(1.0, np.abs(Go).max())
+        h.close()
+
+
+def test_registered_K_errors(dq):
+    h = dq.Handle()
+    K = di.square_hopping(3)
+    K[0, 1] += 0.5                                   # not symmetric
+    with pytest.raises(RuntimeError):
+        h.register_K(_dev(K), 0.1)
+    kid = h.register_K(_dev(di.square_hopping(3)), 0.1)
+    assert kid == 0
+    inst = di.hubbard_instance(3, 4.0, 0.1, 1.0, 5, 3)
+    bt = dq.Batched(h, [(kid, _dev(inst.V), 5)])
+    bt.desc.view(torch.int32)[3] = 7                 # K_id of instance 0 -> not registered
+    with pytest.raises(RuntimeError):
+        bt.run()
+    h.close()
