@@ -109,6 +109,8 @@ def parse():
                    help="CUDA-graph mode of the handle (auto: on for the launch-bound workloads)")
     p.add_argument("--fold", default="auto", choices=["auto", "tree", "sequential"],
                    help="equal-time chain fold of the handle (auto: tree for small batches)")
+    p.add_argument("--gemm-tile", type=int, default=0, choices=[0, 32, 48, 64],
+                   help="FP64 product tile edge (0: chosen by size)")
     p.add_argument("--mixed-slices", type=int, default=8,
                    help="also time the mixed chain with this many BF16 slices (0: skip)")
     return p.parse_args()
@@ -820,7 +822,9 @@ def measure_other(args, wl, rank, world, peak=None):
     fp64_peak = peak["dfma"]["tflops"]
     h = dq.Handle(chain_precision=prec, graphs=graphs, fold=FOLDS[args.fold])
     h.bind_stream()
-    extra = {}
+    if getattr(args, "gemm_tile", 0):
+        h.set_gemm_tile(args.gemm_tile)
+    extra = {"gemm_tile": getattr(args, "gemm_tile", 0)}
     if name == "ragged_1024":
         from paper_2003_05286_gb300 import tune
         insts0 = [di.ragged_params(rank * batch + i) for i in range(batch)]
