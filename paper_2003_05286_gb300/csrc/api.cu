@@ -334,6 +334,20 @@ dqmc_status chunk_products(dqmc_handle h, int dir, int batch, int N, int M, int 
   long long sprev = s.instU;
   double* bufs[2] = {w.C0, w.C1};
   int nb = 0;
+  if (w.oz_s == 0 && N <= CHAIN_SMALL_MAX_N && batch <= 65535 && (dir > 0 || !lim)) {
+    // small N: the whole chunk in one launch, each CTA applying every slice
+    // to a block of columns held in shared memory
+    ChainSmallArgs cs;
+    cs.N = N; cs.batch = batch; cs.nslices = hi - lo + 1; cs.dir = dir; cs.lo = lo; cs.hi = hi;
+    cs.E = E; cs.transE = dir < 0 ? 1 : 0;
+    cs.X = prev; cs.sX = sprev;
+    cs.C = w.C0; cs.sC = NN;
+    cs.expV = expV; cs.sV = sV;
+    cs.lim = lim; cs.lim_base = lo;
+    CKP(PC_CHAIN, 2.0 * N * N * (double)N * batch * (hi - lo + 1), chain_small(cs, st));
+    *out = w.C0;
+    return DQMC_OK;
+  }
   for (int i = 0; i <= hi - lo; ++i) {
     const int l = dir > 0 ? lo + i : hi - i;
     if (w.oz_s > 0) {
@@ -629,7 +643,21 @@ dqmc_status run_chain_tree(dqmc_handle h, int batch, int N, int M, int k, const 
   double* bufs[2] = {w.C0, w.C1};
   const double* prev = w.Iden;
   long long sprev = 0;
-  for (int i = 0; i < k; ++i) {
+  const bool small = N <= CHAIN_SMALL_MAX_N && Q <= 65535;
+  if (small) {
+    // small N: the k slices of every chunk in one launch (padding chunks copy
+    // the identity through)
+    ChainSmallArgs cs;
+    cs.N = N; cs.batch = Q; cs.nslices = k; cs.dir = 1; cs.lo = 1; cs.hi = k;
+    cs.E = E; cs.X = w.Iden; cs.sX = 0;
+    cs.C = bufs[0]; cs.sC = NN;
+    cs.expV = expV; cs.sV = sV; cs.divS = P0; cs.sV_inner = (long long)k * N;
+    cs.lim = w.len; cs.lim_base = 1;
+    CKP(PC_CHAIN, f2 * Q * k, chain_small(cs, st));
+    prev = bufs[0];
+    sprev = NN;
+  }
+  for (int i = 0; i < k && !small; ++i) {
     GemmArgs g;
     g.M = g.N = g.K = N;
     g.batch = Q;

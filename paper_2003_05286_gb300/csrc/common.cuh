@@ -64,6 +64,28 @@ struct GemmArgs {
 cudaError_t gemm_f64(const GemmArgs& a, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
+// The slice products of one chunk in one launch for N <= CHAIN_SMALL_MAX_N
+// (chain_small.cu): for s = 0 .. nslices-1 with l = lo + s (dir > 0) or
+// l = hi - s (dir < 0)
+//   dir > 0:  C_b <- E diag(ev_b(l)) C_b        dir < 0:  C_b <- diag(ev_b(l)) E^T C_b
+// starting from C_b = X_b (transE selects E^T for the backward chain), with
+// ev_b(l) = expV + (b / divS) sV + (b % divS) sV_inner + (l - 1) N.  With lim,
+// instance b applies only the slices s with lim[b] >= lim_base + s (its
+// chain has ended after that), so its result is then the last one computed.
+// Bitwise the result of the corresponding gemm_f64 launches.
+// ---------------------------------------------------------------------------
+constexpr int CHAIN_SMALL_MAX_N = 128;
+struct ChainSmallArgs {
+  int N = 0, batch = 0, nslices = 0, dir = 1, lo = 1, hi = 1;
+  const double* E = nullptr; int transE = 0;
+  const double* X = nullptr; long long sX = 0;
+  double* C = nullptr; long long sC = 0;
+  const double* expV = nullptr; long long sV = 0, sV_inner = 0; int divS = 1;
+  const int* lim = nullptr; int lim_base = 1;
+};
+cudaError_t chain_small(const ChainSmallArgs& a, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
 // Column-pivoted Householder QR, one CTA per instance (Sec. 4.2.2).
 //   Y = A diag(Din) ;  Y P = Q R ;  U = Q, D = |diag R|, T = D^{-1} R (upper,
 //   pivoted column order, zeros below the diagonal), perm = P as an index map.
