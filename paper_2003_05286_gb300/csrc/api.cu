@@ -527,22 +527,23 @@ bool pipeline_enabled() {
 }
 
 // Number of staggered sub-batches of an equal-time chain: DQMC_PIPELINE=n
-// (2..4) overrides the default (2 for FP64 products, 4 for tensor-core ones).
+// (2..8) overrides the default (2 for FP64 products, 4 for tensor-core ones).
+constexpr int kMaxJobs = 8;
 int pipeline_jobs(bool mixed) {
   const char* e = getenv("DQMC_PIPELINE");
-  if (e && e[0] >= '2' && e[0] <= '4' && e[1] == 0) return e[0] - '0';
+  if (e && e[0] >= '2' && e[0] <= '8' && e[1] == 0) return e[0] - '0';
   return mixed ? 4 : 2;
 }
 
 dqmc_status run_chain_multi(dqmc_handle h, const ChainJob* job, int nj, int N, int M, int k,
                             const double* E) {
-  if (nj < 1 || nj > 4) return DQMC_ERR_ARG;
+  if (nj < 1 || nj > kMaxJobs) return DQMC_ERR_ARG;
   CKS(ensure_aux(h, (size_t)nj));
   cudaStream_t main = h->stream;
   cudaEvent_t fork = h->auxev[0];
   cudaEventRecord(fork, main);
   for (int i = 0; i < nj; ++i) cudaStreamWaitEvent(h->aux[i], fork, 0);
-  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev[kMaxJobs] = {};
   dqmc_status rc = DQMC_OK;
   for (int i = 0; i < nj && rc == DQMC_OK; ++i)
     if (cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming) != cudaSuccess) rc = DQMC_ERR_CUDA;
@@ -1296,7 +1297,7 @@ static dqmc_status greens_impl(dqmc_handle h, int batch, int N, int M, const dou
     if (batch >= 4 * nj && pipeline_enabled()) {
       // nj sub-batches on nj streams, product phases staggered so that the QRs
       // of some sub-batches run while the others multiply
-      ChainJob J[4];
+      ChainJob J[kMaxJobs];
       long long o = 0;
       for (int q = 0; q < nj; ++q) {
         const int nb = batch / nj + (q < batch % nj ? 1 : 0);

@@ -496,6 +496,9 @@ __device__ __forceinline__ double group_sum(double v) {
 template <int NT, int TPC, int NQ>
 __global__ void __launch_bounds__(NT) qrp_fused_kernel(const QrpArgs a) {
   constexpr int NW = NT / 32, CPW = 32 / TPC, BATCH = 8;
+  // warps of the reflector step and rows per lane each
+  constexpr int NR = (NQ >= 4 && NW >= 4) ? 4 : 1, KQ = NQ / NR;
+  static_assert(NQ % NR == 0, "rows of the reflector must split evenly");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int N = a.N;
   // a.smem_mats: 0 = W and U in global memory, 1 = W in shared memory,
@@ -517,6 +520,7 @@ __global__ void __launch_bounds__(NT) qrp_fused_kernel(const QrpArgs a) {
   __shared__ float sk[NW];
   __shared__ int si[NW];
   __shared__ int s_flag;
+  __shared__ double s_red[5];                  // partial sums of the reflector step, alpha
 
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int rg = lane / CPW;                   // row group: rows r = rg (mod TPC)
@@ -557,11 +561,18 @@ __global__ void __launch_bounds__(NT) qrp_fused_kernel(const QrpArgs a) {
     // the reflector for position jn from column P -------------------------
     double* vcur = vA;   // v_j
     double* vnxt = vB;   // v_{j+1}
+    // The reflector's vector work (update of the pivot column, its sum of
+    // squares, the scaling, the stores) is spread over NR warps, one per SM
+    // sub-partition: each FP64 warp instruction holds its sub-partition's
+    // pipe for 64 cycles, and this step is on every pivot step's critical
+    // path.  Warp w owns rows lane + 32 (w + NR k).  The partial sums meet in
+    // shared memory behind a named barrier of those NR warps and every one of
+    // them forms the same scalars in the same order.
     auto vote_and_reflect = [&](float key, int idx, int jn) {
       warp_argmax(key, idx);
       if (lane == 0) { sk[wid] = key; si[wid] = idx; }
       __syncthreads();
-      if (wid == 0) {
+      if (wid < NR) {
         key = lane < NW ? sk[lane] : -INFINITY;
         idx = lane < NW ? si[lane] : 0x7fffffff;
         warp_argmax_all(key, idx);
@@ -569,23 +580,31 @@ __global__ void __launch_bounds__(NT) qrp_fused_kernel(const QrpArgs a) {
         const int j = jn - 1;
         const bool upd = j >= 0;
         const double wP = upd ? wsm[P] : 0.0;
-        double xp[NQ], xo[NQ];
+        double xp[KQ], xo[KQ];
 #pragma unroll
-        for (int k = 0; k < NQ; ++k) {
-          const int r = lane + 32 * k;
+        for (int k = 0; k < KQ; ++k) {
+          const int r = lane + 32 * (wid + NR * k);
           xp[k] = r < N ? W[(long long)r * N + P] : 0.0;
           xo[k] = (r < N && P != jn) ? W[(long long)r * N + jn] : 0.0;
         }
         double sig = 0.0, alpha = 0.0;
 #pragma unroll
-        for (int k = 0; k < NQ; ++k) {
-          const int r = lane + 32 * k;
+        for (int k = 0; k < KQ; ++k) {
+          const int r = lane + 32 * (wid + NR * k);
           if (upd && r >= j && r < N) xp[k] = fma(-vcur[r], wP, xp[k]);
           if (r == jn) alpha = xp[k];
           if (r > jn && r < N) sig = fma(xp[k], xp[k], sig);
         }
         sig = warp_sum_all(sig);
-        alpha = __shfl_sync(FULL, alpha, jn & 31);
+        if (NR == 1) {
+          alpha = __shfl_sync(FULL, alpha, jn & 31);
+        } else {
+          if (lane == 0) s_red[wid] = sig;
+          if (((jn >> 5) % NR) == wid && lane == (jn & 31)) s_red[NR] = alpha;
+          asm volatile("bar.sync 1, %0;" ::"r"(NR * 32) : "memory");
+          sig = (s_red[0] + s_red[1]) + (s_red[2] + s_red[3]);
+          alpha = s_red[NR];
+        }
         double tau = 0.0, scal = 0.0, beta = alpha;
         if (sig > 0.0) {
           const double nrm = sqrt(fma(alpha, alpha, sig));
@@ -594,8 +613,8 @@ __global__ void __launch_bounds__(NT) qrp_fused_kernel(const QrpArgs a) {
           scal = 1.0 / (alpha - beta);
         }
 #pragma unroll
-        for (int k = 0; k < NQ; ++k) {
-          const int r = lane + 32 * k;
+        for (int k = 0; k < KQ; ++k) {
+          const int r = lane + 32 * (wid + NR * k);
           if (r < N) {
             // column jn <- pivot column: R rows (final above j, updated at j), beta
             if (r < j) { if (P != jn) W[(long long)r * N + jn] = xp[k]; }
@@ -608,16 +627,16 @@ __global__ void __launch_bounds__(NT) qrp_fused_kernel(const QrpArgs a) {
             if (r >= jn) T[(long long)jn * N + r] = v;
           }
         }
-        if (lane == 0) {
-          taus[jn] = tau;
+        if (wid == 0) {
+          // the per-column bookkeeping follows the swap, one array per lane
+          if (lane == 6) taus[jn] = tau;
           if (P != jn) {
-            double t;
-            t = nrm2[jn]; nrm2[jn] = nrm2[P]; nrm2[P] = t;
-            t = ref2[jn]; ref2[jn] = ref2[P]; ref2[P] = t;
-            t = dsc[jn]; dsc[jn] = dsc[P]; dsc[P] = t;
-            t = wsm[jn]; wsm[jn] = wsm[P]; wsm[P] = t;
-            float f = logd[jn]; logd[jn] = logd[P]; logd[P] = f;
-            int q = perm[jn]; perm[jn] = perm[P]; perm[P] = q;
+            if (lane == 0) { const double t = nrm2[jn]; nrm2[jn] = nrm2[P]; nrm2[P] = t; }
+            else if (lane == 1) { const double t = ref2[jn]; ref2[jn] = ref2[P]; ref2[P] = t; }
+            else if (lane == 2) { const double t = dsc[jn]; dsc[jn] = dsc[P]; dsc[P] = t; }
+            else if (lane == 3) { const double t = wsm[jn]; wsm[jn] = wsm[P]; wsm[P] = t; }
+            else if (lane == 4) { const float f = logd[jn]; logd[jn] = logd[P]; logd[P] = f; }
+            else if (lane == 5) { const int q = perm[jn]; perm[jn] = perm[P]; perm[P] = q; }
           }
         }
       }
@@ -810,5 +829,6 @@ cudaError_t qrp_f64(const QrpArgs& a, cudaStream_t st) {
   }
   return cudaGetLastError();
 }
+
 
 }  // namespace dqmc
