@@ -56,7 +56,8 @@ typedef enum {
   DQMC_ERR_SINGULAR = 5,   /* (status bit) exactly singular pivot */
   DQMC_ERR_TIMEOUT = 6,    /* a bounded device-side wait gave up */
   DQMC_ERR_UNSUPPORTED = 7, /* configuration not built into this library */
-  DQMC_ERR_SCRATCH = 8      /* dqmc_greens_noalloc: problem needs more than its fixed scratch */
+  DQMC_ERR_SCRATCH = 8,     /* dqmc_greens_noalloc: problem needs more than its fixed scratch */
+  DQMC_ERR_CHECK = 9        /* debug build: a device-side check failed (dqmc_debug_read) */
 } dqmc_status;
 
 /* Bits of the per-instance device status word. */
@@ -174,6 +175,19 @@ dqmc_status dqmc_set_decomposition(dqmc_handle h, int decomposition);
 long long dqmc_last_launch_count(dqmc_handle h);
 /* Bytes of device workspace the handle currently holds. */
 long long dqmc_workspace_bytes(dqmc_handle h);
+/* Device bytes the handle holds in all its grow-only buffers: the workspace,
+ * the staging buffer and index tables of the ragged calls, and the two pools
+ * of dqmc_register_K. */
+long long dqmc_device_bytes(dqmc_handle h);
+/* Cap on dqmc_device_bytes; 0 (the default) means none.  A call that would
+ * grow a buffer past the cap returns DQMC_ERR_NOMEM without allocating and
+ * without releasing the buffer it would have replaced, so the handle stays
+ * usable for problems that fit; what that call had already written to its
+ * outputs is unspecified.  Lowering the cap keeps the buffers already held.
+ * It bounds the library's memory inside a larger application, and it is how
+ * the tests drive the allocation-failure paths without exhausting the
+ * device.  bytes < 0: DQMC_ERR_ARG. */
+dqmc_status dqmc_set_memory_limit(dqmc_handle h, long long bytes);
 const char* dqmc_status_string(dqmc_status s);
 
 /* Per-kernel-class timing of subsequent compute calls: every launch of the
@@ -421,6 +435,38 @@ dqmc_status dqmc_selftest_wait_timeout(void* stream, int* status);
  * frees a small device buffer.  Errors: DQMC_ERR_ARG (NULL tflops, kind not
  * 0..2, iters outside 1..2^24), DQMC_ERR_NOMEM, DQMC_ERR_CUDA. */
 dqmc_status dqmc_selftest_fp64_rate(void* stream, int kind, int iters, double* tflops, double* ms);
+
+/* Debug build.  The same sources compiled with -DDQMC_DEBUG give a second
+ * library, lib/libdqmc_gb300_debug.so, with the same entry points and the
+ * same arithmetic (results are bitwise those of the release library).  Its
+ * kernels check, on the device, the invariants their index arithmetic
+ * relies on: the launch geometry and the dynamic shared memory their layout
+ * needs, leading dimensions that cover their rows, gathered and pivoted row
+ * indices inside the matrix, the 16-byte alignment and extent of every bulk
+ * copy and vector store, and the tile window of every tensor-core MMA.  A
+ * failed check never traps: it records (source file, line, the offending
+ * value) -- the first failure per source file is kept -- and the thread
+ * skips the access or the CTA leaves the kernel.  Each launch outside a
+ * stream capture is then waited for and the records read, so the call that
+ * made it returns DQMC_ERR_CHECK (a graph replay is read after its launch).
+ * The debug library is slower (one synchronisation per launch).  The paper
+ * has no counterpart: this is a development aid. */
+/* 1 in the debug library, 0 in the release library. */
+int dqmc_is_debug_build(void);
+/* Synchronises the device and returns the first recorded check failure in
+ * *file (a static string naming the source file; NULL when none is
+ * recorded), *line and *value; clear != 0 resets the records.  Release
+ * library: DQMC_ERR_UNSUPPORTED.  NULL outputs: DQMC_ERR_ARG. */
+dqmc_status dqmc_debug_read(int clear, const char** file, int* line, int* value);
+/* Self-test of the check mechanism (debug library): one CTA of 64 threads
+ * writes x[i] = i + 1 into an internal 64-element device array behind the
+ * check i < 63, so the last thread's check fails.  *fired = 1 when that
+ * failure was recorded with value 63, its write was skipped and every other
+ * write happened; *value = the recorded value.  The skipped write would
+ * have stayed inside the array.  Synchronous on `stream` (NULL = legacy
+ * default stream); clears the records of api.cu.  Release library:
+ * DQMC_ERR_UNSUPPORTED. */
+dqmc_status dqmc_selftest_check(void* stream, int* fired, int* value);
 
 #ifdef __cplusplus
 }

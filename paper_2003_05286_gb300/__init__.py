@@ -22,7 +22,7 @@ __all__ = ["Handle", "greens", "logdet", "greens_tdisplaced", "greens_tdisplaced
            "greens_tdisplaced_from",
            "logdet_grad", "greens_ragged", "RaggedBatch", "Batched",
            "greens_tdisplaced_ragged", "logdet_grad_ragged", "selftest_wait_timeout",
-           "selftest_fp64_rate", "LogDet",
+           "selftest_fp64_rate", "LogDet", "is_debug_build", "debug_read", "selftest_check",
            "n_tau", "lib"]
 
 
@@ -136,6 +136,15 @@ class Handle:
     @property
     def workspace_bytes(self) -> int:
         return int(self._lib.dqmc_workspace_bytes(self.h))
+
+    @property
+    def device_bytes(self) -> int:
+        """Device bytes held by all grow-only buffers of the handle."""
+        return int(self._lib.dqmc_device_bytes(self.h))
+
+    def set_memory_limit(self, nbytes: int):
+        """Caps device_bytes (0: no cap); growth past it raises RuntimeError (NOMEM)."""
+        _abi.check(self._lib.dqmc_set_memory_limit(self.h, int(nbytes)), "dqmc_set_memory_limit")
 
 
 _default: dict[int, Handle] = {}
@@ -543,3 +552,26 @@ def selftest_fp64_rate(kind: str = "dfma", iters: int | None = None) -> tuple[fl
     _abi.check(lib().dqmc_selftest_fp64_rate(stream, code, int(iters), C.byref(tf), C.byref(ms)),
                "dqmc_selftest_fp64_rate")
     return tf.value, ms.value
+
+
+def is_debug_build() -> bool:
+    """True when the loaded library is the debug build (DQMC_DEBUG=1 in the environment)."""
+    return bool(lib().dqmc_is_debug_build())
+
+
+def debug_read(clear: bool = False):
+    """First failed device-side check of the debug build as (file, line, value), or
+    None; synchronises the device.  Raises on the release library."""
+    fn, ln, val = C.c_char_p(), C.c_int(), C.c_int()
+    _abi.check(lib().dqmc_debug_read(int(clear), C.byref(fn), C.byref(ln), C.byref(val)),
+               "dqmc_debug_read")
+    return None if fn.value is None else (fn.value.decode(), ln.value, val.value)
+
+
+def selftest_check(stream: torch.cuda.Stream | None = None) -> tuple[bool, int]:
+    """Self-test of the debug build's check mechanism: (fired, recorded value)."""
+    s = stream if stream is not None else torch.cuda.current_stream()
+    fired, val = C.c_int(), C.c_int()
+    _abi.check(lib().dqmc_selftest_check(C.c_void_p(s.cuda_stream), C.byref(fired), C.byref(val)),
+               "dqmc_selftest_check")
+    return bool(fired.value), val.value

@@ -12,6 +12,7 @@ STATUS_STRINGS = {
     3: "device workspace allocation failed", 4: "non-finite value", 5: "singular pivot",
     6: "bounded device wait gave up", 7: "unsupported configuration",
     8: "problem needs more device scratch than the fixed array holds",
+    9: "a device-side check of the debug build failed",
 }
 STATUS_BITS = {
     "NONFINITE_INPUT": 1 << 0, "NONFINITE_SCALE": 1 << 1, "SINGULAR": 1 << 2,
@@ -54,6 +55,8 @@ SIGNATURES = {
     "dqmc_set_decomposition": (_I, [_P, _I]),
     "dqmc_last_launch_count": (C.c_longlong, [_P]),
     "dqmc_workspace_bytes": (C.c_longlong, [_P]),
+    "dqmc_device_bytes": (C.c_longlong, [_P]),
+    "dqmc_set_memory_limit": (C.c_int, [_P, C.c_longlong]),
     "dqmc_status_string": (C.c_char_p, [_I]),
     "dqmc_profile_enable": (_I, [_P, _I]),
     "dqmc_profile_reset": (_I, [_P]),
@@ -70,6 +73,9 @@ SIGNATURES = {
     "dqmc_greens_noalloc": (_I, [_P, _I, _I, _I, _P, _D, _P, _I, _P, _P, _P, _P]),
     "dqmc_selftest_wait_timeout": (_I, [_P, _P]),
     "dqmc_selftest_fp64_rate": (_I, [_P, _I, _I, C.POINTER(_D), C.POINTER(_D)]),
+    "dqmc_is_debug_build": (_I, []),
+    "dqmc_debug_read": (_I, [_I, C.POINTER(C.c_char_p), C.POINTER(_I), C.POINTER(_I)]),
+    "dqmc_selftest_check": (_I, [_P, C.POINTER(_I), C.POINTER(_I)]),
     "dqmc_register_K": (_I, [_P, _I, _P, _D, C.POINTER(_I)]),
     "dqmc_greens_batched": (_I, [_P, _I, _P, _P, _P, _P, _P, _P]),
     "dqmc_set_graph_mode": (_I, [_P, _I]),
@@ -82,12 +88,20 @@ SIGNATURES = {
 _lib = None
 
 
+def debug_requested() -> bool:
+    """True when the environment asks for the debug library (DQMC_DEBUG set, not 0)."""
+    return os.environ.get("DQMC_DEBUG", "0") not in ("", "0")
+
+
 def load(path: str | None = None):
-    """Loads the in-tree shared library; raises if it has not been built."""
+    """Loads the in-tree shared library; raises if it has not been built.
+
+    With DQMC_DEBUG=1 in the environment the debug library (device-side checks,
+    include/dqmc.h) is loaded instead."""
     global _lib
     if _lib is not None:
         return _lib
-    path = path or _build.lib_path()
+    path = path or _build.lib_path(debug=debug_requested())
     if not os.path.exists(path):
         raise RuntimeError(
             f"CUDA library not built ({path} missing): run "

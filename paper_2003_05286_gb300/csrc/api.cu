@@ -83,6 +83,9 @@ struct dqmc_handle_s {
   double* kpool = nullptr;
   double* epool = nullptr;
   long long kcap = 0, kused = 0;
+  // cap on the device bytes all of the above may hold together (0: none);
+  // growth past it fails with DQMC_ERR_NOMEM before any buffer is released
+  size_t mem_limit = 0;
 };
 
 namespace {
@@ -104,12 +107,26 @@ struct Arena {
   }
 };
 
+// Device bytes the handle holds in its grow-only buffers.
+size_t held_bytes(dqmc_handle h) {
+  return h->ws_bytes + h->rws_bytes + h->rtab_bytes + 2 * (size_t)h->kcap * sizeof(double);
+}
+
+// Whether replacing a buffer of `old` bytes by one of `bytes` stays within the
+// handle's limit.
+bool within_limit(dqmc_handle h, size_t old, size_t bytes) {
+  return h->mem_limit == 0 || held_bytes(h) - old + bytes <= h->mem_limit;
+}
+
 dqmc_status ensure_ws(dqmc_handle h, size_t bytes) {
   if (bytes <= h->ws_bytes) return DQMC_OK;
   if (h->capturing) {   // no allocation inside a capture: the caller grows and captures again
     h->ws_need = bytes;
     return DQMC_ERR_NOMEM;
   }
+  if (!within_limit(h, h->ws_bytes, bytes)) return DQMC_ERR_NOMEM;
+  size_t want = bytes + bytes / 8;
+  if (!within_limit(h, h->ws_bytes, want)) want = bytes;
   h->gvalid = false;    // a captured graph refers to the old workspace
   if (h->ws) {
     cudaStreamSynchronize(h->stream);
@@ -117,7 +134,6 @@ dqmc_status ensure_ws(dqmc_handle h, size_t bytes) {
     h->ws = nullptr;
     h->ws_bytes = 0;
   }
-  size_t want = bytes + bytes / 8;
   if (cudaMalloc(&h->ws, want) != cudaSuccess) {
     cudaGetLastError();
     if (cudaMalloc(&h->ws, bytes) != cudaSuccess) {
@@ -160,8 +176,61 @@ void prof_collect(dqmc_handle h) {
   h->pending.clear();
 }
 
+// ---------------------------------------------------------------------------
+// Debug build (-DDQMC_DEBUG): every translation unit with kernels has its own
+// check word (common.cuh); a launch outside a stream capture is waited for
+// and the words are read, so a failed device-side check surfaces as
+// DQMC_ERR_CHECK from the call that made it.
+// ---------------------------------------------------------------------------
+#ifdef DQMC_DEBUG
+}  // namespace
+namespace dqmc {
+unsigned long long check_word_api(bool clear);
+unsigned long long check_word_gemm(bool clear);
+unsigned long long check_word_qrp(bool clear);
+unsigned long long check_word_lu(bool clear);
+unsigned long long check_word_jacobi(bool clear);
+unsigned long long check_word_chain_small(bool clear);
+unsigned long long check_word_ozaki(bool clear);
+}  // namespace dqmc
+namespace {
+struct CheckUnit {
+  const char* file;
+  unsigned long long (*read)(bool clear);
+};
+const CheckUnit kCheckUnits[] = {
+    {"api.cu", dqmc::check_word_api},         {"gemm_f64.cu", dqmc::check_word_gemm},
+    {"qrp_f64.cu", dqmc::check_word_qrp},     {"lu_f64.cu", dqmc::check_word_lu},
+    {"jacobi_f64.cu", dqmc::check_word_jacobi}, {"chain_small.cu", dqmc::check_word_chain_small},
+    {"ozaki_tc.cu", dqmc::check_word_ozaki},
+};
+#endif
+
+static dqmc_status debug_after_launch(dqmc_handle h) {
+#ifdef DQMC_DEBUG
+  if (h->capturing) return DQMC_OK;
+  // a capture the caller runs on its own stream (the allocation-free call)
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(h->cur, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    return DQMC_ERR_CUDA;
+  }
+  if (cs != cudaStreamCaptureStatusNone) return DQMC_OK;
+  if (cudaStreamSynchronize(h->cur) != cudaSuccess) {
+    cudaGetLastError();
+    return DQMC_ERR_CUDA;
+  }
+  for (const CheckUnit& u : kCheckUnits)
+    if (u.read(false)) return DQMC_ERR_CHECK;
+#else
+  (void)h;
+#endif
+  return DQMC_OK;
+}
+
 // Launch wrapper: counts the launch, and brackets it with events when the
 // profiler is on.  cls/flops classify it (flops = algorithmic FP64 flops).
+// The debug build then waits for it and reads the check words.
 #define CKP(cls_, flops_, expr)                                   \
   do {                                                            \
     ProfRec _r{nullptr, nullptr, (cls_), (double)(flops_)};       \
@@ -178,6 +247,8 @@ void prof_collect(dqmc_handle h) {
       if (h->pending.size() > 4096) prof_collect(h);              \
     }                                                             \
     if (_e != cudaSuccess) return DQMC_ERR_CUDA;                  \
+    dqmc_status _d = debug_after_launch(h);                       \
+    if (_d != DQMC_OK) return _d;                                 \
   } while (0)
 #define CK(expr) CKP(PC_OTHER, 0.0, expr)
 #define CKS(expr)                                  \
@@ -1083,6 +1154,13 @@ dqmc_status dqmc_set_gemm_tile(dqmc_handle h, int tile) {
 
 long long dqmc_last_launch_count(dqmc_handle h) { return h ? h->launches : -1; }
 long long dqmc_workspace_bytes(dqmc_handle h) { return h ? (long long)h->ws_bytes : -1; }
+long long dqmc_device_bytes(dqmc_handle h) { return h ? (long long)held_bytes(h) : -1; }
+
+dqmc_status dqmc_set_memory_limit(dqmc_handle h, long long bytes) {
+  if (!h || bytes < 0) return DQMC_ERR_ARG;
+  h->mem_limit = (size_t)bytes;
+  return DQMC_OK;
+}
 
 const char* dqmc_status_string(dqmc_status s) {
   switch (s) {
@@ -1095,6 +1173,7 @@ const char* dqmc_status_string(dqmc_status s) {
     case DQMC_ERR_TIMEOUT: return "bounded device wait gave up";
     case DQMC_ERR_UNSUPPORTED: return "unsupported configuration";
     case DQMC_ERR_SCRATCH: return "problem needs more device scratch than the fixed array holds";
+    case DQMC_ERR_CHECK: return "a device-side check of the debug build failed";
   }
   return "unknown status";
 }
@@ -1134,7 +1213,8 @@ static dqmc_status graph_call(dqmc_handle h, GraphKey key, F&& body) {
   if (same) {
     if (cudaGraphLaunch(h->gexec, h->stream) != cudaSuccess) return DQMC_ERR_CUDA;
     h->launches = h->glaunches;
-    return DQMC_OK;
+    h->cur = h->stream;
+    return debug_after_launch(h);
   }
   if (!h->gstream && cudaStreamCreateWithFlags(&h->gstream, cudaStreamNonBlocking) != cudaSuccess)
     return DQMC_ERR_CUDA;
@@ -1188,7 +1268,7 @@ static dqmc_status graph_call(dqmc_handle h, GraphKey key, F&& body) {
     h->gvalid = true;
     h->glaunches = h->launches;
     if (cudaGraphLaunch(h->gexec, h->stream) != cudaSuccess) return DQMC_ERR_CUDA;
-    return DQMC_OK;
+    return debug_after_launch(h);
   }
   return DQMC_ERR_NOMEM;
 }
@@ -2192,6 +2272,7 @@ static dqmc_status ragged_impl(dqmc_handle h, int batch, const dqmc_instance* de
   layout(ar);
   if (measure_t.off > h->rtab_bytes) {
     if (h->capturing) return DQMC_ERR_UNSUPPORTED;
+    if (!within_limit(h, h->rtab_bytes, measure_t.off)) return DQMC_ERR_NOMEM;
     if (h->rtab) {
       cudaStreamSynchronize(h->stream);
       cudaFree(h->rtab);
@@ -2314,6 +2395,9 @@ dqmc_status dqmc_register_K(dqmc_handle h, int N, const double* K, double dtau, 
   if (h->kused + NN > h->kcap) {
     // grow both pools; a recorded graph may refer to the old ones
     long long cap = h->kcap * 2 > h->kused + NN ? h->kcap * 2 : h->kused + NN;
+    const size_t oldb = 2 * (size_t)h->kcap * sizeof(double);
+    if (!within_limit(h, oldb, 2 * (size_t)cap * sizeof(double))) cap = h->kused + NN;
+    if (!within_limit(h, oldb, 2 * (size_t)cap * sizeof(double))) return DQMC_ERR_NOMEM;
     double *kp = nullptr, *ep = nullptr;
     if (cudaMalloc(&kp, cap * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&ep, cap * sizeof(double)) != cudaSuccess) {
@@ -2431,6 +2515,7 @@ dqmc_status group_uniform(int batch, const dqmc_instance* desc, std::vector<UGro
 
 dqmc_status ensure_rws(dqmc_handle h, size_t bytes) {
   if (bytes <= h->rws_bytes) return DQMC_OK;
+  if (!within_limit(h, h->rws_bytes, bytes)) return DQMC_ERR_NOMEM;
   if (h->rws) {
     cudaStreamSynchronize(h->stream);
     cudaFree(h->rws);
@@ -2564,3 +2649,97 @@ dqmc_status dqmc_logdet_grad_ragged(dqmc_handle h, int batch, const dqmc_instanc
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Read-out of the debug build's device-side checks
+// ---------------------------------------------------------------------------
+namespace {
+// n threads write x[i] = i + 1 behind a check of i < n_checked; with
+// n_checked = n - 1 the last thread's check fails, so it records its index
+// and skips its write, which would have stayed inside x (n elements) anyway.
+__global__ void check_selftest_kernel(double* x, int n, int n_checked) {
+  const int i = threadIdx.x;
+  if (i < n && DQMC_CHECK(i < n_checked, i)) x[i] = i + 1;
+}
+}  // namespace
+
+extern "C" {
+
+int dqmc_is_debug_build(void) {
+#ifdef DQMC_DEBUG
+  return 1;
+#else
+  return 0;
+#endif
+}
+
+dqmc_status dqmc_debug_read(int clear, const char** file, int* line, int* value) {
+  if (!file || !line || !value) return DQMC_ERR_ARG;
+  *file = nullptr;
+  *line = 0;
+  *value = 0;
+#ifdef DQMC_DEBUG
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    cudaGetLastError();
+    return DQMC_ERR_CUDA;
+  }
+  for (const CheckUnit& u : kCheckUnits) {
+    const unsigned long long w = u.read(clear != 0);
+    if (w == ~0ull) return DQMC_ERR_CUDA;
+    if (w && !*file) {
+      *file = u.file;
+      *line = (int)((w >> 32) & 0x7fffffff);
+      *value = (int)(unsigned int)(w & 0xffffffffull);
+    }
+  }
+  return DQMC_OK;
+#else
+  (void)clear;
+  return DQMC_ERR_UNSUPPORTED;
+#endif
+}
+
+dqmc_status dqmc_selftest_check(void* stream, int* fired, int* value) {
+  if (!fired || !value) return DQMC_ERR_ARG;
+  *fired = 0;
+  *value = -1;
+#ifdef DQMC_DEBUG
+  cudaStream_t st = (cudaStream_t)stream;
+  constexpr int n = 64;
+  double* x = nullptr;
+  if (cudaMalloc(&x, n * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return DQMC_ERR_NOMEM;
+  }
+  dqmc_status rc = DQMC_OK;
+  double hx[n];
+  unsigned long long w = 0;
+  if (cudaDeviceSynchronize() != cudaSuccess) rc = DQMC_ERR_CUDA;
+  if (rc == DQMC_OK && dqmc::check_word_api(true) == ~0ull) rc = DQMC_ERR_CUDA;
+  if (rc == DQMC_OK && cudaMemsetAsync(x, 0, n * sizeof(double), st) != cudaSuccess) rc = DQMC_ERR_CUDA;
+  if (rc == DQMC_OK) {
+    check_selftest_kernel<<<1, n, 0, st>>>(x, n, n - 1);
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(hx, x, sizeof hx, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      rc = DQMC_ERR_CUDA;
+  }
+  if (rc == DQMC_OK && (w = dqmc::check_word_api(true)) == ~0ull) rc = DQMC_ERR_CUDA;
+  if (rc == DQMC_OK) {
+    bool writes_ok = hx[n - 1] == 0.0;
+    for (int i = 0; i < n - 1; ++i) writes_ok = writes_ok && hx[i] == i + 1;
+    *fired = (w >> 63) && writes_ok ? 1 : 0;
+    *value = (int)(unsigned int)(w & 0xffffffffull);
+  }
+  cudaFree(x);
+  cudaGetLastError();
+  return rc;
+#else
+  (void)stream;
+  return DQMC_ERR_UNSUPPORTED;
+#endif
+}
+
+}  // extern "C"
+
+DQMC_CHECK_UNIT(api)

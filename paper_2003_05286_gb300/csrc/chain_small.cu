@@ -36,6 +36,12 @@ __global__ void __launch_bounds__(CS_NT, 1) chain_small_kernel(const ChainSmallA
   const double* X = a.X + (long long)b * a.sX;
   double* C = a.C + (long long)b * a.sC;
   const double* ev = a.expV + (long long)(b / a.divS) * a.sV + (long long)(b % a.divS) * a.sV_inner;
+  // launch contract (debug build): CS_NT threads, RPT rows per thread that
+  // cover N, column blocks that cover N, shared memory for E and two blocks
+  if (!DQMC_CHECK(blockDim.x == CS_NT && N <= 16 * RPT && (int)gridDim.x * CS_CB >= N, N) ||
+      !DQMC_CHECK(dyn_smem_bytes() >= (unsigned)(((long long)N * N + 2LL * N * CS_CB) * 8),
+                  dyn_smem_bytes()))
+    return;
   int nsl = a.nslices;
   if (a.lim) {                                 // slices past the instance's own chain end
     const int last = a.lim[b] - a.lim_base + 1;
@@ -127,3 +133,5 @@ cudaError_t chain_small(const ChainSmallArgs& a, cudaStream_t st) {
 }
 
 }  // namespace dqmc
+
+DQMC_CHECK_UNIT(chain_small)

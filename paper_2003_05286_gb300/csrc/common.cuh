@@ -258,3 +258,58 @@ int oz_groups(int s, int N);
 // waits run out and it ORs DQMC_STATUS_TIMEOUT into *status (device int).
 cudaError_t ozaki_selftest_timeout(int* status, cudaStream_t st);
 }  // namespace dqmc
+
+// ---------------------------------------------------------------------------
+// Device-side checks of the debug build (sources compiled with -DDQMC_DEBUG
+// into the separate debug library).
+//
+// DQMC_CHECK(cond, value) evaluates cond; when it is false it records
+// (source line, low 32 bits of value) in this translation unit's check word
+// (the first failure since the word was last cleared is kept) and yields
+// false, so the caller skips the access or leaves the kernel.  It never
+// traps.  In the release build it is the constant true and cond is not
+// evaluated, so the checks cost nothing there.  A device variable belongs to
+// the module of its translation unit (no relocatable device code), so every
+// unit has its own word; DQMC_CHECK_UNIT(name) at the end of a .cu file
+// defines the host reader dqmc::check_word_<name>, which the debug read-out
+// of api.cu calls for each unit.
+// ---------------------------------------------------------------------------
+namespace dqmc {
+// Bytes of dynamic shared memory the running kernel was launched with.
+__device__ __forceinline__ unsigned dyn_smem_bytes() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(r));
+  return r;
+}
+}  // namespace dqmc
+
+#ifdef DQMC_DEBUG
+namespace dqmc {
+static __device__ unsigned long long g_check_word;
+static __device__ __noinline__ void check_failed(int line, long long value) {
+  const unsigned long long w = (1ull << 63) | ((unsigned long long)(line & 0x7fffffff) << 32) |
+                               (unsigned long long)(unsigned int)value;
+  atomicCAS(&g_check_word, 0ull, w);
+}
+}  // namespace dqmc
+#define DQMC_CHECK(cond, value) \
+  ((cond) ? true : (::dqmc::check_failed(__LINE__, (long long)(value)), false))
+#define DQMC_CHECK_UNIT(name)                                                      \
+  namespace dqmc {                                                                 \
+  unsigned long long check_word_##name(bool clear) {                               \
+    unsigned long long w = 0;                                                      \
+    if (cudaMemcpyFromSymbol(&w, g_check_word, sizeof w) != cudaSuccess) {         \
+      cudaGetLastError();                                                          \
+      return ~0ull;                                                                \
+    }                                                                              \
+    if (clear && w) {                                                              \
+      const unsigned long long z = 0;                                              \
+      if (cudaMemcpyToSymbol(g_check_word, &z, sizeof z) != cudaSuccess) cudaGetLastError(); \
+    }                                                                              \
+    return w;                                                                      \
+  }                                                                                \
+  }
+#else
+#define DQMC_CHECK(cond, value) true
+#define DQMC_CHECK_UNIT(name)
+#endif

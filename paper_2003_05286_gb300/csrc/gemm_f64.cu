@@ -26,6 +26,12 @@ gemm_f64_kernel(const GemmArgs a) {
 
   __shared__ __align__(16) double As[2][BK][BM];
   __shared__ __align__(16) double Bs[2][BK][BN];
+  // launch contract (debug build): the thread mapping needs exactly NT
+  // threads, and every leading dimension must cover its row
+  if (!DQMC_CHECK(blockDim.x == NT, blockDim.x) ||
+      !DQMC_CHECK(a.lda >= (a.transA ? a.M : a.K) && a.ldb >= (a.transB ? a.K : a.N) &&
+                      a.ldc >= a.N, a.ldc))
+    return;
 
   for (int b = blockIdx.z; b < a.batch; b += gridDim.z) {
   if (b != (int)blockIdx.z) __syncthreads();   // shared tiles are reused across batch entries
@@ -81,6 +87,7 @@ gemm_f64_kernel(const GemmArgs a) {
       int gk = kb + k, gn = n0 + n;
       if (gk < a.K && gn < a.N) {
         int row = perm ? perm[gk] : gk;
+        if (!DQMC_CHECK(row >= 0 && row < a.K, row)) row = gk;   // a permutation of 0..K-1
         v = a.transB ? B[(long long)gn * a.ldb + row] : B[(long long)row * a.ldb + gn];
         if (ms) v *= ms[gk];
       }
@@ -220,3 +227,5 @@ cudaError_t gemm_f64(const GemmArgs& a, cudaStream_t st) {
 }
 
 }  // namespace dqmc
+
+DQMC_CHECK_UNIT(gemm)

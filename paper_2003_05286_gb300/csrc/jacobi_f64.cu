@@ -45,6 +45,9 @@ __global__ void __launch_bounds__(NT) jacobi_svd_kernel(const JacobiArgs a) {
   const int N = a.N, Np = N + (N & 1);
   const int tid = threadIdx.x, g = tid / TPP, l4 = tid % TPP;
   const double tol = N * 1.1102230246251565e-16;
+  // launch contract (debug build): four lanes for each of the Np / 2 pairs,
+  // singular values of at most 512 columns in shared memory
+  if (!DQMC_CHECK(blockDim.x == NT && TPP * (Np / 2) <= NT && N <= 512, N)) return;
 
   for (int b = blockIdx.x; b < a.batch; b += gridDim.x) {
     if (a.lim && a.lim[b] < a.lim_at) continue;   // chain of this instance already finished
@@ -170,3 +173,5 @@ cudaError_t jacobi_svd_f64(const JacobiArgs& a, cudaStream_t st) {
 }
 
 }  // namespace dqmc
+
+DQMC_CHECK_UNIT(jacobi)

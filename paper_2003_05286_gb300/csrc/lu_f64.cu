@@ -31,6 +31,16 @@ __global__ void __launch_bounds__(NT) lu_kernel(const LuArgs a) {
   __shared__ double s_lad;
 
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  // launch contract (debug build): NT threads, the pivot column held in
+  // RPT registers per thread, leading dimensions that cover their rows, and
+  // shared memory for the multipliers, the reciprocal pivots and, when
+  // resident, the augmented matrix
+  if (!DQMC_CHECK(blockDim.x == NT && N <= RPT * NT, N) ||
+      !DQMC_CHECK(a.Rdiag || a.ldr >= (a.transR ? N : nr), a.ldr) ||
+      !DQMC_CHECK(a.ldz >= (a.transZ ? N : nr), a.ldz) ||
+      !DQMC_CHECK(dyn_smem_bytes() >= (unsigned)(((a.smem_w ? (long long)N * Wd : 0) + 2LL * N) * 8),
+                  dyn_smem_bytes()))
+    return;
 
   for (int b = blockIdx.x; b < a.batch; b += gridDim.x) {
     const double* __restrict__ A = a.A + (long long)b * a.sA;
@@ -214,3 +224,5 @@ cudaError_t lu_solve_f64(const LuArgs& a0, cudaStream_t st) {
 }
 
 }  // namespace dqmc
+
+DQMC_CHECK_UNIT(lu)

@@ -242,6 +242,23 @@ ozaki_gemm_kernel(const __nv_bfloat16* __restrict__ As, long long sA, int P128,
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int n0 = blockIdx.x * OZ_BN, m0 = blockIdx.y * OZ_BM, b = blockIdx.z;
+  // launch contract (debug build), before any barrier or TMEM allocation:
+  // OZ_THREADS threads, 1..8 digits with their weight groups inside the
+  // allocated TMEM columns, shared memory up to the last flag word, and every
+  // bulk copy's source on a 16-byte boundary (tile bases, digit planes,
+  // instances)
+  if (!DQMC_CHECK(blockDim.x == OZ_THREADS && s >= 1 && s <= 8 &&
+                      pr.ngroups * OZ_BN <= (s > 4 ? 512 : 256),
+                  s) ||
+      !DQMC_CHECK(dyn_smem_bytes() >= (unsigned)((base - smem_raw) + data_bytes +
+                                                 (2 * OZ_STAGES + 1) * 8 + 12),
+                  dyn_smem_bytes()) ||
+      !DQMC_CHECK((reinterpret_cast<uintptr_t>(As) & 15) == 0 &&
+                      (reinterpret_cast<uintptr_t>(Bs) & 15) == 0 && (sA * 2) % 16 == 0 &&
+                      ((long long)P128 * nkb * OZ_BK * 2) % 16 == 0 &&
+                      ((long long)PN * nkb * OZ_BK * 2) % 16 == 0,
+                  sA))
+    return;
   // an instance whose (shorter) chain has already ended: copy its FP64 source
   // tile through when one is given, else leave the output alone.  The test
   // is uniform over the CTA and comes before any barrier or TMEM allocation.
@@ -352,6 +369,8 @@ ozaki_gemm_kernel(const __nv_bfloat16* __restrict__ As, long long sA, int P128,
             if (q0 + 3 < 0 || q0 > s - 1) continue;   // no digit of this block for pd
             // p = 0 reaches every block first: it starts the accumulation
             const uint32_t acc = (first_k && pd == 0) ? 0u : 1u;
+            // the four B tiles of this MMA lie inside the stage's B slots
+            if (!DQMC_CHECK(OZ_BZERO + q0 >= 0 && OZ_BZERO + q0 + 4 <= OZ_BSLOTS, q0)) continue;
             umma(tmem + (uint32_t)(4 * r) * OZ_BN, dAk + (uint64_t)(pd * (OZ_A_TILE >> 4)),
                  dBk + (uint64_t)((OZ_BZERO + q0) * (OZ_B_TILE >> 4)), idesc, acc);
           }
@@ -476,6 +495,11 @@ ozaki_split_kernel(const double* __restrict__ X, long long ldm, long long ldj, l
   const int b = blockIdx.y;
   const int j0 = blockIdx.x * 32;
   const int tid = threadIdx.x;
+  // launch contract (debug build): 256 threads, whole tiles, shared memory
+  // for the staged PM x 33 block
+  if (!DQMC_CHECK(blockDim.x == 256 && PM % 32 == 0 && R > 0 && PJ % R == 0, PM) ||
+      !DQMC_CHECK(dyn_smem_bytes() >= (unsigned)PM * 33u * 8u, dyn_smem_bytes()))
+    return;
   const double* Xb = X + (long long)b * sX;
   const double* scb = sc ? sc + (long long)b * ssc : nullptr;
   const int* gmb = gm ? gm + (long long)b * sgm : nullptr;
@@ -492,6 +516,8 @@ ozaki_split_kernel(const double* __restrict__ X, long long ldm, long long ldj, l
       for (int u = 0; u < 8; ++u) {
         const int m = mb + 8 * u;
         mr[u] = (m < N && j < N) ? (gmb ? gmb[m] : m) : -1;
+        // a gathered row must be a row of X (the pivot order of a QR)
+        if (gmb && m < N && j < N && !DQMC_CHECK(mr[u] >= 0 && mr[u] < N, mr[u])) mr[u] = -1;
       }
       double v[8];
 #pragma unroll
@@ -587,7 +613,10 @@ ozaki_split_kernel(const double* __restrict__ X, long long ldm, long long ldj, l
         }
         w[k >> 1] = small_int_bf16(d0) | (small_int_bf16(d1) << 16);
       }
-      *reinterpret_cast<uint4*>(Sb + q * plane + tile_off) = make_uint4(w[0], w[1], w[2], w[3]);
+      if (DQMC_CHECK(tile_off + 8 <= plane &&
+                         (reinterpret_cast<uintptr_t>(Sb + q * plane + tile_off) & 15) == 0,
+                     tile_off))
+        *reinterpret_cast<uint4*>(Sb + q * plane + tile_off) = make_uint4(w[0], w[1], w[2], w[3]);
     }
   }
 }
@@ -728,3 +757,5 @@ extern "C" dqmc_status dqmc_selftest_wait_timeout(void* stream, int* status) {
              ? DQMC_OK
              : DQMC_ERR_CUDA;
 }
+
+DQMC_CHECK_UNIT(ozaki)

@@ -186,6 +186,11 @@ __global__ void __launch_bounds__(NT) qrp_kernel(const QrpArgs a) {
 
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   constexpr int RPT = 4;   // rows below the diagonal per thread in the reflector pass (N <= 4 NT)
+  // launch contract (debug build): NT threads, rows of the reflector pass
+  // covered, the six double, one float and one int arrays of N in shared memory
+  if (!DQMC_CHECK(blockDim.x == NT && N <= RPT * NT, N) ||
+      !DQMC_CHECK(dyn_smem_bytes() >= (unsigned)N * 56u, dyn_smem_bytes()))
+    return;
 
   for (int b = blockIdx.x; b < a.batch; b += gridDim.x) {
     if (a.lim && a.lim[b] < a.lim_at) continue;   // chain of this instance already finished
@@ -523,6 +528,14 @@ __global__ void __launch_bounds__(NT) qrp_fused_kernel(const QrpArgs a) {
   __shared__ double s_red[5];                  // partial sums of the reflector step, alpha
 
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  // launch contract (debug build): NT threads, every column owned by one
+  // thread group, every row by one lane of the reflector warps, and shared
+  // memory for the resident matrices plus seven double, one float and one
+  // int array of N
+  if (!DQMC_CHECK(blockDim.x == NT && N <= NW * CPW && N <= 32 * NQ, N) ||
+      !DQMC_CHECK(dyn_smem_bytes() >= (unsigned)(a.smem_mats * NNs * 8 + 64LL * N),
+                  dyn_smem_bytes()))
+    return;
   const int rg = lane / CPW;                   // row group: rows r = rg (mod TPC)
   const int c = wid * CPW + lane % CPW;        // this thread's column
   const bool own = c < N;
@@ -832,3 +845,5 @@ cudaError_t qrp_f64(const QrpArgs& a, cudaStream_t st) {
 
 
 }  // namespace dqmc
+
+DQMC_CHECK_UNIT(qrp)

@@ -74,3 +74,47 @@ def test_fp64_rate_rejects_bad_arguments(lib):
     assert f(None, 0, 100, None, None) == 1                 # NULL result pointer
     assert f(None, 3, 100, ctypes.byref(tf), None) == 1     # unknown kind
     assert f(None, 0, 0, ctypes.byref(tf), None) == 1       # no iterations
+
+
+@pytest.fixture(scope="module")
+def dlib():
+    from paper_2003_05286_gb300 import build as b
+    b.build(debug=True)
+    return ctypes.CDLL(b.lib_path(debug=True))
+
+
+def test_debug_library_exports_the_same_calls(lib, dlib):
+    """The debug variant (-DDQMC_DEBUG) is the same C ABI: every declared
+    symbol, and it reports itself as the debug build."""
+    missing = [n for n in _declared() if not hasattr(dlib, n)]
+    assert not missing, missing
+    lib.dqmc_is_debug_build.restype = ctypes.c_int
+    dlib.dqmc_is_debug_build.restype = ctypes.c_int
+    assert lib.dqmc_is_debug_build() == 0 and dlib.dqmc_is_debug_build() == 1
+
+
+def test_debug_read_in_release_library(lib):
+    """Argument checks and the release answer come before any CUDA call."""
+    f = lib.dqmc_debug_read
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_int),
+                  ctypes.POINTER(ctypes.c_int)]
+    fn, ln, val = ctypes.c_char_p(), ctypes.c_int(), ctypes.c_int()
+    assert f(0, None, ctypes.byref(ln), ctypes.byref(val)) == 1
+    assert f(0, ctypes.byref(fn), ctypes.byref(ln), ctypes.byref(val)) == 7   # UNSUPPORTED
+    s = lib.dqmc_selftest_check
+    s.restype = ctypes.c_int
+    s.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    fired = ctypes.c_int()
+    assert s(None, None, ctypes.byref(val)) == 1
+    assert s(None, ctypes.byref(fired), ctypes.byref(val)) == 7
+
+
+def test_memory_limit_rejects_bad_arguments(lib):
+    f = lib.dqmc_set_memory_limit
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_void_p, ctypes.c_longlong]
+    assert f(None, 0) == 1
+    lib.dqmc_device_bytes.restype = ctypes.c_longlong
+    lib.dqmc_device_bytes.argtypes = [ctypes.c_void_p]
+    assert lib.dqmc_device_bytes(None) == -1

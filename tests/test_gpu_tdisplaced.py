@@ -6,6 +6,8 @@ B_1^{-1}...B_l^{-1} and the remainder B_M...B_{l+1}) through inv_sum_loh;
 the GPU takes both from one forward and one backward stack.  Same tolerance
 as the equal-time path: max|dG| <= 1e-10 * max(1, max|G|).
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -215,6 +217,39 @@ def test_g0t_full_size(dq):
             l = min(10 * j, 400)
             O = od.greens_displaced_back(x.K, 0.1, x.V, 10, 0, l)
             assert _cmp(G0t[b, j].cpu().numpy(), O) <= GTOL, (b, j)
+
+
+def test_g_tau0_ill_conditioned_vs_mpmath(dq):
+    """Instance 229 of the same batch, the ill-conditioned field: the library's
+    G(tau,0) at tau = 1, 5, 8 against stored mpmath values at 397 digits
+    (tests/golden/make_golden.py n64), within 16 * eps * cond(mid) of max|G|
+    (cond(mid) from the oracle, 7e5 to 4e6 here), the accuracy any FP64 route
+    of Eq. (inversion_tdgf_loh) has on this field; in the FP64 chain and,
+    since the field is the hard case for it, in the bf16x8 chain too."""
+    path = os.path.join(os.path.dirname(__file__), "golden", "batch_n64_229_displaced_mpmath.txt")
+    gold, cur = {}, None
+    for ln in open(path):
+        if ln.startswith("#"):
+            continue
+        parts = ln.split()
+        if len(parts) == 2:
+            cur = int(parts[1])
+            gold[cur] = []
+        else:
+            gold[cur].append(float(parts[0]))
+    assert sorted(gold) == [10, 50, 80]
+    x = di.batch_n64_tdisplaced(229)
+    eps = np.finfo(np.float64).eps
+    for prec in (0, 8):
+        h = dq.Handle(chain_precision=prec)
+        _, Gt0, st = dq.greens_tdisplaced(_dev(x.K), x.dtau, _dev(x.V), x.k, want_tt=False,
+                                          handle=h)
+        assert int(st) == 0
+        for l, vals in gold.items():
+            Gx = np.array(vals).reshape(64, 64)
+            kappa = od.displaced_condition(x.K, x.dtau, x.V, x.k, l, 0)
+            err = _cmp(Gt0[l // x.k].cpu().numpy(), Gx)
+            assert err <= 16.0 * eps * kappa, (prec, l, err, kappa)
 
 
 # ---------------------------------------------------------------------------

@@ -403,9 +403,9 @@ def test_time_translation():
             assert np.abs(G0 - R0).max() < 1e-12 * max(1.0, np.abs(R0).max()), (l0, d)
 
 
-def _golden_displaced():
+def _golden_displaced(name="single_n16_displaced_mpmath.txt", N=16):
     import os
-    path = os.path.join(os.path.dirname(__file__), "golden", "single_n16_displaced_mpmath.txt")
+    path = os.path.join(os.path.dirname(__file__), "golden", name)
     blocks, cur = {}, None
     for ln in open(path):
         if ln.startswith("#"):
@@ -416,7 +416,7 @@ def _golden_displaced():
             blocks[cur] = []
         else:
             blocks[cur].append(float(parts[0]))
-    return {key: np.array(v).reshape(16, 16) for key, v in blocks.items()}
+    return {key: np.array(v).reshape(N, N) for key, v in blocks.items()}
 
 
 def test_golden_displaced_n16():
@@ -430,3 +430,24 @@ def test_golden_displaced_n16():
         else:
             G = od.greens_displaced_back(inst.K, inst.dtau, inst.V, inst.k, 0, l)
         assert np.abs(G - Gx).max() < 1e-12 * max(1.0, np.abs(Gx).max()), (name, l)
+
+
+def test_golden_displaced_n64_ill_conditioned():
+    """Instance 229 of the 8x8, U=4, beta=40 batch, the ill-conditioned field
+    (|G(tau,0)| up to ~1e4): the oracle's G(tau,0) (Eq. (inversion_tdgf_loh))
+    against the stored mpmath values at tau = 1, 5, 8 (397 digits,
+    tests/golden/make_golden.py n64).  A backward-stable FP64 inversion of the
+    middle matrix resolves G only to about eps * cond(mid) of max|G|; the
+    oracle must stay within 16 times that, and the middle matrix must be as
+    ill-conditioned as the field suggests (cond > 1e5), so the pin exercises
+    that regime."""
+    x = di.batch_n64_tdisplaced(229)
+    gold = _golden_displaced("batch_n64_229_displaced_mpmath.txt", 64)
+    assert sorted(gold) == [("t0", 10), ("t0", 50), ("t0", 80)]
+    eps = np.finfo(np.float64).eps
+    for (_, l), Gx in gold.items():
+        G = od.greens_displaced(x.K, x.dtau, x.V, x.k, l, 0)
+        kappa = od.displaced_condition(x.K, x.dtau, x.V, x.k, l, 0)
+        scale = max(1.0, np.abs(Gx).max())
+        assert kappa > 1e5 and scale > 1e3, (l, kappa, scale)
+        assert np.abs(G - Gx).max() / scale <= 16.0 * eps * kappa, l
