@@ -24,28 +24,28 @@ __global__ void __launch_bounds__(NT) lu_kernel(const LuArgs a) {
   double* smW = reinterpret_cast<double*>(smem_raw);
   double* lbuf = smW + (a.smem_w ? (long long)N * Wd : 0);   // multipliers of the current column
   double* dinv = lbuf + N;                              // 1 / u_jj
+  double* apiv = dinv + N;                              // |u_jj|: log det is summed at the end
   __shared__ unsigned long long sk[32];
   __shared__ int si[32];
   __shared__ double sv[32];
   __shared__ int s_flag, s_sign;
-  __shared__ double s_lad;
 
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   // launch contract (debug build): NT threads, the pivot column held in
   // RPT registers per thread, leading dimensions that cover their rows, and
-  // shared memory for the multipliers, the reciprocal pivots and, when
-  // resident, the augmented matrix
+  // shared memory for the multipliers, the reciprocal and absolute pivots
+  // and, when resident, the augmented matrix
   if (!DQMC_CHECK(blockDim.x == NT && N <= RPT * NT, N) ||
       !DQMC_CHECK(a.Rdiag || a.ldr >= (a.transR ? N : nr), a.ldr) ||
       !DQMC_CHECK(a.ldz >= (a.transZ ? N : nr), a.ldz) ||
-      !DQMC_CHECK(dyn_smem_bytes() >= (unsigned)(((a.smem_w ? (long long)N * Wd : 0) + 2LL * N) * 8),
+      !DQMC_CHECK(dyn_smem_bytes() >= (unsigned)(((a.smem_w ? (long long)N * Wd : 0) + 3LL * N) * 8),
                   dyn_smem_bytes()))
     return;
 
   for (int b = blockIdx.x; b < a.batch; b += gridDim.x) {
     const double* __restrict__ A = a.A + (long long)b * a.sA;
     double* __restrict__ W = a.smem_w ? smW : a.W + (long long)b * a.sW;
-    if (tid == 0) { s_flag = 0; s_sign = 1; s_lad = 0.0; }
+    if (tid == 0) { s_flag = 0; s_sign = 1; }
 
     // ---- load [opA(A) | opR(R)] ------------------------------------------
     for (long long e = tid; e < (long long)N * N; e += NT) {
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(NT) lu_kernel(const LuArgs a) {
         if (piv == 0.0) s_flag |= DQMC_STATUS_SINGULAR;
         if (p != j) s_sign = -s_sign;
         if (piv < 0.0) s_sign = -s_sign;
-        s_lad += log(fabs(piv));
+        apiv[j] = fabs(piv);
         dinv[j] = inv;
       }
       __syncthreads();
@@ -181,6 +181,16 @@ __global__ void __launch_bounds__(NT) lu_kernel(const LuArgs a) {
         col[(long long)i * Wd] = ((s0 + s1) + (s2 + s3)) * dinv[i];
       }
     }
+    // log|det| = sum_j log|u_jj|, taken here rather than once per elimination
+    // step on its critical path: strided partial sums per thread, then a
+    // fixed-order reduction (lane 0 of each warp, warps in order)
+    if (a.logabsdet) {
+      double ls = 0.0;
+      for (int jj = tid; jj < N; jj += NT) ls += log(apiv[jj]);
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) ls += __shfl_xor_sync(0xffffffffu, ls, off);
+      if (lane == 0) sv[wid] = ls;
+    }
     __syncthreads();
     for (long long e = tid; e < (long long)N * nr; e += NT) {
       if (!a.transZ) {
@@ -192,7 +202,11 @@ __global__ void __launch_bounds__(NT) lu_kernel(const LuArgs a) {
       }
     }
     if (tid == 0) {
-      if (a.logabsdet) a.logabsdet[b] = s_lad;
+      if (a.logabsdet) {
+        double lad = 0.0;
+        for (int w = 0; w < NT / 32; ++w) lad += sv[w];
+        a.logabsdet[b] = lad;
+      }
       if (a.sign) a.sign[b] = s_sign;
       if (s_flag && a.status) atomicOr(&a.status[b / a.status_div], s_flag);
     }
@@ -203,7 +217,7 @@ __global__ void __launch_bounds__(NT) lu_kernel(const LuArgs a) {
 cudaError_t lu_solve_f64(const LuArgs& a0, cudaStream_t st) {
   if (a0.batch <= 0 || a0.N <= 0) return cudaSuccess;
   LuArgs a = a0;
-  size_t sm = (size_t)a.N * 2 * sizeof(double) + 16;
+  size_t sm = (size_t)a.N * 3 * sizeof(double) + 16;
   // the augmented matrix in shared memory when it fits (227 KB per CTA): every
   // elimination step reads and updates the trailing block
   const size_t wb = (size_t)a.N * (a.N + a.nrhs) * sizeof(double);

@@ -791,6 +791,278 @@ __global__ void __launch_bounds__(NT) qrp_fused_kernel(const QrpArgs a) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// qrp_small_kernel<TPC>: the same factorisation for N <= 128 / TPC (16 with
+// TPC = 8, 32 with TPC = 4), one CTA of four warps per instance, two barriers
+// per pivot step.
+//
+// A single small instance is latency-bound, and on GB300 every FP64 warp
+// instruction holds its sub-partition's pipe for 64 cycles, so the design
+// keeps the serial part of a step short and spreads the rest over the four
+// warps (one per sub-partition):
+//   * TPC lanes own one column (rows rg + TPC k in registers); a warp owns
+//     32 / TPC columns.
+//   * Columns are never moved: the pivot order is recorded and applied when
+//     T is written, so no column data crosses warps.
+//   * The vote: each warp reduces the keys of its columns by shuffles and
+//     posts its winner; after a barrier every thread picks the same winner
+//     from the four (ties -> lowest column, as in the kernels above;
+//     non-finite keys count as -inf).
+//   * The reflector: only the warp that owns the pivot column works; it
+//     writes H_j = 1 - gamma u u^T in unnormalised form, u_j = alpha - beta,
+//     u_r = a_rP below j, gamma = 1 / (beta (beta - alpha)) (one square root
+//     and one division on the critical path, where v = u / u_j and
+//     tau = gamma u_j^2 of the kernels above take two) to shared memory, and
+//     a barrier publishes it.
+//   * Every column not yet pivoted applies H_j and downdates its norm (the
+//     xLAQP2 safeguard as above), then votes again.
+// Q = H_0 ... H_{N-1} is accumulated backwards without barriers: each column
+// group transforms its own column of Q.  Results agree with the other
+// kernels to rounding; sums run in a different order.
+// ---------------------------------------------------------------------------
+template <int I>
+struct RowIdx {
+  static constexpr int value = I;
+};
+
+// f(RowIdx<k>{}) for k = k0 .. NK-1 (k0 warp-uniform): the rows below k0 are
+// skipped by a jump, not predicated, because a predicated FP64 warp
+// instruction still holds the pipe for 64 cycles
+template <int NK, class F>
+__device__ __forceinline__ void ks_from(int k0, F&& f) {
+  static_assert(NK >= 1 && NK <= 8, "at most 8 rows per lane");
+  if constexpr (NK <= 2) {
+    if (k0 <= 0) f(RowIdx<0>{});
+    if constexpr (NK > 1) if (k0 <= 1) f(RowIdx<1>{});
+    return;
+  }
+  switch (k0) {
+    case 0: f(RowIdx<0>{}); [[fallthrough]];
+    case 1: if constexpr (NK > 1) f(RowIdx<1>{}); [[fallthrough]];
+    case 2: if constexpr (NK > 2) f(RowIdx<2>{}); [[fallthrough]];
+    case 3: if constexpr (NK > 3) f(RowIdx<3>{}); [[fallthrough]];
+    case 4: if constexpr (NK > 4) f(RowIdx<4>{}); [[fallthrough]];
+    case 5: if constexpr (NK > 5) f(RowIdx<5>{}); [[fallthrough]];
+    case 6: if constexpr (NK > 6) f(RowIdx<6>{}); [[fallthrough]];
+    case 7: if constexpr (NK > 7) f(RowIdx<7>{}); [[fallthrough]];
+    default: break;
+  }
+}
+
+// sum over the TPC lanes of a column group; every lane gets the same value
+// (each butterfly level adds the same two partial sums on both sides)
+template <int TPC>
+__device__ __forceinline__ double col_group_sum(double v) {
+#pragma unroll
+  for (int off = 1; off < TPC; off <<= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
+template <int TPC>
+__global__ void __launch_bounds__(128) qrp_small_kernel(const QrpArgs a) {
+  constexpr int NT = 128, NW = 4, CPW = 32 / TPC, NMAX = NW * CPW, RPL = NMAX / TPC;
+  static_assert(RPL >= 1 && RPL <= 8 && RPL * TPC == NMAX && NT == 32 * NW, "thread mapping");
+  __shared__ double s_u[NMAX][NMAX];    // u of step j at rows >= j
+  __shared__ double s_gam[NMAX], s_beta[NMAX], s_dsc[NMAX], s_rinv[NMAX], s_dinv[NMAX];
+  __shared__ int s_piv[NMAX];
+  __shared__ float s_key[NW];
+  __shared__ int s_idx[NW];
+  __shared__ int s_flag;
+  const int N = a.N;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int cw = lane / TPC, rg = lane % TPC;
+  const int c = wid * CPW + cw;          // this lane's column
+  const int gbase = lane & ~(TPC - 1);   // first lane of its column group
+  const bool own = c < N;
+  const unsigned FULL = 0xffffffffu;
+  // launch contract (debug build): 128 threads, N columns covered
+  if (!DQMC_CHECK(blockDim.x == NT && N >= 1 && N <= NMAX, N)) return;
+
+  for (int b = blockIdx.x; b < a.batch; b += gridDim.x) {
+    if (a.lim && a.lim[b] < a.lim_at) continue;   // chain of this instance already finished
+    const double* __restrict__ A = a.A + (long long)b * a.sA;
+    double* __restrict__ Uout = a.U + (long long)b * a.sU;
+    double* __restrict__ Dout = a.D + (long long)b * a.sD;
+    double* __restrict__ T = a.T + (long long)b * a.sT;
+    int* __restrict__ pout = a.perm + (long long)b * a.sperm;
+    const double* Din = a.Din ? a.Din + (long long)b * a.sDin : nullptr;
+
+    if (tid == 0) s_flag = 0;
+    int flag = 0;
+    double x[RPL];
+#pragma unroll
+    for (int k = 0; k < RPL; ++k) {
+      const int r = rg + TPC * k;
+      x[k] = (own && r < N) ? A[(long long)r * N + c] : 0.0;
+      if (!isfinite(x[k])) flag |= DQMC_STATUS_NONFINITE_SCALE;
+    }
+    const double dsc = (own && Din) ? Din[c] : 1.0;
+    if (!(isfinite(dsc) && dsc >= 0.0)) flag |= DQMC_STATUS_NONFINITE_SCALE;
+    const float logd = own ? log2_wide(dsc) : -INFINITY;
+    double nrm2 = 0.0;
+#pragma unroll
+    for (int k = 0; k < RPL; ++k) nrm2 = fma(x[k], x[k], nrm2);
+    nrm2 = col_group_sum<TPC>(nrm2);
+    double ref2 = nrm2;
+    bool done = !own;      // column already pivoted (or not a column)
+    int mystep = 0;        // position of this column in the pivot order
+    __syncthreads();       // s_flag cleared; the previous instance's reads are over
+
+    for (int j = 0; j < N; ++j) {
+      const int k0 = j / TPC;   // rows with k < k0 lie above j
+      // ---- vote ----------------------------------------------------------
+      float key = done ? -INFINITY : logd + 0.5f * log2_wide(nrm2);
+      if (!(key == key)) key = -INFINITY;
+      int idx = done ? 0x7fffffff : c;
+#pragma unroll
+      for (int off = TPC; off < 32; off <<= 1) {
+        const float k2 = __shfl_xor_sync(FULL, key, off);
+        const int i2 = __shfl_xor_sync(FULL, idx, off);
+        if (k2 > key || (k2 == key && i2 < idx)) { key = k2; idx = i2; }
+      }
+      if (lane == 0) { s_key[wid] = key; s_idx[wid] = idx; }
+      __syncthreads();
+      key = s_key[0];
+      idx = s_idx[0];
+#pragma unroll
+      for (int w = 1; w < NW; ++w)
+        if (s_key[w] > key || (s_key[w] == key && s_idx[w] < idx)) { key = s_key[w]; idx = s_idx[w]; }
+      const int P = DQMC_CHECK(idx >= 0 && idx < N, idx) ? idx : 0;
+      const bool mine = c == P;
+      // ---- reflector of column P at rows >= j (the owning warp only) ---------
+      if (wid == P / CPW) {
+        double sp = 0.0, xjv = 0.0;
+        ks_from<RPL>(k0, [&](auto K) {
+          constexpr int k = decltype(K)::value;
+          const int r = rg + TPC * k;
+          const double t = r > j ? x[k] : 0.0;
+          sp = fma(t, t, sp);
+          xjv = r == j ? x[k] : xjv;
+        });
+        const double sig = col_group_sum<TPC>(sp);
+        const double alpha = __shfl_sync(FULL, xjv, gbase | (j % TPC));
+        double beta = alpha, gam = 0.0, uj = 0.0;
+        if (sig > 0.0) {
+          const double nrm = sqrt(fma(alpha, alpha, sig));
+          beta = alpha >= 0.0 ? -nrm : nrm;
+          uj = alpha - beta;
+          gam = 1.0 / (beta * (beta - alpha));
+        }
+        if (mine) {
+          ks_from<RPL>(k0, [&](auto K) {
+            constexpr int k = decltype(K)::value;
+            const int r = rg + TPC * k;
+            if (r >= j && r < N) s_u[j][r] = r == j ? uj : x[k];
+            if (r == j) x[k] = beta;              // r_jj of R
+          });
+          if (rg == 0) { s_gam[j] = gam; s_beta[j] = beta; s_dsc[j] = dsc; s_piv[j] = P; }
+        }
+      }
+      if (mine) { done = true; mystep = j; }
+      __syncthreads();
+      // ---- apply H_j to the columns not yet pivoted, downdate their norms -----
+      {
+        const double gam = s_gam[j];
+        double ur[RPL], pp = 0.0;
+#pragma unroll
+        for (int k = 0; k < RPL; ++k) ur[k] = 0.0;
+        ks_from<RPL>(k0, [&](auto K) {
+          constexpr int k = decltype(K)::value;
+          const int r = rg + TPC * k;
+          ur[k] = (r >= j && r < N) ? s_u[j][r] : 0.0;
+          pp = fma(ur[k], x[k], pp);
+        });
+        // the group sum is a full-warp shuffle: every lane takes part, pivoted
+        // columns included, before the result is discarded for them
+        const double dsum = col_group_sum<TPC>(pp);
+        const double w = done ? 0.0 : gam * dsum;
+        double xjv = 0.0;
+        ks_from<RPL>(k0, [&](auto K) {
+          constexpr int k = decltype(K)::value;
+          if (!done) x[k] = fma(-ur[k], w, x[k]);
+          xjv = rg + TPC * k == j ? x[k] : xjv;
+        });
+        const double rjc = __shfl_sync(FULL, xjv, gbase | (j % TPC));   // updated a_jc
+        double n2 = fma(-rjc, rjc, nrm2);
+        const bool redo = !done && n2 <= 1.4901161193847656e-8 * ref2;
+        if (__any_sync(FULL, redo)) {
+          double ex = 0.0;
+          ks_from<RPL>(k0, [&](auto K) {
+            constexpr int k = decltype(K)::value;
+            const double t = rg + TPC * k > j ? x[k] : 0.0;
+            ex = fma(t, t, ex);
+          });
+          ex = col_group_sum<TPC>(ex);
+          if (redo) n2 = ex;
+        }
+        if (!done) {
+          nrm2 = n2;
+          if (redo) ref2 = n2;
+        }
+      }
+    }
+
+    // ---- Q = H_0 ... H_{N-1} on the identity, backwards, column by column ----
+    double q[RPL];
+#pragma unroll
+    for (int k = 0; k < RPL; ++k) q[k] = rg + TPC * k == c ? 1.0 : 0.0;
+    for (int j = N - 1; j >= 0; --j) {
+      const int k0 = j / TPC;
+      const double gam = s_gam[j];
+      double ur[RPL], pp = 0.0;
+#pragma unroll
+      for (int k = 0; k < RPL; ++k) ur[k] = 0.0;
+      ks_from<RPL>(k0, [&](auto K) {
+        constexpr int k = decltype(K)::value;
+        const int r = rg + TPC * k;
+        ur[k] = (r >= j && r < N) ? s_u[j][r] : 0.0;
+        pp = fma(ur[k], q[k], pp);
+      });
+      const double w = gam * col_group_sum<TPC>(pp);
+      ks_from<RPL>(k0, [&](auto K) {
+        constexpr int k = decltype(K)::value;
+        q[k] = fma(-ur[k], w, q[k]);
+      });
+    }
+
+    // ---- outputs: D_i = |r_ii| Din_{p_i}, perm, T = D^{-1} R in pivot order, U ----
+    if (tid < N) {
+      const double ri = fabs(s_beta[tid]);
+      const double d = ri * s_dsc[tid];
+      if (!(d > 0.0)) flag |= DQMC_STATUS_SINGULAR;
+      if (!isfinite(d)) flag |= DQMC_STATUS_NONFINITE_SCALE;
+      Dout[tid] = d;
+      pout[tid] = s_piv[tid];
+      s_rinv[tid] = ri > 0.0 ? 1.0 / ri : 0.0;
+      s_dinv[tid] = s_dsc[tid] > 0.0 ? 1.0 / s_dsc[tid] : 0.0;
+    }
+    flag = __reduce_or_sync(FULL, flag);
+    if (lane == 0 && flag) atomicOr(&s_flag, flag);
+    __syncthreads();
+    if (own) {
+#pragma unroll
+      for (int k = 0; k < RPL; ++k) {
+        const int i = rg + TPC * k;
+        if (i < N) {
+          // this column is column mystep of R: rows above mystep hold R, row
+          // mystep holds r_jj, the rows below are not part of R
+          T[(long long)i * N + mystep] = i <= mystep ? x[k] * s_rinv[i] * (dsc * s_dinv[i]) : 0.0;
+          Uout[(long long)i * N + c] = q[k];
+        }
+      }
+    }
+    __syncthreads();
+    if (tid == 0 && s_flag && a.status) atomicOr(&a.status[b / a.status_div], s_flag);
+  }
+}
+
+template <int TPC>
+static cudaError_t launch_qrp_small(const QrpArgs& a, cudaStream_t st) {
+  const int grid = a.batch < (1 << 30) ? a.batch : (1 << 30);
+  qrp_small_kernel<TPC><<<grid, 128, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
 static size_t qrp_fused_smem(int N) {
   return (size_t)N * (7 * sizeof(double) + sizeof(float) + sizeof(int)) + 16;
 }
@@ -820,11 +1092,9 @@ static size_t qrp_smem(int N) { return (size_t)N * (6 * sizeof(double) + sizeof(
 
 cudaError_t qrp_f64(const QrpArgs& a, cudaStream_t st) {
   if (a.batch <= 0 || a.N <= 0) return cudaSuccess;
-  // N <= 32: four warps, so that the per-step FP64 work of every column
-  // spreads over all four sub-partitions (two threads per column would put
-  // all columns of N <= 16 in one warp)
-  if (a.N <= 16) return launch_qrp_fused<128, 8, 1>(a, st);
-  if (a.N <= 32) return launch_qrp_fused<128, 4, 1>(a, st);
+  // N <= 32: four warps, two barriers per pivot step (qrp_small_kernel)
+  if (a.N <= 16) return launch_qrp_small<8>(a, st);
+  if (a.N <= 32) return launch_qrp_small<4>(a, st);
   if (a.N <= 64) return launch_qrp_fused<128, 2, 2>(a, st);
   if (a.N <= 128) return launch_qrp_fused<256, 2, 4>(a, st);
   if (a.N <= 256) return launch_qrp_fused<512, 2, 8>(a, st);

@@ -108,7 +108,7 @@ def test_debug_build_checks_pass_and_match_release(dq, tmp_path):
     code = ("import sys; sys.path.insert(0, %r); import test_gpu_debug_build as t; t._child(%r)"
             % (os.path.dirname(os.path.abspath(__file__)), path))
     r = subprocess.run([sys.executable, "-c", code], env=env, cwd=ROOT, capture_output=True,
-                       text=True, timeout=600)
+                       text=True, timeout=300)
     assert r.returncode == 0, r.stdout[-3000:] + r.stderr[-3000:]
     res = torch.load(path)
     assert res["fired"] and res["value"] == 63, (res["fired"], res["value"])
