@@ -836,7 +836,8 @@ def measure_other(args, wl, rank, world, peak=None):
     if name == "ragged_1024":
         from paper_2003_05286_gb300 import tune
         insts0 = [di.ragged_params(rank * batch + i) for i in range(batch)]
-        # k per lattice size: tuned on 4 instances at the largest beta of the group
+        # k per lattice size: tuned on 4 instances at the largest beta of the
+        # group, timed with the sequential fold the full ragged batch runs
         kbyL = {}
         for L in sorted({p[0] for p in insts0}):
             idx = [i for i, p in enumerate(insts0) if p[0] == L]
@@ -845,7 +846,8 @@ def measure_other(args, wl, rank, world, peak=None):
             Mmin = min(x.M for x in sample)
             Ks = torch.tensor(sample[0].K, device=dev)
             Vs = torch.tensor(np.stack([x.V[:Mmin] for x in sample]), device=dev)
-            best, _ = tune.tune(Ks, 0.1, Vs, candidates=(5, 10, 15, 20), tiles=(0,), ref_k=2, tol=1e-10)
+            best, _ = tune.tune(Ks, 0.1, Vs, candidates=(5, 10, 15, 20), tiles=(0,), ref_k=2, tol=1e-10,
+                                fold=dq._abi.FOLD_SEQUENTIAL)
             kbyL[L] = best["k"]
         insts = [di.ragged_instance(rank * batch + i, kbyL[p[0]]) for i, p in enumerate(insts0)]
         extra["k_by_L"] = kbyL

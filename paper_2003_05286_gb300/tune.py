@@ -43,14 +43,17 @@ def _time_ms(fn, reps):
 
 def tune(K: torch.Tensor, dtau: float, V: torch.Tensor, *, candidates=(5, 8, 10, 12, 15, 20),
          tiles=(0, 32, 48, 64), ref_k: int = 2, tol: float = 1e-10, chain_precision: int = 0,
-         reps: int = 2, cache_file: str | None = None, tag: str = ""):
+         reps: int = 2, cache_file: str | None = None, tag: str = "", fold: int | None = None):
     """Pick (k, tile) for fields shaped like V (B, M, N).
 
     Returns (best, table): best = dict(k, tile, err, ms); table = every
-    candidate tried.  tile 0 lets the library choose by size."""
+    candidate tried.  tile 0 lets the library choose by size.  ``fold`` is the
+    chain fold the timed candidates use (dqmc_set_chain_fold; None: the
+    library's choice for the sample's own size): a small sample of a large
+    batch should be timed with the fold the large batch will run."""
     V3 = V if V.dim() == 3 else V.unsqueeze(0)
     B, M, N = V3.shape
-    key = _key(N, M, dtau, chain_precision, tag)
+    key = _key(N, M, dtau, chain_precision, tag + ("" if fold is None else f"-f{fold}"))
     if cache_file and not _CACHE and os.path.exists(cache_file):
         with open(cache_file) as f:
             _CACHE.update(json.load(f))
@@ -61,7 +64,8 @@ def tune(K: torch.Tensor, dtau: float, V: torch.Tensor, *, candidates=(5, 8, 10,
     scale = float(Gref.abs().max().clamp(min=1.0))
     table = []
     for tile in tiles:
-        h = Handle(chain_precision=chain_precision)
+        h = Handle(chain_precision=chain_precision) if fold is None else \
+            Handle(chain_precision=chain_precision, fold=fold)
         h.set_gemm_tile(tile)
         for k in candidates:
             if k > M:
