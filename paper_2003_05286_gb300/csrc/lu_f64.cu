@@ -9,7 +9,8 @@
 // rank-1 update streams rows that are contiguous across the threads of a
 // warp.  Back substitution then runs without any synchronisation: each
 // right-hand-side column belongs to one thread.  log|det| and the sign of
-// det(opA(A)) come out of the pivots.
+// det(opA(A)) come out of the pivots.  Systems with N <= 32 and N + nrhs <= 64
+// take lu_small_kernel below (the columns in registers, one barrier per step).
 #include "common.cuh"
 
 namespace dqmc {
@@ -214,8 +215,210 @@ __global__ void __launch_bounds__(NT) lu_kernel(const LuArgs a) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// lu_small_kernel<NW, RPL>: the same solve for N <= 4 RPL and N + nrhs <= 8 NW
+// (NW warps), one barrier per elimination step.
+//
+// For a small system the kernel above is latency-bound: three barriers per
+// column, and with one thread per column at most one warp does the update.
+// Here four lanes own one column of [opA(A) | opR(R)] (rows rg + 4 k in
+// registers).  At step j the warp owning column j finds the pivot (largest
+// |a_rj|, lowest row on ties, as above), forms the multipliers with the one
+// division of the step and posts them; after the barrier every other column
+// swaps rows j and p and eliminates below j in registers.  U then goes to
+// shared memory and each right-hand-side column solves U z = y on its own
+// (column-oriented substitution with the reciprocal pivots).  log|det| is
+// summed at the end, the sign follows the swaps and the pivot signs.
+// ---------------------------------------------------------------------------
+template <int NW, int RPL>
+__global__ void __launch_bounds__(32 * NW) lu_small_kernel(const LuArgs a) {
+  constexpr int TPC = 4, CPW = 32 / TPC, WMAX = NW * CPW, NMAX = TPC * RPL;
+  static_assert(WMAX >= NMAX, "the columns of A fit the warps");
+  __shared__ double s_l[NMAX][NMAX];   // multipliers of step j at rows > j
+  __shared__ double s_u[NMAX][NMAX];   // U, row-major, after the elimination
+  __shared__ double s_inv[NMAX], s_apv[NMAX], s_ls[NW];
+  __shared__ int s_p[NMAX];
+  __shared__ int s_flag, s_sign;
+  const int N = a.N, nr = a.nrhs, Wd = N + nr;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int cw = lane / TPC, rg = lane % TPC, gbase = lane & ~(TPC - 1);
+  const int c = wid * CPW + cw;         // this lane's column of the augmented matrix
+  const bool own = c < Wd;
+  const unsigned FULL = 0xffffffffu;
+  // launch contract (debug build): NW warps covering the columns, RPL rows
+  // per lane covering N, leading dimensions that cover their rows
+  if (!DQMC_CHECK(blockDim.x == 32 * NW && N >= 1 && N <= NMAX && Wd <= WMAX, Wd) ||
+      !DQMC_CHECK(a.Rdiag || a.ldr >= (a.transR ? N : nr), a.ldr) ||
+      !DQMC_CHECK(a.ldz >= (a.transZ ? N : nr), a.ldz))
+    return;
+
+  for (int b = blockIdx.x; b < a.batch; b += gridDim.x) {
+    const double* __restrict__ A = a.A + (long long)b * a.sA;
+    double* __restrict__ Z = a.Z + (long long)b * a.sZ;
+    if (tid == 0) { s_flag = 0; s_sign = 1; }
+    double x[RPL];
+#pragma unroll
+    for (int k = 0; k < RPL; ++k) {
+      const int r = rg + TPC * k;
+      double v = 0.0;
+      if (own && r < N) {
+        if (c < N) {
+          v = a.transA ? A[(long long)c * N + r] : A[(long long)r * N + c];
+        } else if (a.Rdiag) {
+          const double* Rd = a.Rdiag + (long long)b * a.sRdiag;
+          if (r == c - N) v = a.invRdiag ? 1.0 / Rd[r] : Rd[r];
+        } else {
+          const double* R = a.R + (long long)b * a.sR;
+          const int cc = c - N;
+          v = a.transR ? R[(long long)cc * a.ldr + r] : R[(long long)r * a.ldr + cc];
+        }
+      }
+      x[k] = v;
+    }
+    __syncthreads();   // s_flag, s_sign set; the previous instance's reads are over
+
+    for (int j = 0; j < N; ++j) {
+      const int k0 = j / TPC;   // rows with k < k0 lie above j
+      if (wid == j / CPW) {
+        // ---- pivot of column j (its four lanes; the rest of the warp idles)
+        const bool mine = c == j;
+        unsigned long long key = 0ull;   // |a_rj| bits, ordered like the values
+        int idx = 0x7fffffff;
+        double val = 0.0, ajj = 0.0;
+#pragma unroll
+        for (int k = 0; k < RPL; ++k) {
+          const int r = rg + TPC * k;
+          if (mine && r >= j && r < N) {
+            const unsigned long long k2 =
+                (unsigned long long)__double_as_longlong(x[k]) & 0x7fffffffffffffffull;
+            if (k2 > key || (k2 == key && r < idx)) { key = k2; idx = r; val = x[k]; }
+          }
+          ajj = r == j ? x[k] : ajj;
+        }
+#pragma unroll
+        for (int off = 1; off < TPC; off <<= 1) {
+          const unsigned long long k2 = __shfl_xor_sync(FULL, key, off);
+          const int i2 = __shfl_xor_sync(FULL, idx, off);
+          const double v2 = __shfl_xor_sync(FULL, val, off);
+          if (k2 > key || (k2 == key && i2 < idx)) { key = k2; idx = i2; val = v2; }
+        }
+        ajj = __shfl_sync(FULL, ajj, gbase | (j % TPC));
+        // only the lanes of column j hold a candidate
+        const int p = (idx >= j && idx < N) ? idx : j;
+        if (mine) (void)DQMC_CHECK(idx >= j && idx < N, idx);
+        const double piv = p == j ? ajj : val;
+        const double inv = piv != 0.0 ? 1.0 / piv : 0.0;
+        if (mine) {
+          // multipliers of rows r > j after the swap (row p then holds the old row j)
+          ks_from<RPL>(k0, [&](auto K) {
+            constexpr int k = decltype(K)::value;
+            const int r = rg + TPC * k;
+            if (r > j && r < N) s_l[j][r] = (r == p ? ajj : x[k]) * inv;
+            if (r == j) x[k] = piv;   // u_jj; the rest of column j is not needed
+          });
+          if (rg == 0) {
+            s_p[j] = p;
+            s_inv[j] = inv;
+            s_apv[j] = fabs(piv);
+            if (piv == 0.0) s_flag |= DQMC_STATUS_SINGULAR;
+            if ((p != j) != (piv < 0.0)) s_sign = -s_sign;
+          }
+        }
+      }
+      __syncthreads();
+      // ---- columns c > j: swap rows j and p, eliminate below j -----------------
+      const int p = s_p[j];
+      double vj = 0.0, vp = 0.0;
+#pragma unroll
+      for (int k = 0; k < RPL; ++k) {
+        const int r = rg + TPC * k;
+        vj = r == j ? x[k] : vj;
+        vp = r == p ? x[k] : vp;
+      }
+      vj = __shfl_sync(FULL, vj, gbase | (j % TPC));   // old a_jc
+      vp = __shfl_sync(FULL, vp, gbase | (p % TPC));   // old a_pc: row j after the swap
+      if (own && c > j) {
+        ks_from<RPL>(k0, [&](auto K) {
+          constexpr int k = decltype(K)::value;
+          const int r = rg + TPC * k;
+          double y = r == p ? vj : x[k];
+          if (r == j) y = vp;
+          else if (r > j && r < N) y = fma(-s_l[j][r], vp, y);
+          x[k] = y;
+        });
+      }
+    }
+    // ---- U to shared memory, then z_m = y_m / u_mm, y_r -= u_rm z_m (r < m) -----
+    if (own && c < N) {
+#pragma unroll
+      for (int k = 0; k < RPL; ++k) {
+        const int r = rg + TPC * k;
+        if (r <= c) s_u[r][c] = x[k];
+      }
+    }
+    __syncthreads();
+    // every lane runs the substitution (its shuffles need the whole warp); only
+    // the right-hand-side columns keep the result
+    for (int m = N - 1; m >= 0; --m) {
+      double ym = 0.0;
+#pragma unroll
+      for (int k = 0; k < RPL; ++k) ym = rg + TPC * k == m ? x[k] : ym;
+      const double zm = __shfl_sync(FULL, ym, gbase | (m % TPC)) * s_inv[m];
+#pragma unroll
+      for (int k = 0; k < RPL; ++k) {
+        const int r = rg + TPC * k;
+        if (r == m) x[k] = zm;
+        else if (r < m) x[k] = fma(-s_u[r][m], zm, x[k]);
+      }
+    }
+    if (own && c >= N) {
+      const int cc = c - N;
+#pragma unroll
+      for (int k = 0; k < RPL; ++k) {
+        const int r = rg + TPC * k;
+        if (r < N) {
+          if (a.transZ) Z[(long long)cc * a.ldz + r] = x[k];
+          else Z[(long long)r * a.ldz + cc] = x[k];
+        }
+      }
+    }
+    // log|det| = sum of log|u_jj| in a fixed order (lane 0 of each warp, warps in order)
+    if (a.logabsdet) {
+      double ls = 0.0;
+      for (int jj = tid; jj < N; jj += 32 * NW) ls += log(s_apv[jj]);
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) ls += __shfl_xor_sync(FULL, ls, off);
+      if (lane == 0) s_ls[wid] = ls;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      if (a.logabsdet) {
+        double lad = 0.0;
+        for (int w = 0; w < NW; ++w) lad += s_ls[w];
+        a.logabsdet[b] = lad;
+      }
+      if (a.sign) a.sign[b] = s_sign;
+      if (s_flag && a.status) atomicOr(&a.status[b / a.status_div], s_flag);
+    }
+    __syncthreads();   // shared memory is reused by the next instance
+  }
+}
+
+template <int NW, int RPL>
+static cudaError_t launch_lu_small(const LuArgs& a, cudaStream_t st) {
+  const int grid = a.batch < (1 << 30) ? a.batch : (1 << 30);
+  lu_small_kernel<NW, RPL><<<grid, 32 * NW, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
 cudaError_t lu_solve_f64(const LuArgs& a0, cudaStream_t st) {
   if (a0.batch <= 0 || a0.N <= 0) return cudaSuccess;
+  // small systems: four lanes per column, one barrier per step (lu_small_kernel)
+  if (a0.N <= 32 && a0.nrhs >= 0 && a0.N + a0.nrhs <= 64) {
+    const int wd = a0.N + a0.nrhs;
+    if (a0.N <= 16) return wd <= 32 ? launch_lu_small<4, 4>(a0, st) : launch_lu_small<8, 4>(a0, st);
+    return wd <= 32 ? launch_lu_small<4, 8>(a0, st) : launch_lu_small<8, 8>(a0, st);
+  }
   LuArgs a = a0;
   size_t sm = (size_t)a.N * 3 * sizeof(double) + 16;
   // the augmented matrix in shared memory when it fits (227 KB per CTA): every

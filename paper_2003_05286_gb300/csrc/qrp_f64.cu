@@ -820,35 +820,6 @@ __global__ void __launch_bounds__(NT) qrp_fused_kernel(const QrpArgs a) {
 // group transforms its own column of Q.  Results agree with the other
 // kernels to rounding; sums run in a different order.
 // ---------------------------------------------------------------------------
-template <int I>
-struct RowIdx {
-  static constexpr int value = I;
-};
-
-// f(RowIdx<k>{}) for k = k0 .. NK-1 (k0 warp-uniform): the rows below k0 are
-// skipped by a jump, not predicated, because a predicated FP64 warp
-// instruction still holds the pipe for 64 cycles
-template <int NK, class F>
-__device__ __forceinline__ void ks_from(int k0, F&& f) {
-  static_assert(NK >= 1 && NK <= 8, "at most 8 rows per lane");
-  if constexpr (NK <= 2) {
-    if (k0 <= 0) f(RowIdx<0>{});
-    if constexpr (NK > 1) if (k0 <= 1) f(RowIdx<1>{});
-    return;
-  }
-  switch (k0) {
-    case 0: f(RowIdx<0>{}); [[fallthrough]];
-    case 1: if constexpr (NK > 1) f(RowIdx<1>{}); [[fallthrough]];
-    case 2: if constexpr (NK > 2) f(RowIdx<2>{}); [[fallthrough]];
-    case 3: if constexpr (NK > 3) f(RowIdx<3>{}); [[fallthrough]];
-    case 4: if constexpr (NK > 4) f(RowIdx<4>{}); [[fallthrough]];
-    case 5: if constexpr (NK > 5) f(RowIdx<5>{}); [[fallthrough]];
-    case 6: if constexpr (NK > 6) f(RowIdx<6>{}); [[fallthrough]];
-    case 7: if constexpr (NK > 7) f(RowIdx<7>{}); [[fallthrough]];
-    default: break;
-  }
-}
-
 // sum over the TPC lanes of a column group; every lane gets the same value
 // (each butterfly level adds the same two partial sums on both sides)
 template <int TPC>

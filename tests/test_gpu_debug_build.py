@@ -96,7 +96,11 @@ def _child(path):
     import paper_2003_05286_gb300 as dq
     assert dq.is_debug_build()
     fired, value = dq.selftest_check()
-    out = _workload(dq)
+    try:
+        out = _workload(dq)
+    except RuntimeError:
+        print("recorded check failure:", dq.debug_read())
+        raise
     torch.save({"out": out, "fired": fired, "value": value, "failure": dq.debug_read(clear=True)},
                path)
 
