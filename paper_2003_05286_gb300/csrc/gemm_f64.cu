@@ -220,6 +220,17 @@ cudaError_t gemm_f64(const GemmArgs& a, cudaStream_t st) {
     return cudaGetLastError();
   }
   const int tile = a.tile ? a.tile : pick_tile(a.M, a.N);
+  if (!a.tile) {
+    // a product too small to fill the GPU with this tile (a single instance,
+    // e.g. the Taylor steps of the matrix exponential: 16 CTAs of 64 x 64 at
+    // N = 256) takes 16 x 16 tiles, one output per thread, so that every SM
+    // gets FP64 work; the K order of each output is unchanged
+    const long long ctas = (long long)zb * ((a.M + tile - 1) / tile) * ((a.N + tile - 1) / tile);
+    if (ctas < device_sms()) {
+      launch_gemm<16, 16, 1, 1>(a, zb, st);
+      return cudaGetLastError();
+    }
+  }
   if (tile == 64) launch_gemm<64, 64, 4, 4>(a, zb, st);        // 256 threads, 4x4 each
   else if (tile == 48) launch_gemm<48, 48, 3, 3>(a, zb, st);   // 256 threads, 3x3 each
   else launch_gemm<32, 32, 4, 4>(a, zb, st);                   // 64 threads, 4x4 each
