@@ -589,7 +589,39 @@ struct ChainJob {
   Slots s;
   ChainWs w;
   int* status = nullptr;
+  const int* lim = nullptr;   // per-instance chain length (ragged groups), nullable
 };
+
+// nj contiguous sub-batches of a batch whose slots, workspace, fields (sV
+// apart), status and chain lengths (lim, nullable) are laid out per instance:
+// J[q] holds instances [o_q, o_q + n_q), n_q = batch / nj or one more.
+void make_sub_jobs(ChainJob* J, int nj, int dir, int batch, int N, const double* expV,
+                   long long sV, const Slots& s, const ChainWs& cw, int* status,
+                   const int* lim) {
+  const long long NN = (long long)N * N;
+  long long o = 0;
+  for (int q = 0; q < nj; ++q) {
+    const int nb = batch / nj + (q < batch % nj ? 1 : 0);
+    J[q].dir = dir;
+    J[q].batch = nb;
+    J[q].expV = expV + o * sV;
+    J[q].sV = sV;
+    J[q].s = s;
+    J[q].s.U += o * NN; J[q].s.D += o * N; J[q].s.X += o * NN; J[q].s.X2 += o * NN;
+    J[q].w = cw;
+    J[q].w.C0 += o * NN; J[q].w.C1 += o * NN; J[q].w.W += o * NN; J[q].w.T += o * NN;
+    J[q].w.perm += o * N;
+    if (cw.oz_s > 0) {
+      J[q].w.ozB += o * cw.oz_s * (long long)cw.oz_PK * cw.oz_PK;
+      J[q].w.ozeB += o * cw.oz_PK;
+      J[q].w.ozT += o * cw.oz_s * (long long)cw.oz_P128 * cw.oz_PK;
+      J[q].w.ozeT += o * cw.oz_P128;
+    }
+    J[q].status = status + o;
+    J[q].lim = lim ? lim + o : nullptr;
+    o += nb;
+  }
+}
 
 // Pipelining can be switched off with DQMC_PIPELINE=0 (for A/B timing).
 bool pipeline_enabled() {
@@ -606,14 +638,18 @@ int pipeline_jobs(bool mixed) {
   return mixed ? 4 : 2;
 }
 
+// The jobs run on aux streams sbase .. sbase + nj - 1, forked from and joined
+// back into the current stream h->cur.
 dqmc_status run_chain_multi(dqmc_handle h, const ChainJob* job, int nj, int N, int M, int k,
-                            const double* E) {
-  if (nj < 1 || nj > kMaxJobs) return DQMC_ERR_ARG;
-  CKS(ensure_aux(h, (size_t)nj));
-  cudaStream_t main = h->stream;
-  cudaEvent_t fork = h->auxev[0];
+                            const double* E, int sbase = 0) {
+  if (nj < 1 || nj > kMaxJobs || sbase < 0) return DQMC_ERR_ARG;
+  CKS(ensure_aux(h, (size_t)(sbase + nj)));
+  cudaStream_t main = h->cur;
+  cudaStream_t* aux = h->aux.data() + sbase;
+  cudaEvent_t* auxev = h->auxev.data() + sbase;
+  cudaEvent_t fork = auxev[0];
   cudaEventRecord(fork, main);
-  for (int i = 0; i < nj; ++i) cudaStreamWaitEvent(h->aux[i], fork, 0);
+  for (int i = 0; i < nj; ++i) cudaStreamWaitEvent(aux[i], fork, 0);
   cudaEvent_t ev[kMaxJobs] = {};
   dqmc_status rc = DQMC_OK;
   for (int i = 0; i < nj && rc == DQMC_OK; ++i)
@@ -623,22 +659,22 @@ dqmc_status run_chain_multi(dqmc_handle h, const ChainJob* job, int nj, int N, i
     for (int i = 0; i < nj && rc == DQMC_OK; ++i) {
       const ChainJob& J = job[i];
       const int c = J.dir > 0 ? step : nc - 1 - step;
-      h->cur = h->aux[i];
+      h->cur = aux[i];
       // product phases run one after another: job i after job i-1 of this
       // chunk, job 0 after the last job of the previous chunk
       if (i > 0) cudaStreamWaitEvent(h->cur, ev[i - 1], 0);
       else if (step > 0) cudaStreamWaitEvent(h->cur, ev[nj - 1], 0);
       const double* A = nullptr;
-      rc = chunk_products(h, J.dir, J.batch, N, M, k, c, E, J.expV, J.sV, J.s, J.w, nullptr, &A,
+      rc = chunk_products(h, J.dir, J.batch, N, M, k, c, E, J.expV, J.sV, J.s, J.w, J.lim, &A,
                           J.status);
       if (rc != DQMC_OK) break;
       cudaEventRecord(ev[i], h->cur);
-      rc = chunk_refactor(h, J.dir, J.batch, N, k, c, A, J.s, J.w, J.status, nullptr);
+      rc = chunk_refactor(h, J.dir, J.batch, N, k, c, A, J.s, J.w, J.status, J.lim);
     }
   }
   for (int i = 0; i < nj; ++i) {
-    cudaEventRecord(h->auxev[i], h->aux[i]);
-    cudaStreamWaitEvent(main, h->auxev[i], 0);
+    cudaEventRecord(auxev[i], aux[i]);
+    cudaStreamWaitEvent(main, auxev[i], 0);
   }
   for (int i = 0; i < nj; ++i)
     if (ev[i]) cudaEventDestroy(ev[i]);
@@ -1378,27 +1414,7 @@ static dqmc_status greens_impl(dqmc_handle h, int batch, int N, int M, const dou
       // nj sub-batches on nj streams, product phases staggered so that the QRs
       // of some sub-batches run while the others multiply
       ChainJob J[kMaxJobs];
-      long long o = 0;
-      for (int q = 0; q < nj; ++q) {
-        const int nb = batch / nj + (q < batch % nj ? 1 : 0);
-        J[q].dir = +1;
-        J[q].batch = nb;
-        J[q].expV = expV + o * Mp * N;
-        J[q].sV = Mp * N;
-        J[q].s = s;
-        J[q].s.U += o * NN; J[q].s.D += o * N; J[q].s.X += o * NN; J[q].s.X2 += o * NN;
-        J[q].w = cw;
-        J[q].w.C0 += o * NN; J[q].w.C1 += o * NN; J[q].w.W += o * NN; J[q].w.T += o * NN;
-        J[q].w.perm += o * N;
-        if (cw.oz_s > 0) {
-          J[q].w.ozB += o * cw.oz_s * (long long)cw.oz_PK * cw.oz_PK;
-          J[q].w.ozeB += o * cw.oz_PK;
-          J[q].w.ozT += o * cw.oz_s * (long long)cw.oz_P128 * cw.oz_PK;
-          J[q].w.ozeT += o * cw.oz_P128;
-        }
-        J[q].status = stout + o;
-        o += nb;
-      }
+      make_sub_jobs(J, nj, +1, batch, N, expV, Mp * N, s, cw, stout, nullptr);
       CKS(run_chain_multi(h, J, nj, N, M, k, E));
     } else {
       CKS(run_chain(h, +1, batch, N, M, k, E, expV, Mp * N, s, cw, stout));
@@ -2315,7 +2331,12 @@ static dqmc_status ragged_impl(dqmc_handle h, int batch, const dqmc_instance* de
     h->rtab_key = dkey;
   }
   // ---- streams and the fork event (created outside any capture) --------------
-  const size_t nstreams = groups.size() < 8 ? groups.size() : 8;
+  // up to 8 group slots; a slot has its group's stream and nj more for the
+  // staggered sub-batches of a group large enough to pipeline
+  const int nj = pipeline_jobs(mixed);
+  const size_t nslots = groups.size() < 8 ? groups.size() : 8;
+  const size_t per_slot = (size_t)nj + 1;
+  const size_t nstreams = nslots * per_slot;
   CKS(ensure_aux(h, nstreams));
   if (!h->rfork && cudaEventCreateWithFlags(&h->rfork, cudaEventDisableTiming) != cudaSuccess) {
     h->rfork = nullptr;
@@ -2343,7 +2364,8 @@ static dqmc_status ragged_impl(dqmc_handle h, int batch, const dqmc_instance* de
       const long long NN = (long long)N * N;
       const int ncmax = n_chunks(g.Mmax, k);
       const long long Mp = (long long)(ncmax + 1) * k;
-      h->cur = h->aux[i % nstreams];
+      const size_t slot = (i % nslots) * per_slot;
+      h->cur = h->aux[slot];
       cudaStream_t st = h->cur;
       rc = [&]() -> dqmc_status {
         if (cudaMemsetAsync(w.st, 0, nb * sizeof(int), st) != cudaSuccess) return DQMC_ERR_CUDA;
@@ -2359,7 +2381,15 @@ static dqmc_status ragged_impl(dqmc_handle h, int batch, const dqmc_instance* de
         sl.D = w.D; sl.slotD = 0; sl.instD = N;
         sl.X = w.X0; sl.slotX = 0; sl.instX = NN;
         sl.X2 = w.X1;
-        CKS(run_chain(h, +1, nb, N, g.Mmax, k, E, w.expV, Mp * N, sl, w.cw, w.st, w.Mb));
+        if (nb >= 4 * nj && pipeline_enabled()) {
+          // as a uniform call: sub-batches on their own streams, staggered so
+          // that the QRs of some run while the others multiply
+          ChainJob J[kMaxJobs];
+          make_sub_jobs(J, nj, +1, nb, N, w.expV, Mp * N, sl, w.cw, w.st, w.Mb);
+          CKS(run_chain_multi(h, J, nj, N, g.Mmax, k, E, (int)slot + 1));
+        } else {
+          CKS(run_chain(h, +1, nb, N, g.Mmax, k, E, w.expV, Mp * N, sl, w.cw, w.st, w.Mb));
+        }
         const double* Xf = (ncmax & 1) ? w.X1 : w.X0;
         CKS(run_inversion(h, nb, N, w.U, NN, w.D, N, Xf, NN, G_pool ? w.G : nullptr, w.ld, w.sg,
                           w.st, w.lw, w.pw));
