@@ -113,8 +113,7 @@ __global__ void __launch_bounds__(CS_NT, 1) chain_small_kernel(const ChainSmallA
 template <int RPT>
 cudaError_t launch_chain_small(const ChainSmallArgs& a, cudaStream_t st) {
   const size_t sm = ((size_t)a.N * a.N + 2 * (size_t)a.N * CS_CB) * sizeof(double);
-  cudaError_t e = cudaFuncSetAttribute(chain_small_kernel<RPT>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e = allow_dyn_smem(chain_small_kernel<RPT>);
   if (e != cudaSuccess) return e;
   const dim3 grid((a.N + CS_CB - 1) / CS_CB, a.batch);
   chain_small_kernel<RPT><<<grid, CS_NT, sm, st>>>(a);

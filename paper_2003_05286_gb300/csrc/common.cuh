@@ -12,6 +12,22 @@ namespace dqmc {
 // it is a property of the GPU, not of a context).
 int device_sms();
 
+// Largest dynamic shared memory a CTA of the current device may opt into
+// (queried once per device index and kept).
+int device_smem_optin();
+
+// Opts a kernel into the device's whole dynamic shared memory rather than the
+// size of the launch at hand: one function (one template instance) serves
+// launches of different sizes (e.g. the QR with its matrix resident at
+// N = 144 and in L2 at N = 256), and a CUDA graph recorded with several of
+// them must not depend on which launch set the attribute last.  The
+// attribute only caps; each launch still allocates its own size.
+template <class Kernel>
+inline cudaError_t allow_dyn_smem(Kernel* kernel) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              device_smem_optin());
+}
+
 // Grid of a grid-stride element-wise kernel over n items with tpb threads per
 // block: enough blocks for n, at most 64 per SM of the current device.
 inline int grid_stride_blocks(long long n, int tpb) {

@@ -28,6 +28,26 @@ int device_sms() {
   return sms;
 }
 
+int device_smem_optin() {
+  constexpr int kMaxDev = 64;
+  static int cache[kMaxDev] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 227 * 1024;
+  }
+  if (dev >= 0 && dev < kMaxDev && __atomic_load_n(&cache[dev], __ATOMIC_RELAXED) > 0)
+    return __atomic_load_n(&cache[dev], __ATOMIC_RELAXED);
+  int b = 0;
+  if (cudaDeviceGetAttribute(&b, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+      b <= 0) {
+    cudaGetLastError();
+    return 227 * 1024;
+  }
+  if (dev >= 0 && dev < kMaxDev) __atomic_store_n(&cache[dev], b, __ATOMIC_RELAXED);
+  return b;
+}
+
 namespace {
 constexpr int TPB = 256;
 inline int nblocks(long long n) { return grid_stride_blocks(n, TPB); }

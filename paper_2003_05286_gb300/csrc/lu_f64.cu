@@ -428,13 +428,13 @@ cudaError_t lu_solve_f64(const LuArgs& a0, cudaStream_t st) {
   if (a.smem_w) sm += wb;
   int grid = a.batch < (1 << 30) ? a.batch : (1 << 30);
   if (a.N + a.nrhs <= 64) {
-    cudaFuncSetAttribute(lu_kernel<64, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    allow_dyn_smem(lu_kernel<64, 1>);
     lu_kernel<64, 1><<<grid, 64, sm, st>>>(a);
   } else if (a.N + a.nrhs <= 256) {
-    cudaFuncSetAttribute(lu_kernel<256, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    allow_dyn_smem(lu_kernel<256, 1>);
     lu_kernel<256, 1><<<grid, 256, sm, st>>>(a);
   } else {
-    cudaFuncSetAttribute(lu_kernel<512, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    allow_dyn_smem(lu_kernel<512, 2>);
     lu_kernel<512, 2><<<grid, 512, sm, st>>>(a);
   }
   return cudaGetLastError();

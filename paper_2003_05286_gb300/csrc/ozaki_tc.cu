@@ -674,7 +674,7 @@ cudaError_t ozaki_split(const double* X, long long ldm, long long ldj, long long
   const size_t sm = (size_t)PM * 33 * sizeof(double);
   const dim3 grid((PJ + 31) / 32, batch);
   auto go = [&](auto kern) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    allow_dyn_smem(kern);
     kern<<<grid, 256, sm, st>>>(X, ldm, ldj, sX, sc, ssc, N, PJ, PM, R, S, sS, e, se, gm, sgm);
     return cudaGetLastError();
   };
@@ -713,7 +713,7 @@ static cudaError_t ozaki_gemm_impl(const __nv_bfloat16* As, const int* eA, long 
     if (pr.g[i] != pr.p[i] + pr.q[i]) return cudaErrorNotSupported;
   pr.stall = stall;
   size_t sm = oz_gemm_smem(s);
-  cudaFuncSetAttribute(ozaki_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  allow_dyn_smem(ozaki_gemm_kernel);
   dim3 grid((N + OZ_BN - 1) / OZ_BN, (N + OZ_BM - 1) / OZ_BM, batch);
   ozaki_gemm_kernel<<<grid, OZ_THREADS, sm, st>>>(As, sA, P128, Bs, PN, pr, N, PK / OZ_BK, eA, seA,
                                                   sA != 0, eB, seB, C, sC, status, lim, lim_at,

@@ -1052,8 +1052,7 @@ static cudaError_t launch_qrp_fused(const QrpArgs& a0, cudaStream_t st) {
   a.smem_mats = base + 2 * mat <= kSmemLimit ? 2 : (base + mat <= kSmemLimit ? 1 : 0);
   const size_t sm = base + a.smem_mats * mat;
   const int grid = a.batch < (1 << 30) ? a.batch : (1 << 30);
-  cudaError_t e = cudaFuncSetAttribute(qrp_fused_kernel<NT, TPC, NQ>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e = allow_dyn_smem(qrp_fused_kernel<NT, TPC, NQ>);
   if (e != cudaSuccess) return e;
   qrp_fused_kernel<NT, TPC, NQ><<<grid, NT, sm, st>>>(a);
   return cudaGetLastError();
@@ -1072,13 +1071,13 @@ cudaError_t qrp_f64(const QrpArgs& a, cudaStream_t st) {
   size_t sm = qrp_smem(a.N);
   int grid = a.batch < (1 << 30) ? a.batch : (1 << 30);
   if (a.N <= 32) {
-    cudaFuncSetAttribute(qrp_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    allow_dyn_smem(qrp_kernel<32>);
     qrp_kernel<32><<<grid, 32, sm, st>>>(a);
   } else if (a.N <= 128) {
-    cudaFuncSetAttribute(qrp_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    allow_dyn_smem(qrp_kernel<128>);
     qrp_kernel<128><<<grid, 128, sm, st>>>(a);
   } else {
-    cudaFuncSetAttribute(qrp_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    allow_dyn_smem(qrp_kernel<256>);
     qrp_kernel<256><<<grid, 256, sm, st>>>(a);
   }
   return cudaGetLastError();
