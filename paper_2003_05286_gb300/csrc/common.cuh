@@ -21,11 +21,16 @@ int device_smem_optin();
 // launches of different sizes (e.g. the QR with its matrix resident at
 // N = 144 and in L2 at N = 256), and a CUDA graph recorded with several of
 // them must not depend on which launch set the attribute last.  The
-// attribute only caps; each launch still allocates its own size.
+// attribute only caps; each launch still allocates its own size.  The cap is
+// the opt-in limit less the kernel's static shared memory (their sum may not
+// exceed the limit).
 template <class Kernel>
 inline cudaError_t allow_dyn_smem(Kernel* kernel) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              device_smem_optin());
+                              device_smem_optin() - (int)fa.sharedSizeBytes);
 }
 
 // Grid of a grid-stride element-wise kernel over n items with tpb threads per
@@ -303,7 +308,7 @@ struct RowIdx {
 // instruction still holds its sub-partition's pipe for 64 cycles
 template <int NK, class F>
 __device__ __forceinline__ void ks_from(int k0, F&& f) {
-  static_assert(NK >= 1 && NK <= 8, "at most 8 rows per lane");
+  static_assert(NK >= 1 && NK <= 16, "at most 16 rows per lane");
   if constexpr (NK <= 2) {
     if (k0 <= 0) f(RowIdx<0>{});
     if constexpr (NK > 1) if (k0 <= 1) f(RowIdx<1>{});
@@ -318,6 +323,14 @@ __device__ __forceinline__ void ks_from(int k0, F&& f) {
     case 5: if constexpr (NK > 5) f(RowIdx<5>{}); [[fallthrough]];
     case 6: if constexpr (NK > 6) f(RowIdx<6>{}); [[fallthrough]];
     case 7: if constexpr (NK > 7) f(RowIdx<7>{}); [[fallthrough]];
+    case 8: if constexpr (NK > 8) f(RowIdx<8>{}); [[fallthrough]];
+    case 9: if constexpr (NK > 9) f(RowIdx<9>{}); [[fallthrough]];
+    case 10: if constexpr (NK > 10) f(RowIdx<10>{}); [[fallthrough]];
+    case 11: if constexpr (NK > 11) f(RowIdx<11>{}); [[fallthrough]];
+    case 12: if constexpr (NK > 12) f(RowIdx<12>{}); [[fallthrough]];
+    case 13: if constexpr (NK > 13) f(RowIdx<13>{}); [[fallthrough]];
+    case 14: if constexpr (NK > 14) f(RowIdx<14>{}); [[fallthrough]];
+    case 15: if constexpr (NK > 15) f(RowIdx<15>{}); [[fallthrough]];
     default: break;
   }
 }
