@@ -9,6 +9,11 @@ the library, compares G with a reference computed at a small k, times it with
 CUDA events, and returns the fastest candidate whose deviation stays within
 ``tol``.  Results are cached per (N, M, dtau, precision, SM count).
 
+The environment variable DQMC_TUNE selects the mode: ``on`` (default) uses a
+cached result when there is one, ``force`` tunes again and overwrites the
+cache, ``off`` times nothing and returns ``default_k`` with the library's
+tile choice.
+
 All computation runs through the library's C ABI; this module only chooses
 parameters.
 """
@@ -29,6 +34,14 @@ def _key(N, M, dtau, prec, tag):
     return f"N{N}-M{M}-dt{dtau:g}-p{prec}-sm{sm}-{tag}"
 
 
+def tune_mode() -> str:
+    """DQMC_TUNE: 'on' (default), 'force' or 'off'; anything else is an error."""
+    mode = os.environ.get("DQMC_TUNE", "on").strip().lower() or "on"
+    if mode not in ("on", "force", "off"):
+        raise ValueError(f"DQMC_TUNE must be on, force or off (got {mode!r})")
+    return mode
+
+
 def _time_ms(fn, reps):
     fn()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
@@ -43,7 +56,8 @@ def _time_ms(fn, reps):
 
 def tune(K: torch.Tensor, dtau: float, V: torch.Tensor, *, candidates=(5, 8, 10, 12, 15, 20),
          tiles=(0, 32, 48, 64), ref_k: int = 2, tol: float = 1e-10, chain_precision: int = 0,
-         reps: int = 2, cache_file: str | None = None, tag: str = "", fold: int | None = None):
+         reps: int = 2, cache_file: str | None = None, tag: str = "", fold: int | None = None,
+         default_k: int = 10):
     """Pick (k, tile) for fields shaped like V (B, M, N).
 
     Returns (best, table): best = dict(k, tile, err, ms); table = every
@@ -53,11 +67,14 @@ def tune(K: torch.Tensor, dtau: float, V: torch.Tensor, *, candidates=(5, 8, 10,
     batch should be timed with the fold the large batch will run."""
     V3 = V if V.dim() == 3 else V.unsqueeze(0)
     B, M, N = V3.shape
+    mode = tune_mode()
+    if mode == "off":
+        return dict(k=min(default_k, M), tile=0, err=None, ms=None), None
     key = _key(N, M, dtau, chain_precision, tag + ("" if fold is None else f"-f{fold}"))
     if cache_file and not _CACHE and os.path.exists(cache_file):
         with open(cache_file) as f:
             _CACHE.update(json.load(f))
-    if key in _CACHE:
+    if key in _CACHE and mode == "on":
         return _CACHE[key], None
     href = Handle()
     Gref = greens(K, dtau, V3, min(ref_k, M), handle=href)[0]

@@ -118,3 +118,16 @@ def test_memory_limit_rejects_bad_arguments(lib):
     lib.dqmc_device_bytes.restype = ctypes.c_longlong
     lib.dqmc_device_bytes.argtypes = [ctypes.c_void_p]
     assert lib.dqmc_device_bytes(None) == -1
+
+
+def test_tune_mode_parsing(monkeypatch):
+    """The tuner's mode switch is host logic (no GPU needed)."""
+    from paper_2003_05286_gb300 import tune
+    for v, want in (("", "on"), ("on", "on"), ("FORCE", "force"), (" off ", "off")):
+        monkeypatch.setenv("DQMC_TUNE", v)
+        assert tune.tune_mode() == want
+    monkeypatch.delenv("DQMC_TUNE")
+    assert tune.tune_mode() == "on"
+    monkeypatch.setenv("DQMC_TUNE", "x")
+    with pytest.raises(ValueError):
+        tune.tune_mode()
