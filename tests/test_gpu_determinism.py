@@ -61,3 +61,30 @@ def test_stacks_bitwise_across_runs_and_schedules(dq):
         runs = _run(dq, fn, 0, "0") + _run(dq, fn, 0, "1")
         for r in runs[1:]:
             assert all(torch.equal(a, b) for a, b in zip(runs[0], r) if a is not None)
+
+
+@pytest.mark.parametrize("prec", [0, 8])
+def test_ragged_bitwise_across_runs_and_schedules(dq, prec):
+    """Ragged groups large enough to run as staggered sub-batches (with the
+    per-instance chain lengths of uneven M): bitwise equal to the unpipelined
+    schedule and to a second call."""
+    rng = np.random.default_rng(61)
+    insts = []
+    for i in range(40):
+        L = 4 if i < 20 else 6
+        beta = round(float(rng.uniform(2.0, 6.0)), 1)
+        insts.append(di.hubbard_instance(L, 4.0, 0.1, beta, 10, 6100 + i))
+    Ks = {4: torch.tensor(di.square_hopping(4), device="cuda"),
+          6: torch.tensor(di.square_hopping(6), device="cuda")}
+    items = [(Ks[int(round(x.N ** 0.5))], x.dtau, torch.tensor(x.V, device="cuda"), x.k)
+             for x in insts]
+    batch = dq.RaggedBatch(items)
+
+    def fn(h):
+        Gs, ld, sg, st = batch.run(handle=h)
+        assert int((st != 0).sum()) == 0
+        return tuple(g.clone() for g in Gs) + (ld.clone(), sg.clone())
+
+    runs = _run(dq, fn, prec, "0") + _run(dq, fn, prec, "2") + _run(dq, fn, prec, "4")
+    for r in runs[1:]:
+        assert all(torch.equal(a, b) for a, b in zip(runs[0], r))
