@@ -485,6 +485,8 @@ dqmc_status chunk_qr(dqmc_handle h, int dir, int batch, int N, int k, int c, con
   q.perm = w.perm; q.sperm = N;
   q.status = status;
   q.lim = lim; q.lim_at = c * k + 1;
+  // the FP64 chain's products can share SMs with this QR (see qrp_f64.cu)
+  q.share_sm = h->prec == DQMC_CHAIN_FP64 ? 1 : 0;
   if (h->decomp == DQMC_DECOMP_JACOBI) {
     // U' D' V'^T by one-sided Jacobi; V'^T goes where T' would
     JacobiArgs j;

@@ -124,6 +124,7 @@ struct QrpArgs {
   int* status = nullptr; int status_div = 1;          // nullable
   const int* lim = nullptr; int lim_at = 0;           // skip instance b when lim[b] < lim_at
   int smem_mats = 0;                                  // set by the launcher
+  int share_sm = 0;   // N <= 256: the register-capped kernel that fits beside an FP64 GEMM CTA
 };
 
 cudaError_t qrp_f64(const QrpArgs& a, cudaStream_t st);

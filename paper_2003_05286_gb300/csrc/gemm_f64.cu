@@ -14,8 +14,9 @@
 namespace dqmc {
 
 template <int BM, int BN, int BK, int TM, int TN>
-// At most 168 registers: a 256-thread CTA then leaves room on its SM for one
-// pivoted-QR CTA of the other half-batch (the two run concurrently).
+// At most 168 registers (the 64 x 64 tile takes 120): a 256-thread CTA then
+// fits an SM beside one 512-thread pivoted-QR CTA of 64 registers, so the
+// products of one sub-batch can share SMs with the QRs of another.
 __global__ void __maxnreg__(168)
 gemm_f64_kernel(const GemmArgs a) {
   constexpr int NTX = BN / TN;

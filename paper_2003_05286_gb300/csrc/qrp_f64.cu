@@ -498,8 +498,16 @@ __device__ __forceinline__ double group_sum(double v) {
 
 }  // namespace
 
-template <int NT, int TPC, int NQ>
-__global__ void __launch_bounds__(NT) qrp_fused_kernel(const QrpArgs a) {
+// MINB = 2 holds the 512-thread instance (N <= 256) to 64 registers, so that
+// one QR CTA and one 256-thread FP64 GEMM CTA fit an SM together: the
+// pipelined FP64 chain runs the QR of one sub-batch beside the products of
+// another, and the QR leaves part of its SM's FP64 pipe idle.  The register
+// cap costs the QR a few spills, so chains whose step is bound by the QR's
+// latency (the tensor-core chain) take MINB = 0: no minimum, the compiler's
+// own register choice (an explicit minimum of 1 lets it take ~200 registers
+// in the 128- and 256-thread instances and costs them resident CTAs).
+template <int NT, int TPC, int NQ, int MINB = 0>
+__global__ void __launch_bounds__(NT, MINB) qrp_fused_kernel(const QrpArgs a) {
   constexpr int NW = NT / 32, CPW = 32 / TPC, BATCH = 8;
   // warps of the reflector step and rows per lane each
   constexpr int NR = (NQ >= 4 && NW >= 4) ? 4 : 1, KQ = NQ / NR;
@@ -1047,16 +1055,16 @@ constexpr size_t kSmemLimit = 227 * 1024;
 // memory: every step of the factorisation reads and updates the trailing
 // columns, and from L2 each of those passes costs a round trip the step has
 // to wait for.  N <= 160 fits W, N <= 112 fits W and Q.
-template <int NT, int TPC, int NQ>
+template <int NT, int TPC, int NQ, int MINB = 0>
 static cudaError_t launch_qrp_fused(const QrpArgs& a0, cudaStream_t st) {
   QrpArgs a = a0;
   const size_t base = qrp_fused_smem(a.N), mat = (size_t)a.N * a.N * sizeof(double);
   a.smem_mats = base + 2 * mat <= kSmemLimit ? 2 : (base + mat <= kSmemLimit ? 1 : 0);
   const size_t sm = base + a.smem_mats * mat;
   const int grid = a.batch < (1 << 30) ? a.batch : (1 << 30);
-  cudaError_t e = allow_dyn_smem(qrp_fused_kernel<NT, TPC, NQ>);
+  cudaError_t e = allow_dyn_smem(qrp_fused_kernel<NT, TPC, NQ, MINB>);
   if (e != cudaSuccess) return e;
-  qrp_fused_kernel<NT, TPC, NQ><<<grid, NT, sm, st>>>(a);
+  qrp_fused_kernel<NT, TPC, NQ, MINB><<<grid, NT, sm, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -1072,7 +1080,8 @@ cudaError_t qrp_f64(const QrpArgs& a, cudaStream_t st) {
   if (a.N <= 32) return launch_qrp_small<4, 4>(a, st);
   if (a.N <= 64) return launch_qrp_fused<128, 2, 2>(a, st);
   if (a.N <= 128) return launch_qrp_fused<256, 2, 4>(a, st);
-  if (a.N <= 256) return launch_qrp_fused<512, 2, 8>(a, st);
+  if (a.N <= 256)
+    return a.share_sm ? launch_qrp_fused<512, 2, 8, 2>(a, st) : launch_qrp_fused<512, 2, 8>(a, st);
   size_t sm = qrp_smem(a.N);
   int grid = a.batch < (1 << 30) ? a.batch : (1 << 30);
   if (a.N <= 32) {
