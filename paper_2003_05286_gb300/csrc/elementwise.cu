@@ -377,15 +377,26 @@ cudaError_t expm_prepare(const double* K, int N, double dtau, double sgn, int* s
   return cudaGetLastError();
 }
 
-// The whole matrix exponential of a small K (N <= 16) in one CTA: the same
-// scaling as expm_prepare, the same Horner steps T <- I + (scale/m) K T and
-// squarings T <- T T as the product kernels compute them (each entry an FMA
-// chain over k = 0..N-1, then the scale, then the identity), in shared memory.
-// Replaces ~30 dependent launches of tiny products for a single small lattice.
-__global__ void expm_small_kernel(const double* K, int N, double dtau, double sgn, int terms,
-                                  int max_sq, double* E, int* asym, int* status, int batch,
-                                  int bad_bit) {
-  __shared__ double Ks[256], T0[256], T1[256], red[256];
+// Taylor coefficients 1/m! of the degree-16 polynomial, m = 0..16, each the
+// correctly rounded reciprocal of m! (exact in FP64 up to 18!).
+struct TaylorCoef {
+  double c[17];
+};
+
+// The whole matrix exponential of a small K (N <= 16) in one CTA, in shared
+// memory: the same scaling as expm_prepare, then the degree-16 Taylor
+// polynomial p(X) = sum_m X^m / m! of X = scale K by the method of Paterson
+// and Stockmeyer (1973) with blocks of four: X^2, then X^3 and X^4 together,
+// then p = B_0 + X^4 (B_1 + X^4 (B_2 + X^4 (B_3 + c_16 X^4))) with
+// B_q = c_4q I + c_4q+1 X + c_4q+2 X^2 + c_4q+3 X^3 formed entrywise: five
+// dependent product steps where a Horner evaluation takes sixteen (the step
+// count is what bounds a single small instance).  Then s squarings.  Each
+// product entry is one FMA chain over k = 0..N-1.  Replaces ~30 dependent
+// launches of tiny products for a single small lattice.
+__global__ void expm_small_kernel(const double* K, int N, double dtau, double sgn,
+                                  const TaylorCoef cf, int max_sq, double* E, int* asym,
+                                  int* status, int batch, int bad_bit) {
+  __shared__ double Ks[256], T0[256], T1[256], red[256], P2[256], P3[256], P4[256];
   __shared__ int bad, s_sq;
   __shared__ double s_scale;
   const int tid = threadIdx.x;
@@ -423,18 +434,34 @@ __global__ void expm_small_kernel(const double* K, int N, double dtau, double sg
       for (int b = 0; b < batch; ++b) status[b] |= bad_bit;
   }
   __syncthreads();
-  double* cur = T0;
-  double* nxt = T1;
   const int i = tid / N, j = tid % N;
   const bool own = tid < N * N;
-  for (int m = terms; m >= 1; --m) {
-    if (own) {
-      double acc = 0.0;
-      for (int k = 0; k < N; ++k) acc = fma(Ks[i * N + k], cur[k * N + j], acc);
-      double v = acc * ((1.0 / m) * s_scale);
-      if (i == j) v += 1.0;
-      nxt[tid] = v;
-    }
+  auto prod = [&](const double* A, const double* B) {
+    double acc = 0.0;
+    for (int k = 0; k < N; ++k) acc = fma(A[i * N + k], B[k * N + j], acc);
+    return acc;
+  };
+  // B_q at this entry
+  auto block = [&](int q) {
+    double v = fma(cf.c[4 * q + 3], P3[tid], fma(cf.c[4 * q + 2], P2[tid], cf.c[4 * q + 1] * Ks[tid]));
+    if (i == j) v += cf.c[4 * q];
+    return v;
+  };
+  if (own) Ks[tid] *= s_scale;                    // X = scale K, in place
+  __syncthreads();
+  if (own) P2[tid] = prod(Ks, Ks);
+  __syncthreads();
+  if (own) {
+    P3[tid] = prod(P2, Ks);
+    P4[tid] = prod(P2, P2);
+  }
+  __syncthreads();
+  double* cur = T0;
+  double* nxt = T1;
+  if (own) cur[tid] = fma(cf.c[16], P4[tid], block(3));
+  __syncthreads();
+  for (int q = 2; q >= 0; --q) {
+    if (own) nxt[tid] = prod(P4, cur) + block(q);
     __syncthreads();
     double* t = cur; cur = nxt; nxt = t;
   }
@@ -453,8 +480,14 @@ __global__ void expm_small_kernel(const double* K, int N, double dtau, double sg
 cudaError_t expm_small(const double* K, int N, double dtau, double sgn, int terms, int max_sq,
                        double* E, int* asym, int* status, int batch, int bad_bit,
                        cudaStream_t st) {
-  if (N > 16) return cudaErrorInvalidValue;
-  expm_small_kernel<<<1, 256, 0, st>>>(K, N, dtau, sgn, terms, max_sq, E, asym, status, batch,
+  if (N > 16 || terms != 16) return cudaErrorInvalidValue;
+  TaylorCoef cf;
+  double fact = 1.0;   // m!, exact in FP64 for m <= 18
+  for (int m = 0; m <= 16; ++m) {
+    if (m > 0) fact *= m;
+    cf.c[m] = 1.0 / fact;
+  }
+  expm_small_kernel<<<1, 256, 0, st>>>(K, N, dtau, sgn, cf, max_sq, E, asym, status, batch,
                                        bad_bit);
   return cudaGetLastError();
 }
