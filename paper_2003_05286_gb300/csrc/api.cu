@@ -747,6 +747,10 @@ dqmc_status run_chain_tree(dqmc_handle h, int batch, int N, int M, int k, const 
   const int nc = n_chunks(M, k), P0 = w.P0;
   const int Q = batch * P0;
   const double f2 = 2.0 * N * (double)N * N;
+  // the U and X updates of a level are independent: X runs on an aux stream
+  CKS(ensure_aux(h, 2));
+  cudaStream_t sx = h->aux[0];
+  cudaEvent_t fork = h->auxev[0], join = h->auxev[1];
   CK(set_identity(w.Iden, 0, N, 1, st));
   CK(chunk_len(w.len, batch, P0, nc, k, M, st));
   // a1: C_c for every chunk of every instance (identity for the padding)
@@ -830,6 +834,10 @@ dqmc_status run_chain_tree(dqmc_handle h, int batch, int N, int M, int k, const 
     q.perm = w.perm; q.sperm = N;
     q.status = status; q.status_div = np;
     CKP(PC_QRP, 8.0 / 3.0 * N * N * (double)N * B2, qrp_f64(q, st));
+    // U = U_2 u here and X = x X_1 on the aux stream, joined before the
+    // next level's product reads both
+    if (cudaEventRecord(fork, st) != cudaSuccess || cudaStreamWaitEvent(sx, fork, 0) != cudaSuccess)
+      return DQMC_ERR_CUDA;
     GemmArgs gu;                                      // U = U_2 u
     gu.M = gu.N = gu.K = N; gu.batch = B2;
     gu.A = w.U[cur] + NN; gu.lda = N; gu.sA = 2 * NN;
@@ -843,7 +851,11 @@ dqmc_status run_chain_tree(dqmc_handle h, int batch, int N, int M, int k, const 
     gx.B = w.X[cur]; gx.ldb = N; gx.sB = 2 * NN;
     gx.permB = w.perm; gx.sperm = N;
     gx.C = w.X[nxt]; gx.ldc = N; gx.sC = NN;
-    CKP(PC_XUPD, (double)N * N * (double)N * B2, gemm_f64(gx, st));
+    h->cur = sx;
+    CKP(PC_XUPD, (double)N * N * (double)N * B2, gemm_f64(gx, sx));
+    h->cur = st;
+    if (cudaEventRecord(join, sx) != cudaSuccess || cudaStreamWaitEvent(st, join, 0) != cudaSuccess)
+      return DQMC_ERR_CUDA;
     cur = nxt;
   }
   *Uo = w.U[cur];
